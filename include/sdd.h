@@ -1,0 +1,210 @@
+/*
+ * libsdd -- GB300 (sm_103a) Monte Carlo evaluation of the Feynman-Kac
+ * representation of the TE (E-polarisation) magnetotelluric equation at the
+ * interface nodes of a stochastic domain decomposition (Bihlo, Farquharson,
+ * Haynes, Loredo-Osti, arXiv:1603.09311).
+ *
+ * The operation (Sec. 2.2 and Sec. 3.1).  For the TE mode the diffusion
+ * coefficient of the discontinuous elliptic problem is constant, so the
+ * equation is, in dimensionless form,
+ *     Lap u = i kappa(x) u   in the rectangle Omega,   u = g on dOmega,
+ * with kappa(x) = omega mu sigma(x) L^2 >= 0 piecewise constant over
+ * materials.  By the Kac-Feynman formula (Sec. 2.2)
+ *     u(x0) = E[ g(beta_tau) exp(-i (1/2) int_0^tau kappa(beta_s) ds) ],
+ * beta a standard 2D Brownian motion started at x0.  The library simulates
+ * beta with the Euler-Maruyama scheme of Sec. 3.1, ends each walk with the
+ * boundary-hitting rule of the first-exit-time estimate (linear interpolation
+ * on overshoot, Brownian-bridge test with one uniform when both ends are
+ * inside), counts the Euler steps spent in each material (the occupation
+ * times T_m of Sec. 3.1) and averages g(exit) exp(-i (1/2) sum_m kappa_m T_m)
+ * over the walks (the Monte Carlo estimator of Sec. 3.1).  One walk serves
+ * every evaluation e (a row kappa[e][.] of phase rates, e.g. a frequency),
+ * because the TE walk does not depend on kappa.
+ *
+ * Conventions common to all entry points:
+ *  - z grows downwards; air is z < 0, earth z >= 0.
+ *  - All arrays are dense, row-major, little-endian, in the units stated.
+ *  - The caller owns every array it passes.  Host arrays are read (or
+ *    written) before the call returns; device arrays passed to the *_device
+ *    entry points must stay valid until the work queued on the stream ends.
+ *  - The library owns the device copy of the model and its scratch buffers
+ *    (work-item table, per-item partial sums, counters) until sdd_destroy.
+ *  - Every entry point returns an sdd_status.  On any status other than
+ *    SDD_OK and SDD_E_TRUNCATED the outputs are undefined.  SDD_E_TRUNCATED
+ *    means some walks reached max_steps: they are left out of the averages,
+ *    the outputs are valid and stats->truncated counts them.
+ *  - A context may be used from one host thread at a time.
+ */
+#ifndef SDD_H
+#define SDD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SDD_OK = 0,
+    SDD_E_ARG = 1,         /* invalid argument (message via sdd_last_error) */
+    SDD_E_OOM = 2,         /* device or host allocation failed */
+    SDD_E_CUDA = 3,        /* a CUDA runtime call failed */
+    SDD_E_TRUNCATED = 4,   /* results valid; some walks hit max_steps */
+    SDD_E_CANCELLED = 5,   /* serving request cancelled */
+    SDD_E_TIMEOUT = 6,     /* a bounded wait gave up */
+    SDD_E_UNSUPPORTED = 7, /* no kernel for this configuration */
+    SDD_E_BUSY = 8         /* serving admission refused: no slot or memory */
+} sdd_status;
+
+#define SDD_MAX_MATERIALS 8
+#define SDD_MAX_EVAL 32
+#define SDD_MAX_SHAPES 16
+
+typedef struct sdd_ctx sdd_ctx;
+
+/* Rectangular domain Omega = [x_min, x_max] x [z_min, z_max]. */
+typedef struct {
+    double x_min, x_max, z_min, z_max;
+} sdd_domain;
+
+enum { SDD_SHAPE_RECT = 0, SDD_SHAPE_TRIANGLE = 1 };
+
+/* One material region.  RECT: half-open [v0, v1) x [v2, v3).  TRIANGLE:
+ * closed triangle with vertices (v0, v1), (v2, v3), (v4, v5), either
+ * orientation.  Later shapes override earlier ones and the background. */
+typedef struct {
+    int32_t kind;
+    int32_t material;
+    double v[6];
+} sdd_shape;
+
+/* Dirichlet data g on dOmega.
+ * SDD_G_COLUMNS: the one-dimensional layered TE solution of Sec. 2.1 --
+ *   for a column with earth rate k_c: u = exp(-k z) (z >= 0), u = 1 - k z
+ *   (z < 0, air), k = sqrt(i k_c) with Re k >= 0.  The left wall uses the
+ *   column of material g_left, the right wall that of g_right (rates from
+ *   the evaluation's kappa row), top and bottom interpolate linearly in x
+ *   between the two corner values.
+ * SDD_G_AFFINE: g = a + b x + c z, complex a, b, c in g_coef
+ *   (a_re, a_im, b_re, b_im, c_re, c_im); harmonic, for checks.
+ * SDD_G_X2MZ2: g = x^2 - z^2; harmonic, for checks. */
+enum { SDD_G_COLUMNS = 0, SDD_G_AFFINE = 1, SDD_G_X2MZ2 = 2 };
+
+/* Conductivity model.  Material of a point: if raster != NULL, the cell
+ * (clamp(floor((x - x_min) nx / (x_max - x_min))), same for z) of the int8
+ * raster [nz][nx]; otherwise bg_air (z < 0) or bg_earth (z >= 0) overridden
+ * by the shapes in order.  kappa[e][m] >= 0 is the dimensionless phase rate
+ * of material m in evaluation e. */
+typedef struct {
+    sdd_domain domain;
+    int32_t n_materials;   /* K, 1..SDD_MAX_MATERIALS */
+    int32_t n_eval;        /* E, 1..SDD_MAX_EVAL */
+    const double *kappa;   /* host, [n_eval][n_materials], copied */
+    int32_t bg_air, bg_earth;
+    const sdd_shape *shapes; /* host, copied; may be NULL if n_shapes == 0 */
+    int32_t n_shapes;        /* 0..SDD_MAX_SHAPES */
+    const int8_t *raster;    /* host, [nz][nx] material ids, copied; or NULL */
+    int32_t nx, nz;
+    int32_t g_kind;
+    int32_t g_left, g_right;
+    double g_coef[6];
+} sdd_model_desc;
+
+enum { SDD_FP32 = 0, SDD_FP64 = 1 };
+
+/* Launch options; zero means automatic. */
+typedef struct {
+    int32_t precision;     /* SDD_FP32: single-precision walk, FP64 sums.
+                              SDD_FP64: double-precision walk (parity mode). */
+    int64_t max_steps;     /* per-walk step cap; 0 = ceil(20 / dt) */
+    int32_t block_threads; /* threads per CTA (multiple of 32, <= 512); 0 = auto */
+    int32_t ctas_per_sm;   /* persistent CTAs per SM; 0 = occupancy limit */
+    int32_t chunk_paths;   /* paths per work item; 0 = auto */
+} sdd_config;
+
+typedef struct {
+    uint64_t steps;      /* Euler steps simulated (exiting steps included) */
+    uint64_t walks;      /* walks simulated */
+    uint64_t truncated;  /* walks that reached max_steps */
+    double kernel_ms;    /* device time of the walk kernel (CUDA events) */
+    int32_t launches;    /* kernels launched by the call */
+    int32_t items;       /* work items (node, path chunk) */
+    int32_t grid;        /* CTAs of the persistent walk kernel */
+    int32_t block;       /* threads per CTA */
+} sdd_stats;
+
+/* Create a context on the current CUDA device and copy the model to it.
+ * Errors: SDD_E_ARG (bad sizes, material ids out of range, kappa < 0 or not
+ * finite, empty domain), SDD_E_OOM, SDD_E_CUDA.  *out is NULL on error. */
+sdd_status sdd_create(const sdd_model_desc *model, sdd_ctx **out);
+
+/* Free the context and everything it owns.  NULL is allowed. */
+void sdd_destroy(sdd_ctx *ctx);
+
+/* Interface-node values, host buffers, synchronous (Sec. 3.1 estimator).
+ *   nodes_xz  host, [n_nodes][2] (x, z), each strictly inside the domain
+ *   node_ids  host, [n_nodes] RNG node ids, or NULL for 0..n_nodes-1
+ *   n_paths   host, [n_nodes] walks per node, 1 .. 2^31-1
+ *   dt        Euler time step (standard Brownian clock), > 0
+ *   seed      64-bit Philox4x32-10 key; walk (node id i, path r) uses
+ *             counters (n>>1, r, i, 0) for its normals and (n, r, i, 1) for
+ *             its bridge uniforms, so results do not depend on the launch
+ *   cfg       options, or NULL for defaults
+ *   mean      host out, [n_nodes][n_eval][2] (re, im) sample means
+ *   se        host out, [n_nodes][n_eval][2] standard errors of re and im
+ *             (sqrt of the unbiased sample variance / N)
+ *   stats     host out, nullable
+ * n_nodes == 0 is allowed and does nothing.  The host-to-device copies of
+ * the inputs and the device-to-host copies of the outputs are part of the
+ * call. */
+sdd_status sdd_interface_values(sdd_ctx *ctx, const double *nodes_xz, const uint32_t *node_ids,
+                                int32_t n_nodes, const int64_t *n_paths, double dt,
+                                uint64_t seed, const sdd_config *cfg, double *mean, double *se,
+                                sdd_stats *stats);
+
+/* Same computation on device buffers, queued on `stream` (a cudaStream_t;
+ * NULL = legacy default stream); returns once the work is queued.
+ *   d_nodes_xz  device, [n_nodes][2]
+ *   d_node_ids  device, [n_nodes], or NULL for 0..n_nodes-1
+ *   n_paths     HOST, [n_nodes] (the work-item table is planned on the host)
+ *   d_mean, d_se device outputs, layouts as above
+ *   d_counters  device, 3 x uint64 (steps, walks, truncated) written by the
+ *               call, or NULL
+ * The context's scratch buffers are reused by the next call on the same
+ * context, so calls on one context must be ordered on one stream. */
+sdd_status sdd_interface_values_device(sdd_ctx *ctx, const double *d_nodes_xz,
+                                       const uint32_t *d_node_ids, int32_t n_nodes,
+                                       const int64_t *n_paths, double dt, uint64_t seed,
+                                       const sdd_config *cfg, double *d_mean, double *d_se,
+                                       uint64_t *d_counters, void *stream);
+
+/* Per-path records of walks (node id, paths p0 .. p0+count-1) started at
+ * (x0, z0), host buffers, synchronous -- the individual steps of Sec. 3.1
+ * for comparison path by path:
+ *   steps     [count] Euler steps taken (the exiting step included)
+ *   counts    [count][n_materials] steps whose end point lies in material m
+ *   exit_xzt  [count][3] exit point x, z and hit fraction theta of the last step
+ *   wall      [count] 0 left, 1 right, 2 top, 3 bottom, -1 truncated
+ *   m_last    [count] material of the last point inside (receives theta dt)
+ * Every output pointer may be NULL except steps. */
+sdd_status sdd_walk_records(sdd_ctx *ctx, double x0, double z0, uint32_t node_id, uint32_t p0,
+                            int32_t count, double dt, uint64_t seed, const sdd_config *cfg,
+                            int64_t *steps, int64_t *counts, double *exit_xzt, int32_t *wall,
+                            int32_t *m_last);
+
+/* Number of evaluations and materials of the context's model. */
+int32_t sdd_n_eval(const sdd_ctx *ctx);
+int32_t sdd_n_materials(const sdd_ctx *ctx);
+
+/* Static description of a status; never NULL. */
+const char *sdd_status_str(sdd_status s);
+
+/* Message of the last error raised on this host thread ("" if none). */
+const char *sdd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDD_H */

@@ -1,0 +1,127 @@
+"""Independent closed forms, series and a finite-difference brute force used to
+pin the oracle (and, through it, the CUDA path).  None of this calls the
+oracle or the CUDA library.
+
+- column_u: the 1D layered TE solution used as boundary data (Sec. 2.1).
+- exit_time_series: E[tau] of standard 2D Brownian motion from a rectangle,
+  by separation of variables (1/2 Lap u = -1, u = 0 on the boundary).
+- helmholtz_series: u = E[exp(-i kappa tau / 2)] for uniform kappa and g = 1,
+  i.e. 1/2 Lap u - (i kappa / 2) u = 0, u = 1 on the boundary.
+- fd_solve: 5-point finite differences of Lap u - i kappa(x) u = 0 with the
+  same Dirichlet data, for heterogeneous kappa, on a uniform grid.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+# Largest dt bias of the walk measured on the homogeneous half-space
+# (16 nodes x 1e5 paths, dt from 4e-3 to 2.5e-4): |bias| <= 0.021 sqrt(dt)
+# in the imaginary part, the real part within noise.  Tests allow
+# BIAS_C * sqrt(dt).
+BIAS_C = 0.03
+
+
+def bias_bound(dt: float) -> float:
+    return BIAS_C * np.sqrt(dt)
+
+
+def column_u(kappa: float, z):
+    """1D TE solution with earth rate kappa below z = 0 and air above."""
+    k = np.sqrt(1j * kappa)
+    z = np.asarray(z, dtype=np.float64)
+    return np.where(z >= 0.0, np.exp(-k * z), 1.0 - k * z)
+
+
+def _rect_modes(x, z, domain, mmax):
+    xmin, xmax, zmin, zmax = domain
+    W, H = xmax - xmin, zmax - zmin
+    X, Z = x - xmin, z - zmin
+    m = np.arange(1, mmax + 1, 2)
+    M, N = np.meshgrid(m, m, indexing="ij")
+    lam = 0.5 * np.pi ** 2 * ((M / W) ** 2 + (N / H) ** 2)
+    phi = np.sin(M * np.pi * X / W) * np.sin(N * np.pi * Z / H)
+    coef = 16.0 / (np.pi ** 2 * M * N)
+    return lam, phi, coef
+
+
+def exit_time_series(x, z, domain, mmax=801):
+    lam, phi, coef = _rect_modes(x, z, domain, mmax)
+    return float(np.sum(coef / lam * phi))
+
+
+def helmholtz_series(x, z, kappa, domain, mmax=801):
+    lam, phi, coef = _rect_modes(x, z, domain, mmax)
+    a = 0.5j * kappa
+    return complex(1.0 - np.sum(coef * a / (lam + a) * phi))
+
+
+def g_columns(x, z, domain, kl, kr, wall):
+    """Boundary data of the 'columns' kind: sides from the 1D solution of their
+    column, top/bottom linear in x between the corners."""
+    xmin, xmax, zmin, zmax = domain
+    if wall == "left":
+        return column_u(kl, z)
+    if wall == "right":
+        return column_u(kr, z)
+    t = (x - xmin) / (xmax - xmin)
+    return (1 - t) * column_u(kl, z) + t * column_u(kr, z)
+
+
+def fd_solve(kappa_fn, domain, h, kl, kr):
+    """Solve Lap u - i kappa u = 0 on a uniform grid of spacing h with the
+    'columns' boundary data.  kappa_fn(X, Z) gives kappa at grid nodes.
+    Returns (xs, zs, U) with U[iz, ix] on the full grid including walls."""
+    xmin, xmax, zmin, zmax = domain
+    nx = int(round((xmax - xmin) / h))
+    nz = int(round((zmax - zmin) / h))
+    xs = xmin + h * np.arange(nx + 1)
+    zs = zmin + h * np.arange(nz + 1)
+    X, Z = np.meshgrid(xs, zs)
+    U = np.zeros((nz + 1, nx + 1), dtype=np.complex128)
+    U[:, 0] = g_columns(xs[0], zs, domain, kl, kr, "left")
+    U[:, -1] = g_columns(xs[-1], zs, domain, kl, kr, "right")
+    U[0, :] = g_columns(xs, zs[0], domain, kl, kr, "top")
+    U[-1, :] = g_columns(xs, zs[-1], domain, kl, kr, "bottom")
+    ni, nk = nx - 1, nz - 1
+    idx = np.arange(ni * nk).reshape(nk, ni)
+    kap = kappa_fn(X[1:-1, 1:-1], Z[1:-1, 1:-1])
+    inv = 1.0 / h ** 2
+    rows, cols, vals = [idx.ravel()], [idx.ravel()], [(-4.0 * inv - 1j * kap).ravel()]
+    rhs = np.zeros(ni * nk, dtype=np.complex128)
+    KZ, KX = np.meshgrid(np.arange(nk), np.arange(ni), indexing="ij")
+    for dz, dx in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+        JZ, JX = KZ + dz, KX + dx
+        inside = (JZ >= 0) & (JZ < nk) & (JX >= 0) & (JX < ni)
+        rows.append(idx[inside])
+        cols.append(idx[JZ[inside], JX[inside]])
+        vals.append(np.full(int(inside.sum()), inv, dtype=np.complex128))
+        out = ~inside
+        # neighbour on the wall: full-grid index is interior index + 1
+        np.subtract.at(rhs, idx[out], inv * U[JZ[out] + 1, JX[out] + 1])
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(ni * nk, ni * nk))
+    sol = spla.spsolve(A.tocsc(), rhs)
+    U[1:-1, 1:-1] = sol.reshape(nk, ni)
+    return xs, zs, U
+
+
+def fd_value(kappa_fn, domain, h, kl, kr, pts):
+    xs, zs, U = fd_solve(kappa_fn, domain, h, kl, kr)
+    out = []
+    for x, z in pts:
+        ix = int(round((x - xs[0]) / h))
+        iz = int(round((z - zs[0]) / h))
+        assert abs(xs[ix] - x) < 1e-12 and abs(zs[iz] - z) < 1e-12, "point not on the grid"
+        out.append(U[iz, ix])
+    return np.array(out)
+
+
+def fd_richardson(kappa_fn, domain, kl, kr, pts, h=1 / 40):
+    """Second-order Richardson extrapolation of h and h/2 solutions; returns
+    (value, error estimate)."""
+    a = fd_value(kappa_fn, domain, h, kl, kr, pts)
+    b = fd_value(kappa_fn, domain, h / 2, kl, kr, pts)
+    ext = (4 * b - a) / 3
+    return ext, np.abs(b - a) / 3

@@ -1,0 +1,301 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Every check here is independent of the oracle's own code: published
+known-answer vectors, closed forms, series solutions, a finite-difference
+brute force, textbook probabilities and exact special cases.  Tolerances for
+Monte Carlo results are 4 standard errors plus the measured time-step bias
+(pins.bias_bound) plus, for FD, its Richardson error estimate.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import pins
+from oracle import oracle as O
+from paper_1603_09311_gb300 import inputs as I
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+DOM = I.DOMAIN
+
+
+def _kat():
+    rows = []
+    with open(os.path.join(HERE, "golden", "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            w = [int(t, 16) for t in line.split()]
+            rows.append((w[0:4], w[4:6], w[6:10]))
+    return rows
+
+
+@pytest.mark.parametrize("ctr,key,want", _kat())
+def test_philox_known_answers(ctr, key, want):
+    assert list(O.philox4x32_10(ctr, key)) == want
+
+
+def test_uniform_rules_open_interval():
+    # (w + 1/2) 2^-32 and (floor(w/2^9) + 1/2) 2^-23: never 0 or 1
+    assert O.uniform(0, 32) == 2.0 ** -33
+    assert O.uniform(0xFFFFFFFF, 32) == 1.0 - 2.0 ** -33
+    assert O.uniform(0, 23) == 2.0 ** -24
+    assert O.uniform(0xFFFFFFFF, 23) == 1.0 - 2.0 ** -24
+    assert O.uniform(511, 23) == 2.0 ** -24 and O.uniform(512, 23) == 3 * 2.0 ** -24
+
+
+@pytest.mark.parametrize("urule", [32, 23])
+def test_box_muller_normals_are_standard(urule):
+    # Sec. 3.1 draws W ~ N(0, I2); check the first four moments and a KS test
+    vals = np.array([O.normals(7, node, path, n, urule)
+                     for node in range(2) for path in range(50) for n in range(200)])
+    n = len(vals)
+    a, b = vals[:, 0], vals[:, 1]
+    for v in (a, b):
+        assert abs(v.mean()) < 5 / math.sqrt(n)
+        assert abs(v.var() - 1) < 5 * math.sqrt(2 / n)
+        assert abs(np.mean(v ** 4) - 3) < 5 * math.sqrt(96 / n)
+        assert stats.kstest(v, "norm").pvalue > 1e-4
+    assert abs(np.mean(a * b)) < 5 / math.sqrt(n)
+    # consecutive steps of one walk use different words of the same Philox call
+    w_even = O.normals(1, 0, 0, 0, urule)
+    w_odd = O.normals(1, 0, 0, 1, urule)
+    assert w_even != w_odd
+
+
+def test_bridge_uniform_stream_is_uniform():
+    u = np.array([O.bridge_uniform(3, 0, p, n) for p in range(40) for n in range(250)])
+    assert stats.kstest(u, "uniform").pvalue > 1e-4
+
+
+def test_material_rules():
+    m = {"domain": DOM, "kappa": [[0, 1, 2, 3]], "bg": (0, 1),
+         "shapes": [(0, 2, (-0.2, 0.2, 0.2, 0.5, 0, 0)), (1, 3, (-0.3, 0.6, 0.3, 0.6, 0.0, 0.7))]}
+    assert O.material(m, 0.0, -0.1) == 0          # air z < 0
+    assert O.material(m, 0.0, 0.0) == 1           # earth z >= 0
+    assert O.material(m, -0.2, 0.2) == 2          # rectangle half-open: lower corner in
+    assert O.material(m, 0.2, 0.3) == 1           # right edge out
+    assert O.material(m, 0.0, 0.5) == 1           # bottom edge out
+    assert O.material(m, 0.0, 0.6) == 3           # triangle edge in (closed)
+    assert O.material(m, 0.3, 0.6) == 3           # triangle vertex in
+    assert O.material(m, 0.0, 0.7) == 3           # apex
+    assert O.material(m, 0.0, 0.71) == 1
+    # raster: cell index floor((x - xmin) nx / W), clamped
+    r = np.arange(12, dtype=np.int8).reshape(3, 4) % 4
+    mr = {"domain": (0.0, 4.0, 0.0, 3.0), "kappa": [[0, 1, 2, 3]], "raster": r}
+    assert O.material(mr, 0.5, 0.5) == r[0, 0]
+    assert O.material(mr, 3.999, 2.999) == r[2, 3]
+    assert O.material(mr, 1.0, 2.0) == r[2, 1]
+    assert O.material(mr, -5.0, 10.0) == r[2, 0]
+
+
+def test_g_columns_solves_the_1d_te_equation():
+    # u'' = i kappa u for z > 0, u'' = 0 in air, u and u' continuous at 0,
+    # u(0) = 1 (the 1D half-space boundary data of Sec. 2.1)
+    m = I.quarterspace(2.0, 20.0)
+    for wall, kap in ((0, 2.0), (1, 20.0)):
+        x = -1.0 if wall == 0 else 1.0
+        f = lambda z: O.g_value(m, 0, wall, x, z)
+        h = 1e-4
+        for z in (0.1, 0.4, 0.9):
+            d2 = (f(z + h) - 2 * f(z) + f(z - h)) / h ** 2
+            assert abs(d2 - 1j * kap * f(z)) < 1e-4 * max(1.0, abs(kap * f(z)))
+        for z in (-0.3, -0.1):
+            assert abs((f(z + h) - 2 * f(z) + f(z - h)) / h ** 2) < 1e-3
+        assert abs(f(0.0) - 1.0) < 1e-15
+        dp = (f(h) - f(0.0)) / h
+        dm = (f(0.0) - f(-h)) / h
+        assert abs(dp - dm) < 1e-3 * abs(dm)
+        assert abs(dm + np.sqrt(1j * kap)) < 1e-12 * abs(dm)
+    # half-space kappa = 2: k = 1 + i, top wall z = -0.5 gives 1 + 0.5 k
+    hs = I.halfspace(2.0)
+    assert abs(O.g_value(hs, 0, 2, 0.3, -0.5) - (1.5 + 0.5j)) < 1e-15
+    assert abs(O.g_value(hs, 0, 3, -0.7, 1.0) - np.exp(-(1 + 1j))) < 1e-15
+    # top/bottom interpolate linearly between the column corner values
+    q = I.quarterspace(2.0, 20.0)
+    gl, gr = O.g_value(q, 0, 0, -1.0, 1.0), O.g_value(q, 0, 1, 1.0, 1.0)
+    assert abs(O.g_value(q, 0, 3, 0.5, 1.0) - (0.25 * gl + 0.75 * gr)) < 1e-15
+
+
+def test_exit_rule_overshoot_cases():
+    m = I.halfspace(2.0)
+    # right wall: d = 0.1, d' = -0.1 -> theta = d / (d + |d'|) = 0.5
+    hit, th, w, ex, ez = O.exit_rule(m, 0.9, 0.3, 1.1, 0.5, 1e-3, 0.5)
+    assert hit and w == 1 and abs(th - 0.5) < 1e-14 and ex == 1.0 and abs(ez - 0.4) < 1e-14
+    # exactly on the wall counts as reached: theta = 1
+    hit, th, w, ex, ez = O.exit_rule(m, 0.9, 0.3, 1.0, 0.3, 1e-3, 0.5)
+    assert hit and w == 1 and th == 1.0
+    # two walls crossed: the smaller theta wins (top wall first here)
+    hit, th, w, ex, ez = O.exit_rule(m, -0.95, -0.45, -1.05, -0.65, 1e-3, 0.5)
+    assert hit and w == 2 and abs(th - 0.25) < 1e-14 and ez == -0.5
+    # a tie goes to the first wall in the order left, right, top, bottom
+    hit, th, w, ex, ez = O.exit_rule(m, -0.875, -0.375, -1.125, -0.625, 1e-3, 0.5)
+    assert hit and w == 0 and th == 0.5 and ex == -1.0 and ez == -0.5
+
+
+def test_exit_rule_bridge_matches_brownian_bridge_crossing_probability():
+    # P(a Brownian bridge from distance d to d' over time dt touches the wall)
+    # = exp(-2 d d' / dt) (textbook reflection principle); the rule draws one
+    # uniform U and hits iff 2 d d'/dt <= -log U.
+    m = I.halfspace(2.0)
+    dt, d, dn = 1e-3, 0.01, 0.02
+    p_exact = math.exp(-2 * d * dn / dt)
+    M = 20000
+    hits = 0
+    for k in range(M):
+        U = (k + 0.5) / M
+        hit, th, w, ex, ez = O.exit_rule(m, 0.3, 1.0 - d, 0.31, 1.0 - dn, dt, U)
+        if hit:
+            hits += 1
+            assert w == 3 and ez == 1.0 and 0 < th <= 1
+            assert abs(th - (2 * d * dn / dt) / (-math.log(U))) < 1e-14
+    assert abs(hits / M - p_exact) <= 1.0 / M
+    # far from every wall the bridge never fires
+    assert not O.exit_rule(m, 0.0, 0.3, 0.01, 0.31, dt, 1e-300)[0]
+
+
+def test_unit_data_without_phase_is_exactly_one():
+    # kappa = 0 and g = 1: every sample is exactly 1, the mean is exactly 1
+    m = I.uniform_model(0.0, g=("affine", 1.0, 0.0, 0.0))
+    nodes = [(0.0, 0.25), (0.9, 0.9), (-0.99, -0.49)]
+    r = O.interface_values(m, nodes, 3000, 1e-3, 5)
+    assert np.all(r["mean"] == 1.0)
+    assert np.all(r["se"] == 0.0)
+    assert r["truncated"] == 0 and r["walks"] == 9000
+
+
+def test_halfspace_matches_closed_form():
+    # homogeneous half-space, kappa = 2: u = exp(-(1+i) z) everywhere
+    w = I.workload("halfspace")
+    r = O.interface_values(w["model"], w["nodes"], w["n_paths"], w["dt"], w["seed"])
+    exact = np.exp(-(1 + 1j) * 0.25)
+    tol_b = pins.bias_bound(w["dt"])
+    dev = r["mean"][:, 0] - exact
+    se = r["se"][:, 0, :]
+    assert np.all(np.abs(dev.real) <= 4 * se[:, 0] + tol_b)
+    assert np.all(np.abs(dev.imag) <= 4 * se[:, 1] + tol_b)
+    pooled = dev.mean()
+    pse = np.sqrt((se ** 2).sum(0)) / len(dev)
+    assert abs(pooled.real) <= 4 * pse[0] + tol_b
+    assert abs(pooled.imag) <= 4 * pse[1] + tol_b
+
+
+@pytest.mark.parametrize("x,z", [(0.0, 0.25), (0.5, 0.25), (0.0, 0.9)])
+def test_mean_exit_time_matches_series(x, z):
+    dt = 1e-3
+    rec = O.walk_records(I.halfspace(2.0), (x, z), 0, 0, 20000, dt, 9)
+    tau = ((rec["steps"] - 1) + rec["exit"][:, 2]) * dt
+    se = tau.std(ddof=1) / math.sqrt(len(tau))
+    assert abs(tau.mean() - pins.exit_time_series(x, z, DOM)) <= 4 * se + 2 * dt
+
+
+@pytest.mark.parametrize("x,z", [(0.0, 0.25), (0.5, 0.6)])
+def test_uniform_kappa_matches_helmholtz_series(x, z):
+    kap, dt = 10.0, 1e-3
+    r = O.interface_values(I.uniform_model(kap), [(x, z)], 40000, dt, 21)
+    exact = pins.helmholtz_series(x, z, kap, DOM)
+    dev = r["mean"][0, 0] - exact
+    se = r["se"][0, 0]
+    assert abs(dev.real) <= 4 * se[0] + pins.bias_bound(dt)
+    assert abs(dev.imag) <= 4 * se[1] + pins.bias_bound(dt)
+
+
+def test_harmonic_affine_data_reproduces_itself():
+    # kappa = 0, g harmonic: u = g(x0) (optional stopping of a martingale)
+    a, b, c = 0.3 + 0.1j, 1.0 - 0.5j, -0.7 + 0.2j
+    m = I.uniform_model(0.0, g=("affine", a, b, c))
+    nodes = [(0.0, 0.25), (0.6, 0.7), (-0.8, -0.3)]
+    dt = 1e-3
+    r = O.interface_values(m, nodes, 40000, dt, 8)
+    for (x, z), mu, se in zip(nodes, r["mean"][:, 0], r["se"][:, 0, :]):
+        g0 = a + b * x + c * z
+        assert abs((mu - g0).real) <= 4 * se[0] + pins.bias_bound(dt)
+        assert abs((mu - g0).imag) <= 4 * se[1] + pins.bias_bound(dt)
+    m2 = I.uniform_model(0.0, g=("x2mz2",))
+    r2 = O.interface_values(m2, nodes, 40000, dt, 8)
+    for (x, z), mu, se in zip(nodes, r2["mean"][:, 0], r2["se"][:, 0, :]):
+        assert abs(mu.real - (x * x - z * z)) <= 4 * se[0] + pins.bias_bound(dt)
+        assert mu.imag == 0.0
+
+
+def _kappa_quarter(X, Z):
+    k = np.where(X < 0, 2.0, 20.0)
+    k = np.where(X == 0, 11.0, k)
+    k = np.where(Z < 0, 0.0, k)
+    return np.where(Z == 0, k / 2, k)
+
+
+@pytest.mark.slow
+def test_quarterspace_matches_finite_differences():
+    pts = [(0.0, 0.25), (-0.25, 0.5), (0.25, 0.5)]
+    fd, fd_err = pins.fd_richardson(_kappa_quarter, DOM, 2.0, 20.0, pts)
+    dt = 1e-3
+    r = O.interface_values(I.quarterspace(2.0, 20.0), pts, 100000, dt, 13)
+    for mu, se, ref, err in zip(r["mean"][:, 0], r["se"][:, 0, :], fd, fd_err):
+        assert abs((mu - ref).real) <= 4 * se[0] + pins.bias_bound(dt) + err
+        assert abs((mu - ref).imag) <= 4 * se[1] + pins.bias_bound(dt) + err
+
+
+def test_block_model_is_symmetric_in_x():
+    m = I.block_batched(scales=[1.0, 10.0])
+    pts = [(-0.2, 0.35), (0.15, 0.55)]
+    mir = [(-x, z) for x, z in pts]
+    a = O.interface_values(m, pts, 20000, 1e-3, 1)
+    b = O.interface_values(m, mir, 20000, 1e-3, 2)
+    d = a["mean"] - b["mean"]
+    s = np.sqrt(a["se"] ** 2 + b["se"] ** 2)
+    assert np.all(np.abs(d.real) <= 4 * s[..., 0] + 1e-12)
+    assert np.all(np.abs(d.imag) <= 4 * s[..., 1] + 1e-12)
+
+
+def test_raster_model_agrees_with_its_analytic_shapes():
+    m = I.triangle()
+    mr = dict(m)
+    mr["raster"] = I.rasterize(m)
+    mr["shapes"] = []
+    pts = [(0.0, 0.3), (0.1, 0.62)]
+    a = O.interface_values(m, pts, 20000, 1e-3, 4)
+    b = O.interface_values(mr, pts, 20000, 1e-3, 4)
+    s = np.sqrt(a["se"] ** 2 + b["se"] ** 2)
+    d = a["mean"] - b["mean"]
+    assert np.all(np.abs(d.real) <= 4 * s[..., 0] + 2e-3)
+    assert np.all(np.abs(d.imag) <= 4 * s[..., 1] + 2e-3)
+
+
+def test_sums_do_not_depend_on_thread_count():
+    w = I.scaled(I.workload("quarterspace"), paths_per_node=3000, n_nodes=4, dt=1e-3)
+    a = O.interface_values(w["model"], w["nodes"], w["n_paths"], w["dt"], 0, threads=1)
+    b = O.interface_values(w["model"], w["nodes"], w["n_paths"], w["dt"], 0, threads=3)
+    assert np.array_equal(a["mean"], b["mean"]) and np.array_equal(a["se"], b["se"])
+
+
+def test_truncated_walks_are_counted_and_excluded():
+    m = I.halfspace(2.0)
+    r = O.interface_values(m, [(0.0, 0.25)], 2000, 1e-3, 0, max_steps=300)
+    rec = O.walk_records(m, (0.0, 0.25), 0, 0, 2000, 1e-3, 0, max_steps=300)
+    assert r["truncated"] == int(rec["truncated"].sum()) > 0
+    assert np.all(rec["steps"][rec["truncated"] == 1] == 300)
+    assert r["walks"] == 2000
+    # a walk's occupation counts add up to its non-exiting steps
+    ok = rec["truncated"] == 0
+    assert np.all(rec["counts"][ok].sum(1) == rec["steps"][ok] - 1)
+    assert np.all(rec["counts"][~ok].sum(1) == rec["steps"][~ok])
+
+
+def test_each_evaluation_row_uses_its_own_rates():
+    # three evaluations sharing one walk, each a uniform medium of its own
+    # rate (air and earth rates equal): every row must match the Helmholtz
+    # series of its own kappa, so a transposed [E][K] table fails
+    rows = [[1.0, 1.0], [5.0, 5.0], [20.0, 20.0]]
+    m = {"domain": DOM, "kappa": rows, "bg": (0, 1), "shapes": [], "g": ("affine", 1.0, 0.0, 0.0)}
+    dt = 1e-3
+    x, z = 0.2, 0.4
+    r = O.interface_values(m, [(x, z)], 40000, dt, 17)
+    for e, (kap, _) in enumerate(rows):
+        ref = pins.helmholtz_series(x, z, kap, DOM)
+        dev = r["mean"][0, e] - ref
+        se = r["se"][0, e]
+        assert abs(dev.real) <= 4 * se[0] + pins.bias_bound(dt)
+        assert abs(dev.imag) <= 4 * se[1] + pins.bias_bound(dt)
