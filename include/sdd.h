@@ -118,7 +118,7 @@ typedef struct {
     int32_t precision;     /* SDD_FP32: single-precision walk, FP64 sums.
                               SDD_FP64: double-precision walk (parity mode). */
     int64_t max_steps;     /* per-walk step cap; 0 = ceil(20 / dt) */
-    int32_t block_threads; /* threads per CTA (multiple of 32, <= 512); 0 = auto */
+    int32_t block_threads; /* threads per CTA (multiple of 32, <= 256); 0 = auto */
     int32_t ctas_per_sm;   /* persistent CTAs per SM; 0 = occupancy limit */
     int32_t chunk_paths;   /* paths per work item; 0 = auto */
 } sdd_config;

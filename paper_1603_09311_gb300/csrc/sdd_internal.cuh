@@ -1,0 +1,106 @@
+// Internal device-side definitions of libsdd (not part of the C ABI).
+//
+// Shared by the host API (sdd_api.cu) and the two walk translation units
+// (walk_f32.cu: single-precision walk; walk_f64.cu: double-precision parity
+// walk compiled without FMA contraction).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sdd {
+
+constexpr int kMaxK = 8;
+constexpr int kMaxE = 32;
+constexpr int kMaxShapes = 16;
+constexpr int kRing = 64;  // exit records buffered per warp
+
+enum Geo : int { GEO_SHAPES = 0, GEO_RASTER = 1 };
+
+// One work item: paths [path0, path0 + count) of node `node`.
+struct Item {
+    int32_t node;
+    uint32_t path0;
+    int32_t count;
+    int32_t pad;
+};
+
+// A material shape.  f: single-precision copy in domain-centred coordinates
+// (rectangle bounds, or the three edge lines A X + B Z + C >= 0 of a
+// triangle, orientation folded in).  d: double-precision absolute copy
+// (rectangle bounds or the vertices), evaluated exactly as the definition.
+struct ShapeDev {
+    int32_t kind, mat;
+    float f[9];
+    double d[6];
+    double dsign;  // orientation sign of a triangle
+};
+
+// Per-evaluation constants of the boundary data (SDD_G_COLUMNS): the column
+// wavenumbers k = sqrt(i kappa) of the left and right columns and the four
+// corner values used by the top/bottom interpolation.
+struct EvalDev {
+    double kl_re, kl_im, kr_re, kr_im;
+    double tl_re, tl_im, tr_re, tr_im;  // top-left, top-right corners
+    double bl_re, bl_im, br_re, br_im;  // bottom-left, bottom-right corners
+};
+
+struct ModelDev {
+    double xmin, xmax, zmin, zmax;
+    double xc, zc, hw, hh;  // centre and half sizes
+    int32_t K, E, Epad;
+    int32_t bg_air, bg_earth;
+    int32_t n_shapes;
+    ShapeDev shapes[kMaxShapes];
+    const int8_t *raster;
+    int32_t nx, nz;
+    double sx, sz;  // nx / (xmax - xmin), nz / (zmax - zmin)
+    int32_t g_kind;
+    double g_coef[6];
+    double kappa[kMaxE * kMaxK];  // [E][K]
+    EvalDev ev[kMaxE];
+    // single-precision constants of the centred walk (X = x - xc, Z = z - zc)
+    float fhw, fhh;  // half width / height
+    float fxc, fzc;  // centre
+    float fzs;       // earth surface z = 0 in centred coordinates
+    float fsx, fsz;  // raster cells per unit length
+    float fox, foz;  // hw * sx - 1/2, hh * sz - 1/2 (cell index = round(X sx + ox))
+};
+
+struct WalkArgs {
+    const Item *items;
+    int32_t n_items;
+    const double *nodes;       // [n][2] absolute
+    const uint32_t *node_ids;  // nullable
+    double dt;
+    double sdt;                // sqrt(dt)
+    float f_cdt;               // -2 ln(2) dt: squared step radius = f_cdt * log2(u0)
+    float f_c2dt;              // 2 / dt
+    float f_bthr;              // bridge filter: d d' above this cannot hit
+    uint32_t key0, key1;       // Philox key (seed)
+    uint32_t max_steps;
+    double *slots;             // [n_items][E][4]: sum re, sum im, sum re^2, sum im^2
+    int32_t *item_trunc;       // [n_items] truncated walks
+    unsigned long long *counters;  // steps, walks, truncated
+    int32_t *queue;            // next item (zero before launch)
+    int32_t *error;            // nonzero if a device-side check failed
+    // per-path dump (sdd_walk_records); when rec_steps != nullptr the walk
+    // records are written here instead of being summed
+    int64_t *rec_steps;
+    int64_t *rec_counts;       // [count][K]
+    double *rec_exit;          // [count][3]
+    int32_t *rec_wall;
+    int32_t *rec_mlast;
+};
+
+// Launchers (one per precision translation unit).
+cudaError_t launch_walk_f32(int kmax, int geo, const ModelDev &M, const WalkArgs &A, int grid,
+                            int block, cudaStream_t s);
+cudaError_t launch_walk_f64(int kmax, int geo, const ModelDev &M, const WalkArgs &A, int grid,
+                            int block, cudaStream_t s);
+// Largest number of resident CTAs per SM for a configuration.
+int occupancy_f32(int kmax, int geo, int block);
+int occupancy_f64(int kmax, int geo, int block);
+size_t smem_bytes(bool f64, int kmax, int block);
+
+}  // namespace sdd

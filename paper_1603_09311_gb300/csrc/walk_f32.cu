@@ -1,0 +1,287 @@
+// Single-precision walk (the throughput path).
+//
+// Position stepping, wall tests, material lookup and the per-walk phase
+// factor are FP32; the per-material step counts are integers; the phase sum
+// and the Monte Carlo sums are FP64.  Compiled with -ftz=true
+// -prec-div=false -prec-sqrt=false.
+//
+// One Euler-Maruyama step of Sec. 3.1 (discretised process, kappa_i = 1):
+//   (u0, u1)  two uniforms ((w >> 9) + 1/2) 2^-23 from one Philox call,
+//   r^2 = -2 ln(u0) dt,  beta' = beta + r (cos 2 pi u1, sin 2 pi u1),
+// then the boundary rule of the first-exit-time estimate: overshoot ->
+// theta = d / (d + |d'|) on the first wall reached; else the Brownian-bridge
+// test 2 d d' / dt <= -ln U_gamma with one uniform per step; else the step's
+// time goes to the material of beta' (Sec. 3.1, no regime change for TE).
+//
+// The walk runs in centred coordinates X = x - xc, Z = z - zc, so the
+// distance to the nearer wall of each pair is h - |X|.  Two steps share one
+// Philox call (words 0,1 for the even step, 2,3 for the odd one).
+#include "walk_sched.cuh"
+
+namespace sdd {
+
+// u = (floor(w / 2^9) + 1/2) 2^-23, exact: 1.m - (1 - 2^-24) by Sterbenz.
+__device__ __forceinline__ float uni23(uint32_t w) {
+    return __uint_as_float(0x3f800000u | (w >> 9)) - 0.99999994039535522f;
+}
+
+template <int KMAX_, int GEO>
+struct WalkerF32 {
+    using Real = float;
+    static constexpr int KMAX = KMAX_;
+
+    float X, Z, dmin;
+    uint32_t n;
+    uint32_t cnt[KMAX > 1 ? KMAX - 1 : 1];
+    int mcur;
+    uint32_t nid, pre_x, pre_y;
+
+    __device__ __forceinline__ static int material(const ModelDev &M, float X, float Z) {
+        if (GEO == GEO_RASTER) {
+            int ix = __float_as_int(fmaf(X, M.fsx, M.fox) + 12582912.0f) - 0x4B400000;
+            int iz = __float_as_int(fmaf(Z, M.fsz, M.foz) + 12582912.0f) - 0x4B400000;
+            ix = min(max(ix, 0), M.nx - 1);
+            iz = min(max(iz, 0), M.nz - 1);
+            return (int)__ldg(M.raster + iz * M.nx + ix);
+        } else {
+            int m = (Z >= M.fzs) ? M.bg_earth : M.bg_air;
+            for (int s = 0; s < M.n_shapes; ++s) {
+                const ShapeDev &S = M.shapes[s];
+                bool in;
+                if (S.kind == 0) {
+                    in = X >= S.f[0] && X < S.f[1] && Z >= S.f[2] && Z < S.f[3];
+                } else {
+                    in = fmaf(S.f[0], X, fmaf(S.f[1], Z, S.f[2])) >= 0.f &&
+                         fmaf(S.f[3], X, fmaf(S.f[4], Z, S.f[5])) >= 0.f &&
+                         fmaf(S.f[6], X, fmaf(S.f[7], Z, S.f[8])) >= 0.f;
+                }
+                if (in) m = S.mat;
+            }
+            return m;
+        }
+    }
+
+    __device__ __forceinline__ void count(int m) {
+        if (KMAX == 2) {
+            cnt[0] += (uint32_t)m;
+        } else {
+#pragma unroll
+            for (int j = 1; j < KMAX; ++j) cnt[j - 1] += (m == j) ? 1u : 0u;
+        }
+    }
+
+    __device__ __forceinline__ void start(const ModelDev &M, const WalkArgs &A, double x0,
+                                          double z0, uint32_t path, uint32_t node_id) {
+        X = (float)(x0 - M.xc);
+        Z = (float)(z0 - M.zc);
+        dmin = fminf(M.fhw - fabsf(X), M.fhh - fabsf(Z));
+        n = 0;
+#pragma unroll
+        for (int j = 0; j < (KMAX > 1 ? KMAX - 1 : 1); ++j) cnt[j] = 0;
+        mcur = material(M, X, Z);
+        nid = node_id;
+        pre_x = __umulhi(0xCD9E8D57u, node_id) ^ path ^ A.key0;
+        pre_y = 0xCD9E8D57u * node_id;
+    }
+
+    // Exit on overshoot: theta_w = d_w / (d_w - d'_w) over the walls with
+    // d'_w <= 0, smallest first, ties to the first in left, right, top, bottom.
+    __device__ __forceinline__ void overshoot(const ModelDev &M, float Xn, float Zn,
+                                              ExitInfo<float> &ei) const {
+        const float d[4] = {X + M.fhw, M.fhw - X, Z + M.fhh, M.fhh - Z};
+        const float e[4] = {Xn + M.fhw, M.fhw - Xn, Zn + M.fhh, M.fhh - Zn};
+        float best = 2.0f;
+        int bw = 0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            if (e[w] <= 0.f) {
+                const float t = d[w] / (d[w] - e[w]);
+                if (t < best) { best = t; bw = w; }
+            }
+        }
+        place(M, Xn, Zn, best, bw, ei);
+    }
+
+    __device__ __forceinline__ void place(const ModelDev &M, float Xn, float Zn, float th, int w,
+                                          ExitInfo<float> &ei) const {
+        ei.th = th;
+        ei.wall = w;
+        ei.x = fmaf(th, Xn - X, X);
+        ei.z = fmaf(th, Zn - Z, Z);
+        if (w == 0) ei.x = -M.fhw;
+        if (w == 1) ei.x = M.fhw;
+        if (w == 2) ei.z = -M.fhh;
+        if (w == 3) ei.z = M.fhh;
+    }
+
+    // Brownian-bridge test with one uniform for all walls: the walk touched
+    // wall w during the step iff 2 d_w d'_w / dt <= -ln U (smallest product).
+    __device__ __forceinline__ bool bridge(const ModelDev &M, const WalkArgs &A, uint32_t path,
+                                        float Xn, float Zn, ExitInfo<float> &ei) const {
+        const float d[4] = {X + M.fhw, M.fhw - X, Z + M.fhh, M.fhh - Z};
+        const float e[4] = {Xn + M.fhw, M.fhw - Xn, Zn + M.fhh, M.fhh - Zn};
+        float best = d[0] * e[0];
+        int bw = 0;
+#pragma unroll
+        for (int w = 1; w < 4; ++w) {
+            const float p = d[w] * e[w];
+            if (p < best) { best = p; bw = w; }
+        }
+        const float es = best * A.f_c2dt;
+        const uint4 b = philox4x32_10(make_uint4(n, path, nid, 1u), A.key0, A.key1);
+        const float L = -logf(uni23(b.x));
+        if (es <= L) {
+            place(M, Xn, Zn, es / L, bw, ei);
+            return true;
+        }
+        return false;
+    }
+
+    __device__ __forceinline__ int substep(const ModelDev &M, const WalkArgs &A, uint32_t path,
+                                           uint32_t wa, uint32_t wb, ExitInfo<float> &ei) {
+        const float u0 = uni23(wa), u1 = uni23(wb);
+        const float r = sqrtf(fmaxf(A.f_cdt * __log2f(u0), 0.f));
+        float sn, cs;
+        __sincosf(fmaf(u1, 6.28318530718f, -3.14159265359f), &sn, &cs);
+        // cos(2 pi u1) = -cs, sin(2 pi u1) = -sn
+        const float Xn = fmaf(-r, cs, X);
+        const float Zn = fmaf(-r, sn, Z);
+        const float dn = fminf(M.fhw - fabsf(Xn), M.fhh - fabsf(Zn));
+        if (dn <= 0.f) {
+            overshoot(M, Xn, Zn, ei);
+            return 1;
+        }
+        if (dmin * dn <= A.f_bthr) {
+            if (bridge(M, A, path, Xn, Zn, ei)) return 1;
+        }
+        const int m = material(M, Xn, Zn);
+        count(m);
+        X = Xn;
+        Z = Zn;
+        dmin = dn;
+        mcur = m;
+        ++n;
+        if (n >= A.max_steps) {
+            ei.x = X; ei.z = Z; ei.th = 0.f; ei.wall = 0;
+            return 2;
+        }
+        return 0;
+    }
+
+    __device__ __forceinline__ int iterate(const ModelDev &M, const WalkArgs &A, uint32_t path,
+                                           ExitInfo<float> &ei) {
+        const uint4 w = philox4x32_10_pre(n >> 1, 0u, pre_x, pre_y, A.key0, A.key1);
+        const int r = substep(M, A, path, w.x, w.y, ei);
+        if (r) return r;
+        return substep(M, A, path, w.z, w.w, ei);
+    }
+
+    __device__ static void to_abs(const ModelDev &M, float X, float Z, double &x, double &z) {
+        x = (double)X + M.xc;
+        z = (double)Z + M.zc;
+    }
+
+    // 1D column solution at depth z: exp(-k z) in the earth, 1 - k z in air.
+    __device__ static void column(float kr, float ki, float z, float &gr, float &gi) {
+        if (z >= 0.f) {
+            const float a = expf(-kr * z);
+            float s, c;
+            sincosf(ki * z, &s, &c);
+            gr = a * c;
+            gi = -a * s;
+        } else {
+            gr = fmaf(-kr, z, 1.f);
+            gi = -ki * z;
+        }
+    }
+
+    // Sample of one walk for evaluation e: g(exit) exp(-i (1/2) sum_m kappa_{e,m} T_m).
+    __device__ static double2 sample(const ModelDev &M, const SharedTables &T, int e, float X,
+                                     float Z, float th, int wall, int mlast, const uint32_t *c,
+                                     double dt) {
+        const double *kap = T.kappa + e * M.K;
+        double ph = 0.0;
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < M.K) ph = fma(kap[k], (double)c[k], ph);
+        ph = fma(kap[mlast], (double)th, ph);
+        ph *= 0.5 * dt;
+        const double q = rint(ph * 0.15915494309189535);
+        const float pr = (float)fma(-q, 6.283185307179586, ph);
+        float sw, cw;
+        sincosf(pr, &sw, &cw);
+        float gr, gi;
+        const float x = X + M.fxc, z = Z + M.fzc;
+        if (M.g_kind == 1) {
+            const double *a = M.g_coef;
+            gr = (float)(a[0] + a[2] * (double)x + a[4] * (double)z);
+            gi = (float)(a[1] + a[3] * (double)x + a[5] * (double)z);
+        } else if (M.g_kind == 2) {
+            gr = x * x - z * z;
+            gi = 0.f;
+        } else {
+            const EvalDev &E = T.ev[e];
+            if (wall == 0) {
+                column((float)E.kl_re, (float)E.kl_im, z, gr, gi);
+            } else if (wall == 1) {
+                column((float)E.kr_re, (float)E.kr_im, z, gr, gi);
+            } else {
+                const float t = (X + M.fhw) / (2.f * M.fhw);
+                const double lr = wall == 2 ? E.tl_re : E.bl_re, li = wall == 2 ? E.tl_im : E.bl_im;
+                const double rr = wall == 2 ? E.tr_re : E.br_re, ri = wall == 2 ? E.tr_im : E.br_im;
+                gr = fmaf(t, (float)(rr - lr), (float)lr);
+                gi = fmaf(t, (float)(ri - li), (float)li);
+            }
+        }
+        // (cw - i sw)(gr + i gi)
+        return make_double2((double)fmaf(cw, gr, sw * gi), (double)fmaf(cw, gi, -sw * gr));
+    }
+};
+
+template <int KMAX, int GEO>
+static cudaError_t launch_one(const ModelDev &M, const WalkArgs &A, int grid, int block,
+                              cudaStream_t s) {
+    const size_t sm = shared_bytes<float, KMAX>(block / 32);
+    auto k = walk_kernel<WalkerF32<KMAX, GEO>>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k<<<grid, block, sm, s>>>(M, A);
+    return cudaGetLastError();
+}
+
+template <int KMAX, int GEO>
+static int occ_one(int block) {
+    const size_t sm = shared_bytes<float, KMAX>(block / 32);
+    auto k = walk_kernel<WalkerF32<KMAX, GEO>>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, sm) != cudaSuccess) return 0;
+    return n;
+}
+
+#define SDD_DISPATCH(FN, ...)                                                   \
+    switch (kmax * 2 + geo) {                                                   \
+    case 4: return FN<2, GEO_SHAPES>(__VA_ARGS__);                              \
+    case 5: return FN<2, GEO_RASTER>(__VA_ARGS__);                              \
+    case 6: return FN<3, GEO_SHAPES>(__VA_ARGS__);                              \
+    case 7: return FN<3, GEO_RASTER>(__VA_ARGS__);                              \
+    case 8: return FN<4, GEO_SHAPES>(__VA_ARGS__);                              \
+    case 9: return FN<4, GEO_RASTER>(__VA_ARGS__);                              \
+    case 16: return FN<8, GEO_SHAPES>(__VA_ARGS__);                             \
+    case 17: return FN<8, GEO_RASTER>(__VA_ARGS__);                             \
+    default: break;                                                             \
+    }
+
+cudaError_t launch_walk_f32(int kmax, int geo, const ModelDev &M, const WalkArgs &A, int grid,
+                            int block, cudaStream_t s) {
+    SDD_DISPATCH(launch_one, M, A, grid, block, s)
+    return cudaErrorInvalidValue;
+}
+
+int occupancy_f32(int kmax, int geo, int block) {
+    SDD_DISPATCH(occ_one, block)
+    return 0;
+}
+
+}  // namespace sdd

@@ -1,0 +1,367 @@
+// Persistent walk scheduler shared by the single- and double-precision walks.
+//
+// Work model.  The estimator of Sec. 3.1 averages independent walks per
+// interface node; the node values are independent of one another (Sec. 5).
+// The host cuts every node's paths into work items (node, path chunk).
+// Each warp of a persistent grid takes items from a global atomic counter and
+// keeps its 32 lanes busy: a lane whose walk has reached the boundary takes
+// the next path of the warp's current item at once, and when that item is
+// fully handed out the warp opens the next item while the last walks of the
+// previous one finish (two items may be open per warp).  Uneven exit times
+// therefore idle no lane until the queue is empty.
+//
+// Exit records.  A finished walk writes a small record (exit point, hit
+// fraction theta, wall, last material, per-material step counts) into a
+// per-warp ring in shared memory.  Once 32 records are waiting, the whole
+// warp turns them into samples g(exit) exp(-i (1/2) sum_m kappa_{e,m} T_m)
+// for every evaluation e, lane l handling evaluation l mod Epad, and adds
+// them to per-lane FP64 sums (sum re, sum im, sum re^2, sum im^2) kept per
+// open item.  When an item's last walk is done its sums are reduced across
+// the lanes with warp shuffles (fixed order) and written to the item's slot;
+// a second kernel adds the slots of each node in item order.
+#pragma once
+
+#include "sdd_internal.cuh"
+
+namespace sdd {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32 -> 64-bit products with multipliers 0xD2511F53 and 0xCD9E8D57, the
+// key bumped by 0x9E3779B9 / 0xBB67AE85 between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// The same generator when counter words 1..3 are fixed for the whole walk:
+// the first round's product of word 2 is precomputed (pre_x = hi1 ^ c1 ^ k0,
+// pre_y = lo1), leaving one product in round one.
+__device__ __forceinline__ uint4 philox4x32_10_pre(uint32_t c0, uint32_t c3, uint32_t pre_x,
+                                                   uint32_t pre_y, uint32_t k0, uint32_t k1) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    uint4 c = make_uint4(pre_x, pre_y, hi0 ^ c3 ^ k1, lo0);
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+        const uint32_t h0 = __umulhi(0xD2511F53u, c.x), l0 = 0xD2511F53u * c.x;
+        const uint32_t h1 = __umulhi(0xCD9E8D57u, c.z), l1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(h1 ^ c.y ^ k0, l1, h0 ^ c.w ^ k1, l0);
+    }
+    return c;
+}
+
+// Shared-memory layout of one CTA: model tables, then for each warp its
+// exit-record ring, its scheduler state and its lanes' FP64 sums.
+template <class Real, int KMAX>
+struct Ring {
+    Real x[kRing], z[kRing], th[kRing];
+    uint32_t meta[kRing];  // wall | m_last << 2 | tag << 5 | truncated << 6
+    uint32_t n[kRing];     // occupation steps (all steps but the exiting one)
+    uint32_t path[kRing];
+    uint32_t cnt[KMAX > 1 ? KMAX - 1 : 1][kRing];  // steps in materials 1..K-1
+};
+
+// Scheduler state of one warp (every field is the same for all its lanes,
+// each lane reads back what it wrote) and the lanes' sums, kept out of
+// registers because only the exit handler touches them.
+struct WarpState {
+    double acc[2][4][32];  // [set][sum re, sum im, sum re^2, sum im^2][lane]
+    unsigned long long steps[32];
+    unsigned long long walks, trunc;
+    double nx0, nz0;
+    int32_t item[2];   // item of accumulator set (-1: free)
+    int32_t out[2];    // walks handed out and not yet ended
+    int32_t ntr[2];    // truncated walks
+    int32_t disp_set, disp_rem;
+    uint32_t disp_next, nid;
+    uint32_t head, tail;
+    int32_t queue_empty;
+};
+
+struct SharedTables {
+    double kappa[kMaxE * kMaxK];
+    EvalDev ev[kMaxE];
+};
+
+template <class Real, int KMAX>
+struct WarpSmem {
+    Ring<Real, KMAX> ring;
+    WarpState st;
+};
+
+template <class Real, int KMAX>
+__host__ __device__ constexpr size_t shared_bytes(int warps) {
+    return sizeof(SharedTables) + (size_t)warps * sizeof(WarpSmem<Real, KMAX>);
+}
+
+// Exit information handed from a walker to the scheduler.
+template <class Real>
+struct ExitInfo {
+    Real x, z, th;  // exit point (walker coordinates) and hit fraction
+    int wall;       // 0..3
+};
+
+// Scheduler kernel.  W is a walker type providing
+//   using Real; static constexpr int KMAX;
+//   start(M, A, x0, z0, path, node_id)  -- begin a walk
+//   iterate(M, A, path, ExitInfo&) -> 0 running, 1 exited, 2 truncated
+//     (two Euler steps per call)
+//   fields n, cnt[KMAX-1], mcur
+//   static sample(M, T, e, x, z, th, wall, mlast, counts, dt) -> double2
+//   static to_abs(M, x, z, ax, az)
+template <class W>
+__global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ ModelDev M,
+                                                   const WalkArgs A) {
+    using Real = typename W::Real;
+    constexpr int KMAX = W::KMAX;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SharedTables &T = *reinterpret_cast<SharedTables *>(smem_raw);
+    WarpSmem<Real, KMAX> &WS =
+        reinterpret_cast<WarpSmem<Real, KMAX> *>(smem_raw + sizeof(SharedTables))[threadIdx.x >> 5];
+    Ring<Real, KMAX> &R = WS.ring;
+    WarpState &S = WS.st;
+
+    for (int i = threadIdx.x; i < M.E * M.K; i += blockDim.x) T.kappa[i] = M.kappa[i];
+    for (int i = threadIdx.x; i < M.E; i += blockDim.x) T.ev[i] = M.ev[i];
+
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const bool dump = A.rec_steps != nullptr;
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) S.acc[s][q][lane] = 0.0;
+    S.steps[lane] = 0ull;
+    if (lane == 0) {
+        S.walks = 0ull; S.trunc = 0ull;
+        S.item[0] = S.item[1] = -1;
+        S.out[0] = S.out[1] = 0;
+        S.ntr[0] = S.ntr[1] = 0;
+        S.disp_set = -1; S.disp_rem = 0; S.disp_next = 0; S.nid = 0;
+        S.head = S.tail = 0;
+        S.queue_empty = 0;
+        S.nx0 = S.nz0 = 0.0;
+    }
+    __syncthreads();
+
+    // per-lane walk state
+    W w;
+    bool active = false;
+    int tag = 0;
+    uint32_t path = 0;
+
+    // Turn records [head, head + cnt) of the ring into samples; lane l
+    // handles evaluation l mod Epad of records l / Epad, l / Epad + 32 / Epad, ...
+    auto process = [&](int cnt) {
+        const int Epad = M.Epad;
+        const int my_e = lane & (Epad - 1);
+        const int my_ro = lane / Epad;
+        const int per_round = 32 / Epad;
+        const uint32_t head = S.head;
+        const int rounds = (cnt * Epad + 31) >> 5;
+        for (int k = 0; k < rounds; ++k) {
+            const int ri = k * per_round + my_ro;
+            if (ri < cnt && my_e < M.E) {
+                const int s = (head + ri) & (kRing - 1);
+                const uint32_t meta = R.meta[s];
+                const bool tr = (meta >> 6) & 1u;
+                const int rt = (meta >> 5) & 1u;
+                uint32_t c[KMAX];
+                uint32_t rest = R.n[s];
+#pragma unroll
+                for (int j = 1; j < KMAX; ++j) {
+                    c[j] = R.cnt[j - 1][s];
+                    rest -= c[j];
+                }
+                c[0] = rest;
+                if (dump) {
+                    if (my_e == 0) {
+                        const int64_t o = (int64_t)(R.path[s] - A.items[0].path0);
+                        double ex, ez;
+                        W::to_abs(M, R.x[s], R.z[s], ex, ez);
+                        A.rec_steps[o] = (int64_t)R.n[s] + (tr ? 0 : 1);
+#pragma unroll
+                        for (int j = 0; j < KMAX; ++j)
+                            if (j < M.K) A.rec_counts[o * M.K + j] = (int64_t)c[j];
+                        A.rec_exit[3 * o + 0] = ex;
+                        A.rec_exit[3 * o + 1] = ez;
+                        A.rec_exit[3 * o + 2] = (double)R.th[s];
+                        A.rec_wall[o] = tr ? -1 : (int)(meta & 3u);
+                        A.rec_mlast[o] = (int)((meta >> 2) & 7u);
+                    }
+                } else if (!tr) {
+                    const double2 v = W::sample(M, T, my_e, R.x[s], R.z[s], R.th[s],
+                                                (int)(meta & 3u), (int)((meta >> 2) & 7u), c, A.dt);
+                    double *a0 = &S.acc[rt][0][lane];
+                    a0[0] += v.x;
+                    a0[32] += v.y;
+                    a0[64] = fma(v.x, v.x, a0[64]);
+                    a0[96] = fma(v.y, v.y, a0[96]);
+                }
+            }
+        }
+        __syncwarp();
+        S.head = head + (uint32_t)cnt;
+        __syncwarp();
+    };
+
+    // Reduce the sums of set s across lanes (fixed order) and store them.
+    auto flush_set = [&](int s) {
+        const int Epad = M.Epad;
+        double v0 = S.acc[s][0][lane], v1 = S.acc[s][1][lane];
+        double v2 = S.acc[s][2][lane], v3 = S.acc[s][3][lane];
+        for (int off = 16; off >= Epad; off >>= 1) {
+            v0 += __shfl_xor_sync(kFull, v0, off);
+            v1 += __shfl_xor_sync(kFull, v1, off);
+            v2 += __shfl_xor_sync(kFull, v2, off);
+            v3 += __shfl_xor_sync(kFull, v3, off);
+        }
+        const int it = S.item[s];
+        if (!dump) {
+            if (lane < M.E) {
+                double *o = A.slots + ((size_t)it * M.E + lane) * 4;
+                o[0] = v0; o[1] = v1; o[2] = v2; o[3] = v3;
+            }
+            if (lane == 0) A.item_trunc[it] = S.ntr[s];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) S.acc[s][q][lane] = 0.0;
+        __syncwarp();
+        if (lane == 0) { S.item[s] = -1; S.ntr[s] = 0; }
+        __syncwarp();
+    };
+
+    // Hand paths to idle lanes; open new items while a set is free.
+    auto refill = [&]() {
+        unsigned need = __ballot_sync(kFull, !active);
+        while (need) {
+            if (S.disp_rem == 0) {
+                if (S.queue_empty) break;
+                const int fs = S.item[0] < 0 ? 0 : (S.item[1] < 0 ? 1 : -1);
+                if (fs < 0) break;  // both sets open: wait for one to finish
+                int it = 0;
+                if (lane == 0) it = atomicAdd(A.queue, 1);
+                it = __shfl_sync(kFull, it, 0);
+                if (it >= A.n_items) {
+                    if (lane == 0) S.queue_empty = 1;
+                    __syncwarp();
+                    break;
+                }
+                const Item I = A.items[it];
+                if (lane == 0) {
+                    S.item[fs] = it;
+                    S.out[fs] = 0;
+                    S.ntr[fs] = 0;
+                    S.disp_set = fs;
+                    S.disp_next = I.path0;
+                    S.disp_rem = I.count;
+                    S.nx0 = A.nodes[2 * I.node];
+                    S.nz0 = A.nodes[2 * I.node + 1];
+                    S.nid = A.node_ids ? A.node_ids[I.node] : (uint32_t)I.node;
+                }
+                __syncwarp();
+                if (I.count == 0) continue;
+            }
+            const int rem = S.disp_rem;
+            const int navail = __popc(need);
+            const int k = navail < rem ? navail : rem;
+            const int rank = __popc(need & lt_mask);
+            const bool mine = ((need >> lane) & 1u) && rank < k;
+            if (mine) {
+                path = S.disp_next + (uint32_t)rank;
+                tag = S.disp_set;
+                active = true;
+                w.start(M, A, S.nx0, S.nz0, path, S.nid);
+            }
+            const unsigned got = __ballot_sync(kFull, mine);
+            need &= ~got;
+            if (lane == 0) {
+                S.disp_next += (uint32_t)k;
+                S.disp_rem = rem - k;
+                S.out[S.disp_set] += k;
+            }
+            __syncwarp();
+        }
+    };
+
+    refill();
+    int n_active = __popc(__ballot_sync(kFull, active));
+    ExitInfo<Real> ei;
+    while (n_active > 0) {
+        int st = 0;
+        if (active) st = w.iterate(M, A, path, ei);
+        const unsigned em = __ballot_sync(kFull, st != 0);
+        if (em == 0) continue;
+
+        // 1. records of the walks that ended
+        const int nex = __popc(em);
+        const uint32_t tail = S.tail;
+        if (st != 0) {
+            const int slot = (tail + __popc(em & lt_mask)) & (kRing - 1);
+            const bool tr = st == 2;
+            R.x[slot] = ei.x;
+            R.z[slot] = ei.z;
+            R.th[slot] = ei.th;
+            R.meta[slot] = (uint32_t)ei.wall | ((uint32_t)w.mcur << 2) | ((uint32_t)tag << 5) |
+                           ((uint32_t)tr << 6);
+            R.n[slot] = w.n;
+            R.path[slot] = path;
+#pragma unroll
+            for (int j = 1; j < KMAX; ++j) R.cnt[j - 1][slot] = w.cnt[j - 1];
+            S.steps[lane] += (unsigned long long)w.n + (tr ? 0ull : 1ull);
+            active = false;
+        }
+        const unsigned t1 = __ballot_sync(kFull, st != 0 && tag == 1);
+        const unsigned tr0 = __ballot_sync(kFull, st == 2 && tag == 0);
+        const unsigned tr1 = __ballot_sync(kFull, st == 2 && tag == 1);
+        if (lane == 0) {
+            S.tail = tail + (uint32_t)nex;
+            S.out[1] -= __popc(t1);
+            S.out[0] -= nex - __popc(t1);
+            S.ntr[0] += __popc(tr0);
+            S.ntr[1] += __popc(tr1);
+            S.walks += (unsigned long long)nex;
+            S.trunc += (unsigned long long)(__popc(tr0) + __popc(tr1));
+        }
+        __syncwarp();
+
+        // 2. a full batch of records
+        while (S.tail - S.head >= 32) process(32);
+
+        // 3. items whose walks have all ended
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+            if (S.item[s] >= 0 && S.out[s] == 0 && !(S.disp_set == s && S.disp_rem > 0)) {
+                if (S.tail != S.head) process((int)(S.tail - S.head));
+                flush_set(s);
+            }
+        }
+
+        // 4. new walks for idle lanes
+        refill();
+        n_active = __popc(__ballot_sync(kFull, active));
+    }
+    // every item handed to this warp has been flushed (its walks all ended)
+
+    unsigned long long my_steps = S.steps[lane];
+    for (int off = 16; off > 0; off >>= 1) my_steps += __shfl_xor_sync(kFull, my_steps, off);
+    if (lane == 0 && !dump) {
+        atomicAdd(&A.counters[0], my_steps);
+        atomicAdd(&A.counters[1], S.walks);
+        atomicAdd(&A.counters[2], S.trunc);
+    }
+}
+
+}  // namespace sdd

@@ -1,0 +1,277 @@
+"""Thin ctypes binding of libsdd (include/sdd.h): argument marshalling only.
+
+Every step of the Monte Carlo evaluation runs in the CUDA library; there is
+no CPU fallback.  If libsdd.so is missing or cannot be loaded, ``lib()``
+raises and nothing here computes anything.
+
+The functions carry the names of the C entry points:
+    sdd_create(model)                           -> Context
+    sdd_destroy(ctx)
+    sdd_interface_values(ctx, nodes, n_paths, dt, seed, ...)        host arrays
+    sdd_interface_values_device(ctx, d_nodes, n_paths, dt, seed, d_mean, d_se, ...)
+    sdd_walk_records(ctx, x0, z0, node_id, p0, count, dt, seed, ...)
+    sdd_status_str(status), sdd_last_error()
+Models are the plain dicts of ``inputs.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsdd.so")
+
+SDD_OK, SDD_E_ARG, SDD_E_OOM, SDD_E_CUDA, SDD_E_TRUNCATED = 0, 1, 2, 3, 4
+SDD_E_CANCELLED, SDD_E_TIMEOUT, SDD_E_UNSUPPORTED, SDD_E_BUSY = 5, 6, 7, 8
+SDD_FP32, SDD_FP64 = 0, 1
+MAX_K, MAX_E, MAX_SHAPES = 8, 32, 16
+
+
+class SddError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib().sdd_last_error().decode()
+        super().__init__(f"{where}: {lib().sdd_status_str(status).decode()} ({msg})")
+
+
+class sdd_domain(ctypes.Structure):
+    _fields_ = [("x_min", ctypes.c_double), ("x_max", ctypes.c_double),
+                ("z_min", ctypes.c_double), ("z_max", ctypes.c_double)]
+
+
+class sdd_shape(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("material", ctypes.c_int32), ("v", ctypes.c_double * 6)]
+
+
+class sdd_model_desc(ctypes.Structure):
+    _fields_ = [
+        ("domain", sdd_domain),
+        ("n_materials", ctypes.c_int32), ("n_eval", ctypes.c_int32),
+        ("kappa", ctypes.POINTER(ctypes.c_double)),
+        ("bg_air", ctypes.c_int32), ("bg_earth", ctypes.c_int32),
+        ("shapes", ctypes.POINTER(sdd_shape)), ("n_shapes", ctypes.c_int32),
+        ("raster", ctypes.POINTER(ctypes.c_int8)), ("nx", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("g_kind", ctypes.c_int32), ("g_left", ctypes.c_int32), ("g_right", ctypes.c_int32),
+        ("g_coef", ctypes.c_double * 6),
+    ]
+
+
+class sdd_config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("max_steps", ctypes.c_int64),
+                ("block_threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("chunk_paths", ctypes.c_int32)]
+
+
+class sdd_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_uint64), ("walks", ctypes.c_uint64),
+                ("truncated", ctypes.c_uint64), ("kernel_ms", ctypes.c_double),
+                ("launches", ctypes.c_int32), ("items", ctypes.c_int32),
+                ("grid", ctypes.c_int32), ("block", ctypes.c_int32)]
+
+
+P = ctypes.POINTER
+_lib = None
+
+# (name, restype, argtypes) of every entry point declared in include/sdd.h
+SIGNATURES = [
+    ("sdd_create", ctypes.c_int, [P(sdd_model_desc), P(ctypes.c_void_p)]),
+    ("sdd_destroy", None, [ctypes.c_void_p]),
+    ("sdd_interface_values", ctypes.c_int,
+     [ctypes.c_void_p, P(ctypes.c_double), P(ctypes.c_uint32), ctypes.c_int32, P(ctypes.c_int64),
+      ctypes.c_double, ctypes.c_uint64, P(sdd_config), P(ctypes.c_double), P(ctypes.c_double),
+      P(sdd_stats)]),
+    ("sdd_interface_values_device", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_int64),
+      ctypes.c_double, ctypes.c_uint64, P(sdd_config), ctypes.c_void_p, ctypes.c_void_p,
+      ctypes.c_void_p, ctypes.c_void_p]),
+    ("sdd_walk_records", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32,
+      ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, P(sdd_config), P(ctypes.c_int64),
+      P(ctypes.c_int64), P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_int32)]),
+    ("sdd_n_eval", ctypes.c_int32, [ctypes.c_void_p]),
+    ("sdd_n_materials", ctypes.c_int32, [ctypes.c_void_p]),
+    ("sdd_status_str", ctypes.c_char_p, [ctypes.c_int]),
+    ("sdd_last_error", ctypes.c_char_p, []),
+]
+
+
+def lib():
+    """Load libsdd.so (built by ``paper_1603_09311_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libsdd.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(P(ctypes.c_double))
+
+
+def make_desc(model: dict):
+    """sdd_model_desc of a model dict, plus the arrays it points into."""
+    kappa = np.ascontiguousarray(np.atleast_2d(np.asarray(model["kappa"], dtype=np.float64)))
+    E, K = kappa.shape
+    keep = [kappa]
+    d = sdd_model_desc()
+    dom = model["domain"]
+    d.domain = sdd_domain(*[float(v) for v in dom])
+    d.n_materials, d.n_eval = K, E
+    d.kappa = _dp(kappa)
+    bg = model.get("bg", (0, 1))
+    d.bg_air, d.bg_earth = int(bg[0]), int(bg[1])
+    shapes = model.get("shapes", [])
+    if shapes:
+        arr = (sdd_shape * len(shapes))()
+        for i, (kind, mat, v) in enumerate(shapes):
+            arr[i].kind, arr[i].material = int(kind), int(mat)
+            vv = list(v) + [0.0] * (6 - len(v))
+            for j in range(6):
+                arr[i].v[j] = float(vv[j])
+        keep.append(arr)
+        d.shapes = ctypes.cast(arr, P(sdd_shape))
+    d.n_shapes = len(shapes)
+    raster = model.get("raster")
+    if raster is not None:
+        r = np.ascontiguousarray(raster, dtype=np.int8)
+        keep.append(r)
+        d.raster = r.ctypes.data_as(P(ctypes.c_int8))
+        d.nz, d.nx = r.shape
+    g = model.get("g", ("columns", 1, 1))
+    if g[0] == "columns":
+        d.g_kind, d.g_left, d.g_right = 0, int(g[1]), int(g[2])
+    elif g[0] == "affine":
+        d.g_kind = 1
+        a, b, c = (complex(t) for t in g[1:4])
+        for j, v in enumerate([a.real, a.imag, b.real, b.imag, c.real, c.imag]):
+            d.g_coef[j] = v
+    elif g[0] == "x2mz2":
+        d.g_kind = 2
+    else:
+        raise ValueError(f"unknown g kind {g[0]}")
+    return d, keep
+
+
+def make_config(precision="fp32", max_steps=0, block_threads=0, ctas_per_sm=0, chunk_paths=0):
+    c = sdd_config()
+    c.precision = SDD_FP64 if precision in ("fp64", SDD_FP64) else SDD_FP32
+    c.max_steps, c.block_threads = int(max_steps), int(block_threads)
+    c.ctas_per_sm, c.chunk_paths = int(ctas_per_sm), int(chunk_paths)
+    return c
+
+
+class Context:
+    """Owns an sdd_ctx; closes it on close() or garbage collection."""
+
+    def __init__(self, handle, E, K):
+        self.handle, self.E, self.K = handle, E, K
+
+    def close(self):
+        if self.handle:
+            lib().sdd_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sdd_create(model: dict) -> Context:
+    d, _keep = make_desc(model)
+    h = ctypes.c_void_p()
+    st = lib().sdd_create(ctypes.byref(d), ctypes.byref(h))
+    if st != SDD_OK:
+        raise SddError(st, "sdd_create")
+    return Context(h, d.n_eval, d.n_materials)
+
+
+def sdd_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+def _paths(n_paths, n):
+    npth = np.asarray(n_paths, dtype=np.int64)
+    if npth.ndim == 0:
+        npth = np.full(n, int(npth), dtype=np.int64)
+    return np.ascontiguousarray(npth)
+
+
+def sdd_interface_values(ctx: Context, nodes, n_paths, dt: float, seed: int, node_ids=None,
+                         config: sdd_config | None = None, **cfg):
+    """Host-buffer call.  Returns (mean complex [n][E], se [n][E][2], stats dict);
+    raises SddError unless the status is SDD_OK or SDD_E_TRUNCATED."""
+    nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64).reshape(-1, 2))
+    n = nodes.shape[0]
+    npth = _paths(n_paths, n)
+    mean = np.zeros((n, ctx.E, 2))
+    se = np.zeros((n, ctx.E, 2))
+    st_out = sdd_stats()
+    ids = None
+    if node_ids is not None:
+        ids = np.ascontiguousarray(np.asarray(node_ids, dtype=np.uint32))
+    c = config if config is not None else make_config(**cfg)
+    st = lib().sdd_interface_values(
+        ctx.handle, _dp(nodes), None if ids is None else ids.ctypes.data_as(P(ctypes.c_uint32)),
+        n, npth.ctypes.data_as(P(ctypes.c_int64)), float(dt), int(seed) & (2 ** 64 - 1),
+        ctypes.byref(c), _dp(mean), _dp(se), ctypes.byref(st_out))
+    if st not in (SDD_OK, SDD_E_TRUNCATED):
+        raise SddError(st, "sdd_interface_values")
+    stats = {f: getattr(st_out, f) for f, _ in sdd_stats._fields_}
+    stats["status"] = st
+    return mean[..., 0] + 1j * mean[..., 1], se, stats
+
+
+def sdd_interface_values_device(ctx: Context, d_nodes_ptr: int, n_nodes: int, n_paths, dt: float,
+                                seed: int, d_mean_ptr: int, d_se_ptr: int, d_node_ids_ptr: int = 0,
+                                d_counters_ptr: int = 0, stream: int = 0,
+                                config: sdd_config | None = None, **cfg) -> int:
+    """Device-buffer call queued on `stream` (raw pointers, e.g. torch data_ptr())."""
+    npth = _paths(n_paths, n_nodes)
+    c = config if config is not None else make_config(**cfg)
+    st = lib().sdd_interface_values_device(
+        ctx.handle, ctypes.c_void_p(d_nodes_ptr), ctypes.c_void_p(d_node_ids_ptr or None), n_nodes,
+        npth.ctypes.data_as(P(ctypes.c_int64)), float(dt), int(seed) & (2 ** 64 - 1),
+        ctypes.byref(c), ctypes.c_void_p(d_mean_ptr), ctypes.c_void_p(d_se_ptr),
+        ctypes.c_void_p(d_counters_ptr or None), ctypes.c_void_p(stream or None))
+    if st != SDD_OK:
+        raise SddError(st, "sdd_interface_values_device")
+    return st
+
+
+def sdd_walk_records(ctx: Context, x0: float, z0: float, node_id: int, p0: int, count: int,
+                     dt: float, seed: int, config: sdd_config | None = None, **cfg):
+    """Per-path records (steps, counts [count][K], exit [count][3], wall, m_last)."""
+    steps = np.zeros(count, dtype=np.int64)
+    counts = np.zeros((count, ctx.K), dtype=np.int64)
+    ext = np.zeros((count, 3))
+    wall = np.zeros(count, dtype=np.int32)
+    mlast = np.zeros(count, dtype=np.int32)
+    c = config if config is not None else make_config(**cfg)
+    st = lib().sdd_walk_records(ctx.handle, float(x0), float(z0), int(node_id), int(p0), int(count),
+                                float(dt), int(seed) & (2 ** 64 - 1), ctypes.byref(c),
+                                steps.ctypes.data_as(P(ctypes.c_int64)),
+                                counts.ctypes.data_as(P(ctypes.c_int64)), _dp(ext),
+                                wall.ctypes.data_as(P(ctypes.c_int32)),
+                                mlast.ctypes.data_as(P(ctypes.c_int32)))
+    if st != SDD_OK:
+        raise SddError(st, "sdd_walk_records")
+    return {"steps": steps, "counts": counts, "exit": ext, "wall": wall, "m_last": mlast,
+            "truncated": (wall < 0).astype(np.int32)}
+
+
+def sdd_status_str(status: int) -> str:
+    return lib().sdd_status_str(status).decode()
+
+
+def sdd_last_error() -> str:
+    return lib().sdd_last_error().decode()

@@ -1,0 +1,101 @@
+"""Host-side checks of the C ABI (no GPU): the library builds and loads,
+exports every entry point declared in include/sdd.h, its struct layouts match
+the ctypes binding, and argument errors are reported before any CUDA call."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1603_09311_gb300 import build as B
+from paper_1603_09311_gb300 import inputs as I
+from paper_1603_09311_gb300 import sdd
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sdd.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return sdd.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sdd_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 8
+    for n in names:
+        assert hasattr(L, n), f"{n} declared in include/sdd.h but not exported"
+    bound = {s[0] for s in sdd.SIGNATURES}
+    assert set(names) == bound, "binding and header disagree"
+    nm = subprocess.run(["nm", "-D", "--defined-only", sdd.LIB_PATH], capture_output=True, text=True).stdout
+    for n in names:
+        assert re.search(rf"\bT {n}\b", nm), f"{n} is not a C (unmangled) export"
+
+
+def test_struct_layout_matches_header(tmp_path):
+    probe = tmp_path / "probe.c"
+    probe.write_text(f'''
+#include <stdio.h>
+#include <stddef.h>
+#include "{HEADER}"
+int main(void) {{
+  printf("%zu %zu %zu %zu %zu\\n", sizeof(sdd_model_desc), sizeof(sdd_shape), sizeof(sdd_config),
+         sizeof(sdd_stats), sizeof(sdd_domain));
+  printf("%zu %zu %zu %zu\\n", offsetof(sdd_model_desc, raster), offsetof(sdd_model_desc, g_coef),
+         offsetof(sdd_config, chunk_paths), offsetof(sdd_stats, block));
+  return 0;
+}}''')
+    exe = tmp_path / "probe"
+    subprocess.run(["gcc", str(probe), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    want = [ctypes.sizeof(sdd.sdd_model_desc), ctypes.sizeof(sdd.sdd_shape),
+            ctypes.sizeof(sdd.sdd_config), ctypes.sizeof(sdd.sdd_stats), ctypes.sizeof(sdd.sdd_domain),
+            sdd.sdd_model_desc.raster.offset, sdd.sdd_model_desc.g_coef.offset,
+            sdd.sdd_config.chunk_paths.offset, sdd.sdd_stats.block.offset]
+    assert [int(v) for v in out] == want
+
+
+def test_status_strings(L):
+    for s in range(9):
+        assert sdd.sdd_status_str(s)
+    assert "unknown" in sdd.sdd_status_str(99)
+
+
+@pytest.mark.parametrize("mutate,msg", [
+    (lambda m: m.update(kappa=[[0.0, -1.0]]), "kappa"),
+    (lambda m: m.update(kappa=[[0.0, float("nan")]]), "kappa"),
+    (lambda m: m.update(domain=(1.0, -1.0, 0.0, 1.0)), "domain"),
+    (lambda m: m.update(bg=(0, 5)), "background"),
+    (lambda m: m.update(shapes=[(0, 7, (0, 1, 0, 1, 0, 0))]), "shape material"),
+    (lambda m: m.update(shapes=[(3, 1, (0, 1, 0, 1, 0, 0))]), "shape kind"),
+    (lambda m: m.update(g=("columns", 0, 9)), "g_left"),
+    (lambda m: m.update(kappa=np.zeros((33, 2))), "n_eval"),
+    (lambda m: m.update(kappa=np.zeros((1, 9))), "n_materials"),
+    (lambda m: m.update(raster=np.full((4, 4), 3, dtype=np.int8)), "raster"),
+])
+def test_bad_models_are_rejected_before_any_cuda_call(L, mutate, msg):
+    m = I.halfspace(2.0)
+    mutate(m)
+    with pytest.raises(sdd.SddError) as e:
+        sdd.sdd_create(m)
+    assert e.value.status == sdd.SDD_E_ARG
+    assert msg in str(e.value)
+
+
+def test_null_context_is_an_argument_error(L):
+    n = np.zeros(2)
+    p = np.ones(1, dtype=np.int64)
+    st = L.sdd_interface_values(None, n.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), None, 1,
+                                p.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), 1e-3, 0, None,
+                                None, None, None)
+    assert st == sdd.SDD_E_ARG
+    L.sdd_destroy(None)  # allowed

@@ -1,0 +1,214 @@
+"""Parity of the CUDA library with the FP64 oracle, through the C ABI.
+
+FP64 mode (same Philox streams, same uniform rule (w + 1/2) 2^-32): every
+discrete outcome of every walk -- its number of steps, its per-material step
+counts, the wall it leaves by and its last material -- must equal the
+oracle's, its exit point and hit fraction to 1e-12, and the node means to
+1e-10 relative to the largest |g| (last-ulp differences of log/sin/cos
+between the two math libraries are the only source of difference).
+
+FP32 mode (same streams, uniform rule (floor(w/2^9) + 1/2) 2^-23, FP32
+positions): node means within 4 combined standard errors + 1e-4 of the
+oracle's on the same streams.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1603_09311_gb300 import build as B
+from paper_1603_09311_gb300 import inputs as I
+from paper_1603_09311_gb300 import sdd
+
+pytestmark = pytest.mark.gpu
+
+FP64_REL = 1e-10        # relative to max |g| on the boundary
+FP32_NSE, FP32_ABS = 4.0, 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+    sdd.lib()
+
+
+def _triangle_raster():
+    m = I.triangle()
+    r = dict(m)
+    r["raster"] = I.rasterize(m)
+    r["shapes"] = []
+    return r
+
+
+def _many_materials():
+    # K = 8: air, host and six shapes (rectangles and triangles), overlapping
+    shapes = [(0, 2, (-0.8, -0.4, 0.1, 0.4, 0, 0)), (1, 3, (-0.5, 0.2, -0.1, 0.2, -0.3, 0.7)),
+              (0, 4, (0.1, 0.5, 0.3, 0.6, 0, 0)), (1, 5, (0.2, 0.0, 0.8, 0.1, 0.6, 0.5)),
+              (0, 6, (-0.2, 0.2, 0.6, 0.9, 0, 0)), (1, 7, (0.4, 0.7, 0.9, 0.7, 0.7, 0.95))]
+    kap = [[0.0, 2.0, 5.0, 20.0, 0.5, 50.0, 1.0, 10.0]]
+    return {"domain": I.DOMAIN, "kappa": kap, "bg": (0, 1), "shapes": shapes, "g": ("columns", 1, 1)}
+
+
+MODELS = {
+    "halfspace": (I.halfspace(2.0), (0.3, 0.25)),
+    "quarterspace": (I.quarterspace(2.0, 20.0), (0.0, 0.5)),
+    "block16": (I.block_batched(), (0.2, 0.35)),
+    "triangle": (I.triangle(), (0.05, 0.4)),
+    "triangle_raster": (_triangle_raster(), (0.05, 0.4)),
+    "eight_materials": (_many_materials(), (0.0, 0.45)),
+    "affine_g": (I.uniform_model(3.0, g=("affine", 0.5 + 0.1j, 1.0 - 0.2j, -0.3 + 0.4j)), (0.4, 0.1)),
+    "x2mz2_g": (I.uniform_model(0.0, g=("x2mz2",)), (-0.6, 0.8)),
+}
+
+
+def _gmax(model):
+    # a bound on |g| over the boundary (all test models)
+    kap = np.asarray(model["kappa"], dtype=float).max()
+    return max(2.0, 1.0 + 0.5 * np.sqrt(kap) * 1.5)
+
+
+@pytest.mark.parametrize("name", sorted(MODELS))
+def test_fp64_walks_equal_oracle_path_by_path(name):
+    model, (x0, z0) = MODELS[name]
+    dt, seed, nid, p0, count = 1e-3, 12345, 7, 101, 3000
+    ctx = sdd.sdd_create(model)
+    g = sdd.sdd_walk_records(ctx, x0, z0, nid, p0, count, dt, seed, precision="fp64")
+    o = O.walk_records(model, (x0, z0), nid, p0, count, dt, seed, urule=32)
+    assert np.array_equal(g["steps"], o["steps"])
+    assert np.array_equal(g["counts"], o["counts"])
+    assert np.array_equal(g["wall"], np.where(o["truncated"] == 1, -1, o["wall"]))
+    assert np.array_equal(g["m_last"], o["m_last"])
+    assert np.allclose(g["exit"], o["exit"], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("name", sorted(MODELS))
+def test_fp64_node_values_match_oracle(name):
+    model, _ = MODELS[name]
+    nodes = np.array([[0.0, 0.25], [-0.55, 0.6], [0.35, -0.2], [0.7, 0.85], [0.05, 0.4]])
+    n_paths = np.array([1, 31, 33, 700, 2049])  # ragged: single walk, partial warps, several items
+    dt, seed = 1e-3, 99
+    ctx = sdd.sdd_create(model)
+    mean, se, st = sdd.sdd_interface_values(ctx, nodes, n_paths, dt, seed, precision="fp64",
+                                            chunk_paths=64)
+    ref = O.interface_values(model, nodes, n_paths, dt, seed, urule=32)
+    tol = FP64_REL * _gmax(model)
+    assert np.allclose(mean.real, ref["mean"].real, rtol=0, atol=tol)
+    assert np.allclose(mean.imag, ref["mean"].imag, rtol=0, atol=tol)
+    ok = n_paths > 1
+    assert np.allclose(se[ok], ref["se"][ok], rtol=1e-8, atol=1e-12)
+    assert np.all(np.isnan(se[~ok]))
+    assert st["walks"] == n_paths.sum() and st["steps"] == ref["steps"]
+
+
+@pytest.mark.parametrize("name", sorted(MODELS))
+def test_fp32_node_values_match_oracle(name):
+    model, _ = MODELS[name]
+    nodes = np.array([[0.0, 0.25], [-0.55, 0.6], [0.35, -0.2], [0.7, 0.85], [0.05, 0.4], [-0.9, 0.05]])
+    n_paths = np.array([4096, 3001, 5000, 4096, 2500, 4500])
+    dt, seed = 1e-3, 2024
+    ctx = sdd.sdd_create(model)
+    mean, se, st = sdd.sdd_interface_values(ctx, nodes, n_paths, dt, seed)
+    ref = O.interface_values(model, nodes, n_paths, dt, seed, urule=23)
+    tol = FP32_NSE * np.sqrt(se ** 2 + ref["se"] ** 2) + FP32_ABS
+    d = mean - ref["mean"]
+    assert np.all(np.abs(d.real) <= tol[..., 0])
+    assert np.all(np.abs(d.imag) <= tol[..., 1])
+    assert st["walks"] == n_paths.sum() and st["truncated"] == 0
+    # same streams: the step totals agree to a fraction of a percent
+    assert abs(st["steps"] - ref["steps"]) <= 0.01 * ref["steps"]
+
+
+def test_fp32_walks_follow_the_oracle_streams():
+    model, (x0, z0) = MODELS["quarterspace"]
+    ctx = sdd.sdd_create(model)
+    g = sdd.sdd_walk_records(ctx, x0, z0, 3, 0, 4000, 1e-3, 77)
+    o = O.walk_records(model, (x0, z0), 3, 0, 4000, 1e-3, 77, urule=23)
+    same = np.mean(g["steps"] == o["steps"])
+    assert same >= 0.9, same
+    assert np.array_equal(g["counts"].sum(1), g["steps"] - 1)
+
+
+def test_empty_and_single_inputs():
+    ctx = sdd.sdd_create(I.halfspace(2.0))
+    mean, se, st = sdd.sdd_interface_values(ctx, np.zeros((0, 2)), np.zeros(0, dtype=np.int64), 1e-3, 0)
+    assert mean.shape == (0, 1) and st["walks"] == 0
+    mean, se, st = sdd.sdd_interface_values(ctx, [[0.0, 0.25]], [1], 1e-3, 0, precision="fp64")
+    ref = O.interface_values(I.halfspace(2.0), [[0.0, 0.25]], [1], 1e-3, 0, urule=32)
+    assert abs(mean[0, 0] - ref["mean"][0, 0]) <= 1e-12 and np.all(np.isnan(se))
+
+
+def test_nodes_next_to_walls_and_node_ids():
+    model = I.halfspace(2.0)
+    eps = 1e-6
+    nodes = np.array([[-1 + eps, 0.3], [1 - eps, 0.3], [0.2, -0.5 + eps], [0.2, 1 - eps],
+                      [-1 + eps, -0.5 + eps]])
+    ids = np.array([40, 41, 42, 43, 44], dtype=np.uint32)
+    ctx = sdd.sdd_create(model)
+    mean, se, st = sdd.sdd_interface_values(ctx, nodes, 500, 1e-3, 5, node_ids=ids, precision="fp64")
+    ref = O.interface_values(model, nodes, 500, 1e-3, 5, urule=32, node_id0=40)
+    assert np.allclose(mean, ref["mean"], rtol=0, atol=1e-10)
+    # permuting the nodes together with their ids permutes the results
+    perm = np.array([3, 0, 4, 2, 1])
+    m2, _, _ = sdd.sdd_interface_values(ctx, nodes[perm], 500, 1e-3, 5, node_ids=ids[perm],
+                                        precision="fp64")
+    assert np.allclose(m2, mean[perm], rtol=0, atol=1e-12)
+
+
+def test_truncation_matches_oracle_exactly():
+    model = I.quarterspace(2.0, 20.0)
+    nodes = np.array([[0.0, 0.4], [0.3, 0.2]])
+    ctx = sdd.sdd_create(model)
+    mean, se, st = sdd.sdd_interface_values(ctx, nodes, 3000, 1e-3, 8, precision="fp64", max_steps=120)
+    ref = O.interface_values(model, nodes, 3000, 1e-3, 8, urule=32, max_steps=120)
+    assert st["status"] == sdd.SDD_E_TRUNCATED
+    assert st["truncated"] == ref["truncated"] > 0
+    assert np.allclose(mean, ref["mean"], rtol=0, atol=1e-10 * 30)
+
+
+def test_launch_shape_does_not_change_results():
+    w = I.scaled(I.workload("block"), n_nodes=12, paths_per_node=3000, dt=1e-3)
+    ctx = sdd.sdd_create(w["model"])
+    base, _, _ = sdd.sdd_interface_values(ctx, w["nodes"], w["n_paths"], w["dt"], 1)
+    scale = np.abs(base).max()
+    for cfg in ({"block_threads": 128}, {"chunk_paths": 32}, {"chunk_paths": 2048},
+                {"ctas_per_sm": 1, "block_threads": 64}):
+        m, _, _ = sdd.sdd_interface_values(ctx, w["nodes"], w["n_paths"], w["dt"], 1, **cfg)
+        assert np.allclose(m, base, rtol=0, atol=1e-12 * scale), cfg
+
+
+def test_device_api_matches_host_api():
+    torch = pytest.importorskip("torch")
+    w = I.scaled(I.workload("quarterspace"), n_nodes=8, paths_per_node=5000, dt=1e-3)
+    ctx = sdd.sdd_create(w["model"])
+    hm, hs, _ = sdd.sdd_interface_values(ctx, w["nodes"], w["n_paths"], w["dt"], 4)
+    dev = torch.device("cuda:0")
+    d_nodes = torch.tensor(w["nodes"], dtype=torch.float64, device=dev)
+    d_mean = torch.empty((8, 1, 2), dtype=torch.float64, device=dev)
+    d_se = torch.empty((8, 1, 2), dtype=torch.float64, device=dev)
+    d_cnt = torch.zeros(3, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    sdd.sdd_interface_values_device(ctx, d_nodes.data_ptr(), 8, w["n_paths"], w["dt"], 4,
+                                    d_mean.data_ptr(), d_se.data_ptr(),
+                                    d_counters_ptr=d_cnt.data_ptr(), stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    dm = d_mean.cpu().numpy()
+    assert np.allclose(dm[..., 0] + 1j * dm[..., 1], hm, rtol=0, atol=1e-12)
+    assert np.allclose(d_se.cpu().numpy(), hs, rtol=1e-9, atol=0)
+    assert int(d_cnt[1]) == 8 * 5000
+
+
+@pytest.mark.slow
+def test_full_size_quarterspace_sampled_nodes():
+    # the benchmarked launch: 64 nodes x 1e5 paths, dt = 1e-4, default launch;
+    # two nodes recomputed by the oracle in full
+    w = I.workload("quarterspace")
+    ctx = sdd.sdd_create(w["model"])
+    mean, se, st = sdd.sdd_interface_values(ctx, w["nodes"], w["n_paths"], w["dt"], w["seed"])
+    assert st["walks"] == 6_400_000 and st["truncated"] == 0
+    # each sampled node keeps its own node id (its index in the full call)
+    for j in (9, 50):
+        r = O.interface_values(w["model"], w["nodes"][j:j + 1], w["n_paths"][j:j + 1], w["dt"],
+                               w["seed"], urule=23, node_id0=j)
+        tol = FP32_NSE * np.sqrt(se[j] ** 2 + r["se"][0] ** 2) + FP32_ABS
+        d = mean[j] - r["mean"][0]
+        assert np.all(np.abs(d.real) <= tol[..., 0]) and np.all(np.abs(d.imag) <= tol[..., 1])
+    assert np.all(np.isfinite(mean)) and np.all(se > 0)
