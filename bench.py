@@ -1,0 +1,320 @@
+"""Benchmark: TE Feynman-Kac interface-node Monte Carlo on one GB300.
+
+One step = one full evaluation of the quarter-space workload: 64 interface
+nodes on x = 0, z in [0, 0.9], 1e5 walks per node, dt = 1e-4 (dimensionless,
+earth kappa 2 left / 20 right, air 0), single-precision walk with FP64 sums.
+
+  value   walk-steps/s with the inputs resident in HBM (device-buffer C ABI,
+          CUDA events on the launching stream, L2 flushed between steps)
+  e2e     the same through the host-buffer C ABI (host<->device copies inside)
+  roofline  issue-bound ("alu"): algorithmic thread-instructions per step x
+          steps / walk-kernel time, against SMs x 128 lanes x max SM clock
+  cpu_baseline  the FP64 oracle on the host cores, on a bounded sample
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs the whole workload on its own node ids
+(weak scaling, no collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1603_09311_gb300 import inputs as I  # noqa: E402
+
+WORKLOAD = "quarterspace"
+METRIC = "walk-steps/s"
+# Algorithmic thread-instructions per Euler step of the single-precision walk
+# (derivation in the design doc): half a Philox4x32-10 call (20), two uniforms (4),
+# Box-Muller (7), Euler update (2), wall tests and bridge filter (6),
+# quarter-space material lookup (7), two occupation counters (4), step
+# bookkeeping (3).
+INST_PER_STEP = 53
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def barrier_max(value: float, world: int, torch):
+    if world == 1:
+        return value
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(w, seconds_target: float = 15.0):
+    """Time the oracle on a bounded sample of the workload: every node, the
+    first n walks of each, n sized so the run takes about seconds_target."""
+    from oracle import oracle as O
+    threads = O.max_threads()
+    probe = 100
+    t0 = time.time()
+    r = O.interface_values(w["model"], w["nodes"], probe, w["dt"], w["seed"], urule=23)
+    dtp = max(time.time() - t0, 1e-3)
+    n = int(min(max(probe, probe * seconds_target / dtp), w["n_paths"].max()))
+    t0 = time.time()
+    r = O.interface_values(w["model"], w["nodes"], n, w["dt"], w["seed"], urule=23)
+    el = time.time() - t0
+    return {"value": r["steps"] / el, "unit": METRIC, "cores": threads, "kind": "oracle",
+            "sample": f"{len(w['nodes'])} nodes x first {n} walks of the workload "
+                      f"({r['steps']:.3e} steps, {el:.1f} s)",
+            "seconds": el}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = I.workload(WORKLOAD)
+    from oracle import oracle as O
+    # each step: every node, a bounded number of walks, sized so the whole run
+    # (warmup + steps) ends within a few minutes
+    total_steps = args.warmup + args.steps
+    per_step_s = max(2.0, 150.0 / total_steps)
+    base = cpu_baseline(w, per_step_s)
+    n = int(base["sample"].split("first ")[1].split(" ")[0])
+    times, steps = [], 0
+    for i in range(total_steps):
+        t0 = time.time()
+        r = O.interface_values(w["model"], w["nodes"], n, w["dt"], w["seed"] + i, urule=23)
+        el = time.time() - t0
+        if i >= args.warmup:
+            times.append(el)
+            steps += r["steps"]
+    value = steps / sum(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: 64 nodes, first {n} of 1e5 walks per node, dt 1e-4",
+                       "l2": "n/a (host)"},
+            "cpu_baseline": {"value": value, "unit": METRIC, "cores": base["cores"],
+                             "kind": "oracle", "sample": f"64 nodes x {n} walks per step"},
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sdd", choices=["sdd", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true",
+                    help="16 nodes x 1e5 walks of the same workload (for profiler captures)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1603_09311_gb300 import build as B
+    from paper_1603_09311_gb300 import sdd
+    if rank == 0:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    B.build()
+
+    w = I.workload(WORKLOAD)
+    if args.small:
+        w = I.scaled(w, n_nodes=16)
+    n = len(w["nodes"])
+    node_ids = np.arange(n, dtype=np.uint32) + np.uint32(rank * n)
+    ctx = sdd.sdd_create(w["model"])
+    dev = torch.device("cuda", local)
+    d_nodes = torch.tensor(w["nodes"], dtype=torch.float64, device=dev)
+    d_ids = torch.tensor(node_ids.astype(np.int64), dtype=torch.int64, device=dev).to(torch.int32)
+    d_mean = torch.empty((n, ctx.E, 2), dtype=torch.float64, device=dev)
+    d_se = torch.empty((n, ctx.E, 2), dtype=torch.float64, device=dev)
+    d_cnt = torch.zeros((max(args.steps, args.warmup), 3), dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def step(seed, k):
+        sdd.sdd_interface_values_device(ctx, d_nodes.data_ptr(), n, w["n_paths"], w["dt"], seed,
+                                        d_mean.data_ptr(), d_se.data_ptr(),
+                                        d_node_ids_ptr=d_ids.data_ptr(),
+                                        d_counters_ptr=d_cnt[k].data_ptr(), stream=stream.cuda_stream)
+
+    for i in range(args.warmup):
+        step(w["seed"] + 1000 + i, i)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region: K steps, L2 flushed between steps
+    sampler = ClockSampler(local)
+    sampler.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    steps_done = 0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        step(w["seed"] + k, k)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = barrier_max(sum(step_ms), world, torch)
+    cnt = d_cnt[: args.steps].cpu().numpy()
+    steps_local = int(cnt[:, 0].sum())
+    steps_done_one = steps_local / args.steps
+    assert int(cnt[:, 1].min()) == n * int(w["n_paths"][0]), "a step did not run every walk"
+    steps_done = int(round(barrier_max(float(steps_local), world, torch) * world))
+    mean = d_mean.cpu().numpy()
+    se = d_se.cpu().numpy()
+    value = steps_done / (total_ms * 1e-3)
+    se_c = np.sqrt((se ** 2).sum(-1))
+    solves = int((se_c <= 1e-3).sum())
+
+    # ---- end-to-end through the host-buffer C ABI (copies inside the timed region)
+    e2e_steps, e2e_t, h2d, d2h = 0, 0.0, 0, 0
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, st = sdd.sdd_interface_values(ctx, w["nodes"], w["n_paths"], w["dt"], w["seed"] + k,
+                                            node_ids=node_ids)
+        e2e_t += time.perf_counter() - t0
+        e2e_steps += st["steps"]
+        h2d, d2h = st["h2d_bytes"], st["d2h_bytes"]
+        kernel_ms_host = st["kernel_ms"]
+    e2e_t = barrier_max(e2e_t, world, torch)
+    e2e_value = e2e_steps * world / e2e_t
+
+    peaks, src = load_peaks()
+    clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tinst = n_sm * 128 * clk_mhz * 1e6 / 1e12
+    walk_ms = statistics.mean(step_ms)  # walk kernel dominates each step (ncu share in profiles/)
+    achieved = INST_PER_STEP * steps_done_one / (walk_ms * 1e-3) / 1e12
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": (f"quarterspace: {n} nodes on x=0, z in [0,0.9], "
+                                    f"{int(w['n_paths'][0])} walks/node, dt 1e-4, kappa 2|20 earth, "
+                                    "0 air (dimensionless)"),
+                       "walks_per_step": int(n * w["n_paths"][0]),
+                       "steps_per_step": int(steps_done_one),
+                       "l2": "flushed between steps (256 MB write)",
+                       "precision": "FP32 walk, FP64 sums"},
+            "node_solves_per_s": solves * world / (total_ms * 1e-3 / args.steps) if solves else 0.0,
+            "nodes_at_se_1e-3": f"{solves}/{n}",
+            "max_node_se": float(se_c.max()),
+            "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tinst,
+                         "unit": "Tinst/s", "frac": achieved / peak_tinst, "traffic": None,
+                         "peak_source": f"{n_sm} SMs x 128 lanes x {clk_mhz:.0f} MHz ({src} max clock)",
+                         "inst_per_step": INST_PER_STEP},
+            "clocks": clocks,
+            "gpu_launches": 2 * args.steps,
+        }
+        if not args.no_cpu_baseline and world == 1:
+            cb = cpu_baseline(w)
+            cb.pop("seconds", None)
+            line["cpu_baseline"] = cb
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    ctx.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

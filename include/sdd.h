@@ -117,7 +117,9 @@ enum { SDD_FP32 = 0, SDD_FP64 = 1 };
 typedef struct {
     int32_t precision;     /* SDD_FP32: single-precision walk, FP64 sums.
                               SDD_FP64: double-precision walk (parity mode). */
-    int64_t max_steps;     /* per-walk step cap; 0 = ceil(20 / dt) */
+    int64_t max_steps;     /* per-walk step cap, 0..2^26; 0 = ceil(20 / dt).  Rounded
+                              up to an even number (walks advance two Euler steps
+                              per Philox call) */
     int32_t block_threads; /* threads per CTA (multiple of 32, <= 256); 0 = auto */
     int32_t ctas_per_sm;   /* persistent CTAs per SM; 0 = occupancy limit */
     int32_t chunk_paths;   /* paths per work item; 0 = auto */
@@ -132,6 +134,8 @@ typedef struct {
     int32_t items;       /* work items (node, path chunk) */
     int32_t grid;        /* CTAs of the persistent walk kernel */
     int32_t block;       /* threads per CTA */
+    uint64_t h2d_bytes;  /* host-to-device bytes copied by the call */
+    uint64_t d2h_bytes;  /* device-to-host bytes copied by the call */
 } sdd_stats;
 
 /* Create a context on the current CUDA device and copy the model to it.

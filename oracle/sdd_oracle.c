@@ -40,7 +40,7 @@
  * the 64-bit seed, counter = (n>>1, r, node, 0) for the normals of step n
  * (words 0,1 for even n, words 2,3 for odd n) and (n, r, node, 1) word 0 for
  * the bridge uniform of step n.  A 32-bit word w becomes a uniform in (0,1)
- * by u = (w + 1/2) 2^-32 (urule 32) or u = (floor(w/2^9) + 1/2) 2^-23
+ * by u = (w + 1/2) 2^-32 (urule 32) or u = (w mod 2^23 + 1/2) 2^-23
  * (urule 23, the rule of the single-precision walk).
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -shared -fPIC.
@@ -116,7 +116,7 @@ void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint3
 double orc_uniform(uint32_t w, int urule)
 {
     if (urule == 23)
-        return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0);
+        return ((double)(w & 0x7fffffu) + 0.5) * (1.0 / 8388608.0);
     return ((double)w + 0.5) * (1.0 / 4294967296.0);
 }
 

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -70,9 +71,19 @@ struct sdd_ctx {
     cudaEvent_t items_done = nullptr;  // last copy out of h_items finished
     cudaStream_t stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // the item table last uploaded (reused when a call plans the same items)
+    std::vector<int64_t> plan_paths;
+    int plan_chunk = -1;
+    uint32_t plan_offset = 0;
+    bool plan_valid = false;
+    uint64_t last_h2d = 0;
 };
 
 namespace {
+
+// Cap on the steps of one walk: keeps the occupation power sums (up to
+// 27 x steps for four materials) inside 32 bits.
+constexpr int64_t kMaxSteps = 1ll << 26;
 
 int kmax_for(int K) { return K <= 2 ? 2 : (K <= 3 ? 3 : (K <= 4 ? 4 : 8)); }
 
@@ -233,6 +244,8 @@ struct Plan {
     std::vector<Item> items;
     std::vector<int32_t> node_item0;  // [n_nodes + 1]
     long long total_paths = 0;
+    bool cached = false;     // identical to the table already on the device
+    bool cacheable = false;  // may be reused by a later call with the same key
 };
 
 sdd_status check_call(sdd_ctx *ctx, int32_t n_nodes, const int64_t *n_paths, double dt,
@@ -247,8 +260,8 @@ sdd_status check_call(sdd_ctx *ctx, int32_t n_nodes, const int64_t *n_paths, dou
     if (cfg) {
         if (cfg->precision != SDD_FP32 && cfg->precision != SDD_FP64)
             return fail(SDD_E_ARG, "precision must be SDD_FP32 or SDD_FP64");
-        if (cfg->max_steps < 0 || cfg->max_steps > 0x7fffffffll)
-            return fail(SDD_E_ARG, "max_steps out of range");
+        if (cfg->max_steps < 0 || cfg->max_steps > kMaxSteps)
+            return fail(SDD_E_ARG, "max_steps must be in 0..2^26");
         if (cfg->block_threads != 0 &&
             (cfg->block_threads % 32 != 0 || cfg->block_threads < 32 || cfg->block_threads > 256))
             return fail(SDD_E_ARG, "block_threads must be a multiple of 32 in 32..256");
@@ -278,7 +291,8 @@ Launch choose_launch(const sdd_ctx *ctx, const sdd_config *cfg, double dt, long 
     L.f64 = cfg && cfg->precision == SDD_FP64;
     L.kmax = kmax_for(ctx->K);
     L.block = (cfg && cfg->block_threads) ? cfg->block_threads : 256;
-    int occ = L.f64 ? occupancy_f64(L.kmax, ctx->geo, L.block) : occupancy_f32(L.kmax, ctx->geo, L.block);
+    int occ = L.f64 ? occupancy_f64(L.kmax, ctx->geo, L.block)
+                    : occupancy_f32(L.kmax, ctx->geo, ctx->M.n_shapes, L.block);
     if (occ < 1) occ = 1;
     if (cfg && cfg->ctas_per_sm > 0 && cfg->ctas_per_sm < occ) occ = cfg->ctas_per_sm;
     L.grid = ctx->n_sm * occ;
@@ -292,11 +306,12 @@ Launch choose_launch(const sdd_ctx *ctx, const sdd_config *cfg, double dt, long 
     }
     L.chunk = (int)chunk;
     L.max_steps = (cfg && cfg->max_steps) ? cfg->max_steps : (int64_t)std::ceil(20.0 / dt);
-    if (L.max_steps > 0x7fffffffll) L.max_steps = 0x7fffffffll;
+    if (L.max_steps > kMaxSteps) L.max_steps = kMaxSteps;
+    L.max_steps += L.max_steps & 1;  // walks advance two steps per random-number call
     return L;
 }
 
-Plan plan_items(int32_t n_nodes, const int64_t *n_paths, int chunk, uint32_t p_offset = 0) {
+Plan plan_items(int32_t n_nodes, const int64_t *n_paths, int chunk, uint32_t p_offset) {
     Plan P;
     P.node_item0.resize(n_nodes + 1);
     for (int j = 0; j < n_nodes; ++j) {
@@ -315,6 +330,28 @@ Plan plan_items(int32_t n_nodes, const int64_t *n_paths, int chunk, uint32_t p_o
     return P;
 }
 
+// Plan the items of a call; reuse the device copy of the previous table when
+// the call has the same path counts, chunk and path offset.
+Plan plan_cached(sdd_ctx *ctx, int32_t n_nodes, const int64_t *n_paths, int chunk,
+                 uint32_t p_offset, bool cacheable) {
+    Plan P = plan_items(n_nodes, n_paths, chunk, p_offset);
+    const bool same = cacheable && ctx->plan_valid && ctx->plan_chunk == chunk &&
+                      ctx->plan_offset == p_offset && (int32_t)ctx->plan_paths.size() == n_nodes &&
+                      std::equal(ctx->plan_paths.begin(), ctx->plan_paths.end(), n_paths);
+    P.cached = same;
+    P.cacheable = cacheable;
+    if (!same) {
+        // the device table becomes valid for this key only once its upload is queued
+        ctx->plan_valid = false;
+        if (cacheable) {
+            ctx->plan_paths.assign(n_paths, n_paths + n_nodes);
+            ctx->plan_chunk = chunk;
+            ctx->plan_offset = p_offset;
+        }
+    }
+    return P;
+}
+
 WalkArgs base_args(sdd_ctx *ctx, const Launch &L, double dt, uint64_t seed) {
     WalkArgs A;
     std::memset(&A, 0, sizeof(A));
@@ -326,6 +363,10 @@ WalkArgs base_args(sdd_ctx *ctx, const Launch &L, double dt, uint64_t seed) {
     A.f_bthr = (float)(24.0 * std::log(2.0) * dt / 2.0 * 1.001);
     A.key0 = (uint32_t)(seed & 0xffffffffu);
     A.key1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        A.rk0[r] = A.key0 + (uint32_t)r * 0x9E3779B9u;
+        A.rk1[r] = A.key1 + (uint32_t)r * 0xBB67AE85u;
+    }
     A.max_steps = (uint32_t)L.max_steps;
     return A;
 }
@@ -342,19 +383,24 @@ sdd_status run(sdd_ctx *ctx, const Plan &P, const Launch &L, WalkArgs A, cudaStr
     SDD_CUDA(ctx->queue.ensure(sizeof(int32_t)));
     SDD_CUDA(ctx->err.ensure(sizeof(int32_t)));
     const size_t hbytes = ni * sizeof(Item) + (n_nodes + 1) * sizeof(int32_t);
-    if (ctx->items_done) SDD_CUDA(cudaEventSynchronize(ctx->items_done));
-    if (hbytes > ctx->h_items_cap) {
-        if (ctx->h_items) cudaFreeHost(ctx->h_items);
-        ctx->h_items = nullptr;
-        ctx->h_items_cap = 0;
-        SDD_CUDA(cudaMallocHost((void **)&ctx->h_items, hbytes + hbytes / 4 + 256));
-        ctx->h_items_cap = hbytes + hbytes / 4 + 256;
+    ctx->last_h2d = 0;
+    if (!P.cached) {
+        if (ctx->items_done) SDD_CUDA(cudaEventSynchronize(ctx->items_done));
+        if (hbytes > ctx->h_items_cap) {
+            if (ctx->h_items) cudaFreeHost(ctx->h_items);
+            ctx->h_items = nullptr;
+            ctx->h_items_cap = 0;
+            SDD_CUDA(cudaMallocHost((void **)&ctx->h_items, hbytes + hbytes / 4 + 256));
+            ctx->h_items_cap = hbytes + hbytes / 4 + 256;
+        }
+        std::memcpy(ctx->h_items, P.items.data(), ni * sizeof(Item));
+        std::memcpy(reinterpret_cast<unsigned char *>(ctx->h_items) + ni * sizeof(Item),
+                    P.node_item0.data(), (n_nodes + 1) * sizeof(int32_t));
+        SDD_CUDA(cudaMemcpyAsync(ctx->items.p, ctx->h_items, hbytes, cudaMemcpyHostToDevice, s));
+        SDD_CUDA(cudaEventRecord(ctx->items_done, s));
+        ctx->last_h2d = hbytes;
+        ctx->plan_valid = P.cacheable;
     }
-    std::memcpy(ctx->h_items, P.items.data(), ni * sizeof(Item));
-    std::memcpy(reinterpret_cast<unsigned char *>(ctx->h_items) + ni * sizeof(Item),
-                P.node_item0.data(), (n_nodes + 1) * sizeof(int32_t));
-    SDD_CUDA(cudaMemcpyAsync(ctx->items.p, ctx->h_items, hbytes, cudaMemcpyHostToDevice, s));
-    SDD_CUDA(cudaEventRecord(ctx->items_done, s));
     SDD_CUDA(cudaMemsetAsync(ctx->queue.p, 0, sizeof(int32_t), s));
     SDD_CUDA(cudaMemsetAsync(ctx->counters.p, 0, 3 * sizeof(unsigned long long), s));
     A.items = (const Item *)ctx->items.p;
@@ -474,7 +520,7 @@ sdd_status sdd_interface_values(sdd_ctx *ctx, const double *nodes_xz, const uint
     long long total = 0;
     for (int j = 0; j < n_nodes; ++j) total += n_paths[j];
     const Launch L = choose_launch(ctx, cfg, dt, total);
-    const Plan P = plan_items(n_nodes, n_paths, L.chunk);
+    const Plan P = plan_cached(ctx, n_nodes, n_paths, L.chunk, 0, true);
     cudaStream_t s = ctx->stream;
     const size_t ob = (size_t)n_nodes * ctx->E * 2 * sizeof(double);
     SDD_CUDA(ctx->nodes.ensure((size_t)n_nodes * 2 * sizeof(double)));
@@ -500,6 +546,9 @@ sdd_status sdd_interface_values(sdd_ctx *ctx, const double *nodes_xz, const uint
     float ms = 0.f;
     SDD_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
     if (stats) {
+        stats->h2d_bytes = ctx->last_h2d + (uint64_t)n_nodes * 2 * sizeof(double) +
+                           (node_ids ? (uint64_t)n_nodes * sizeof(uint32_t) : 0);
+        stats->d2h_bytes = 2 * ob + sizeof(cnt);
         stats->steps = cnt[0];
         stats->walks = cnt[1];
         stats->truncated = cnt[2];
@@ -524,7 +573,7 @@ sdd_status sdd_interface_values_device(sdd_ctx *ctx, const double *d_nodes_xz,
     long long total = 0;
     for (int j = 0; j < n_nodes; ++j) total += n_paths[j];
     const Launch L = choose_launch(ctx, cfg, dt, total);
-    const Plan P = plan_items(n_nodes, n_paths, L.chunk);
+    const Plan P = plan_cached(ctx, n_nodes, n_paths, L.chunk, 0, true);
     cudaStream_t s = (cudaStream_t)stream;
     WalkArgs A = base_args(ctx, L, dt, seed);
     A.nodes = d_nodes_xz;
@@ -551,7 +600,7 @@ sdd_status sdd_walk_records(sdd_ctx *ctx, double x0, double z0, uint32_t node_id
     st = check_nodes(ctx, xz, 1);
     if (st != SDD_OK) return st;
     const Launch L = choose_launch(ctx, cfg, dt, count);
-    const Plan P = plan_items(1, &np, L.chunk, p0);
+    const Plan P = plan_cached(ctx, 1, &np, L.chunk, p0, false);
     cudaStream_t s = ctx->stream;
     SDD_CUDA(ctx->nodes.ensure(2 * sizeof(double)));
     SDD_CUDA(ctx->node_ids.ensure(sizeof(uint32_t)));

@@ -78,6 +78,7 @@ struct WalkArgs {
     float f_c2dt;              // 2 / dt
     float f_bthr;              // bridge filter: d d' above this cannot hit
     uint32_t key0, key1;       // Philox key (seed)
+    uint32_t rk0[10], rk1[10]; // the key of each Philox round (key bumped by the Weyl constants)
     uint32_t max_steps;
     double *slots;             // [n_items][E][4]: sum re, sum im, sum re^2, sum im^2
     int32_t *item_trunc;       // [n_items] truncated walks
@@ -99,7 +100,7 @@ cudaError_t launch_walk_f32(int kmax, int geo, const ModelDev &M, const WalkArgs
 cudaError_t launch_walk_f64(int kmax, int geo, const ModelDev &M, const WalkArgs &A, int grid,
                             int block, cudaStream_t s);
 // Largest number of resident CTAs per SM for a configuration.
-int occupancy_f32(int kmax, int geo, int block);
+int occupancy_f32(int kmax, int geo, int n_shapes, int block);
 int occupancy_f64(int kmax, int geo, int block);
 size_t smem_bytes(bool f64, int kmax, int block);
 

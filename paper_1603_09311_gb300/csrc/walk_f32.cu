@@ -6,7 +6,7 @@
 // -prec-div=false -prec-sqrt=false.
 //
 // One Euler-Maruyama step of Sec. 3.1 (discretised process, kappa_i = 1):
-//   (u0, u1)  two uniforms ((w >> 9) + 1/2) 2^-23 from one Philox call,
+//   (u0, u1)  two uniforms (w mod 2^23 + 1/2) 2^-23 from one Philox call,
 //   r^2 = -2 ln(u0) dt,  beta' = beta + r (cos 2 pi u1, sin 2 pi u1),
 // then the boundary rule of the first-exit-time estimate: overshoot ->
 // theta = d / (d + |d'|) on the first wall reached; else the Brownian-bridge
@@ -20,55 +20,107 @@
 
 namespace sdd {
 
-// u = (floor(w / 2^9) + 1/2) 2^-23, exact: 1.m - (1 - 2^-24) by Sterbenz.
-__device__ __forceinline__ float uni23(uint32_t w) {
-    return __uint_as_float(0x3f800000u | (w >> 9)) - 0.99999994039535522f;
+// Uniforms of the single-precision walk: the low 23 bits of a Philox word as
+// the mantissa of a float in [1, 2); u = (w mod 2^23 + 1/2) 2^-23 exactly
+// (1.m - (1 - 2^-24), an exact difference by Sterbenz' lemma).
+__device__ __forceinline__ float one_plus(uint32_t w) {
+    return __uint_as_float((w & 0x007fffffu) | 0x3f800000u);
 }
+__device__ __forceinline__ float uni23(uint32_t w) { return one_plus(w) - 0.99999994039535522f; }
 
-template <int KMAX_, int GEO>
+// Occupation counters.  KMAX = 2: the step count of material 1.  KMAX = 3, 4:
+// power sums s_p = sum over steps of m^p (p = 1 .. KMAX-1), which determine
+// the counts of materials 1 .. KMAX-1 (a Vandermonde system, solved once at
+// the exit).  KMAX = 8: one counter per material.
+template <int KMAX>
+struct Occupancy {
+    uint32_t s[KMAX > 1 ? KMAX - 1 : 1];
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int j = 0; j < (KMAX > 1 ? KMAX - 1 : 1); ++j) s[j] = 0;
+    }
+    __device__ __forceinline__ void add(int m) {
+        const uint32_t u = (uint32_t)m;
+        if (KMAX == 2) {
+            s[0] += u;
+        } else if (KMAX == 3) {
+            s[0] += u;
+            s[1] += u * u;
+        } else if (KMAX == 4) {
+            const uint32_t u2 = u * u;
+            s[0] += u;
+            s[1] += u2;
+            s[2] += u2 * u;
+        } else {
+#pragma unroll
+            for (int j = 1; j < KMAX; ++j) s[j - 1] += (m == j) ? 1u : 0u;
+        }
+    }
+    // counts of materials 1 .. KMAX-1
+    __device__ __forceinline__ void counts(uint32_t *c) const {
+        if (KMAX == 2) {
+            c[0] = s[0];
+        } else if (KMAX == 3) {
+            // s1 = c1 + 2 c2, s2 = c1 + 4 c2
+            const uint32_t c2 = (s[1] - s[0]) >> 1;
+            c[1] = c2;
+            c[0] = s[0] - 2u * c2;
+        } else if (KMAX == 4) {
+            // s1 = c1 + 2 c2 + 3 c3, s2 = c1 + 4 c2 + 9 c3, s3 = c1 + 8 c2 + 27 c3
+            const uint32_t c3 = (s[2] - 3u * s[1] + 2u * s[0]) / 6u;
+            const uint32_t c2 = (s[1] - s[0] - 6u * c3) >> 1;
+            c[2] = c3;
+            c[1] = c2;
+            c[0] = s[0] - 2u * c2 - 3u * c3;
+        } else {
+#pragma unroll
+            for (int j = 0; j < KMAX - 1; ++j) c[j] = s[j];
+        }
+    }
+};
+
+// NS: compile-time bound on the number of shapes (GEO_SHAPES); the shape
+// loop is unrolled so every shape parameter is an immediate constant operand.
+template <int KMAX_, int GEO, int NS>
 struct WalkerF32 {
     using Real = float;
     static constexpr int KMAX = KMAX_;
 
-    float X, Z, dmin;
-    uint32_t n;
-    uint32_t cnt[KMAX > 1 ? KMAX - 1 : 1];
-    int mcur;
+    float X, Z, dmin;  // centred position, distance to the nearest wall
+    uint32_t n;        // Euler steps accepted (even at the start of iterate)
+    Occupancy<KMAX> occ;
     uint32_t nid, pre_x, pre_y;
 
     __device__ __forceinline__ static int material(const ModelDev &M, float X, float Z) {
         if (GEO == GEO_RASTER) {
+            // round(v - 1/2) = floor(v) for v = (X + hw) sx >= 0 (magic-number rounding)
             int ix = __float_as_int(fmaf(X, M.fsx, M.fox) + 12582912.0f) - 0x4B400000;
             int iz = __float_as_int(fmaf(Z, M.fsz, M.foz) + 12582912.0f) - 0x4B400000;
-            ix = min(max(ix, 0), M.nx - 1);
-            iz = min(max(iz, 0), M.nz - 1);
+            ix = min(ix, M.nx - 1);
+            iz = min(iz, M.nz - 1);
             return (int)__ldg(M.raster + iz * M.nx + ix);
         } else {
             int m = (Z >= M.fzs) ? M.bg_earth : M.bg_air;
-            for (int s = 0; s < M.n_shapes; ++s) {
-                const ShapeDev &S = M.shapes[s];
-                bool in;
-                if (S.kind == 0) {
-                    in = X >= S.f[0] && X < S.f[1] && Z >= S.f[2] && Z < S.f[3];
-                } else {
-                    in = fmaf(S.f[0], X, fmaf(S.f[1], Z, S.f[2])) >= 0.f &&
-                         fmaf(S.f[3], X, fmaf(S.f[4], Z, S.f[5])) >= 0.f &&
-                         fmaf(S.f[6], X, fmaf(S.f[7], Z, S.f[8])) >= 0.f;
+#pragma unroll
+            for (int s = 0; s < NS; ++s) {
+                if (s < M.n_shapes) {
+                    const ShapeDev &S = M.shapes[s];
+                    bool in;
+                    if (S.kind == 0) {
+                        in = X >= S.f[0] && X < S.f[1] && Z >= S.f[2] && Z < S.f[3];
+                    } else {
+                        in = fmaf(S.f[0], X, fmaf(S.f[1], Z, S.f[2])) >= 0.f &&
+                             fmaf(S.f[3], X, fmaf(S.f[4], Z, S.f[5])) >= 0.f &&
+                             fmaf(S.f[6], X, fmaf(S.f[7], Z, S.f[8])) >= 0.f;
+                    }
+                    m = in ? S.mat : m;
                 }
-                if (in) m = S.mat;
             }
             return m;
         }
     }
 
-    __device__ __forceinline__ void count(int m) {
-        if (KMAX == 2) {
-            cnt[0] += (uint32_t)m;
-        } else {
-#pragma unroll
-            for (int j = 1; j < KMAX; ++j) cnt[j - 1] += (m == j) ? 1u : 0u;
-        }
-    }
+    __device__ __forceinline__ void counts(uint32_t *c) const { occ.counts(c); }
 
     __device__ __forceinline__ void start(const ModelDev &M, const WalkArgs &A, double x0,
                                           double z0, uint32_t path, uint32_t node_id) {
@@ -76,30 +128,10 @@ struct WalkerF32 {
         Z = (float)(z0 - M.zc);
         dmin = fminf(M.fhw - fabsf(X), M.fhh - fabsf(Z));
         n = 0;
-#pragma unroll
-        for (int j = 0; j < (KMAX > 1 ? KMAX - 1 : 1); ++j) cnt[j] = 0;
-        mcur = material(M, X, Z);
+        occ.clear();
         nid = node_id;
-        pre_x = __umulhi(0xCD9E8D57u, node_id) ^ path ^ A.key0;
+        pre_x = __umulhi(0xCD9E8D57u, node_id) ^ path ^ A.rk0[0];
         pre_y = 0xCD9E8D57u * node_id;
-    }
-
-    // Exit on overshoot: theta_w = d_w / (d_w - d'_w) over the walls with
-    // d'_w <= 0, smallest first, ties to the first in left, right, top, bottom.
-    __device__ __forceinline__ void overshoot(const ModelDev &M, float Xn, float Zn,
-                                              ExitInfo<float> &ei) const {
-        const float d[4] = {X + M.fhw, M.fhw - X, Z + M.fhh, M.fhh - Z};
-        const float e[4] = {Xn + M.fhw, M.fhw - Xn, Zn + M.fhh, M.fhh - Zn};
-        float best = 2.0f;
-        int bw = 0;
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            if (e[w] <= 0.f) {
-                const float t = d[w] / (d[w] - e[w]);
-                if (t < best) { best = t; bw = w; }
-            }
-        }
-        place(M, Xn, Zn, best, bw, ei);
     }
 
     __device__ __forceinline__ void place(const ModelDev &M, float Xn, float Zn, float th, int w,
@@ -112,14 +144,32 @@ struct WalkerF32 {
         if (w == 1) ei.x = M.fhw;
         if (w == 2) ei.z = -M.fhh;
         if (w == 3) ei.z = M.fhh;
+        ei.mlast = material(M, X, Z);
     }
 
-    // Brownian-bridge test with one uniform for all walls: the walk touched
-    // wall w during the step iff 2 d_w d'_w / dt <= -ln U (smallest product).
-    __device__ __forceinline__ bool bridge(const ModelDev &M, const WalkArgs &A, uint32_t path,
-                                        float Xn, float Zn, ExitInfo<float> &ei) const {
+    // The step (X, Z) -> (Xn, Zn) came within reach of a wall.  Overshoot:
+    // theta_w = d_w / (d_w - d'_w) over the walls with d'_w <= 0, smallest
+    // first, ties to the first of left, right, top, bottom.  Both inside: the
+    // Brownian-bridge test with one uniform for all walls, hit iff
+    // 2 d_w d'_w / dt <= -ln U for the smallest product.
+    __device__ __forceinline__ bool near_wall(const ModelDev &M, const WalkArgs &A, uint32_t path,
+                                           uint32_t step, float Xn, float Zn,
+                                           ExitInfo<float> &ei) const {
         const float d[4] = {X + M.fhw, M.fhw - X, Z + M.fhh, M.fhh - Z};
         const float e[4] = {Xn + M.fhw, M.fhw - Xn, Zn + M.fhh, M.fhh - Zn};
+        if (e[0] <= 0.f || e[1] <= 0.f || e[2] <= 0.f || e[3] <= 0.f) {
+            float best = 2.0f;
+            int bw = 0;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                if (e[w] <= 0.f) {
+                    const float t = d[w] / (d[w] - e[w]);
+                    if (t < best) { best = t; bw = w; }
+                }
+            }
+            place(M, Xn, Zn, best, bw, ei);
+            return true;
+        }
         float best = d[0] * e[0];
         int bw = 0;
 #pragma unroll
@@ -128,7 +178,7 @@ struct WalkerF32 {
             if (p < best) { best = p; bw = w; }
         }
         const float es = best * A.f_c2dt;
-        const uint4 b = philox4x32_10(make_uint4(n, path, nid, 1u), A.key0, A.key1);
+        const uint4 b = philox_rk(make_uint4(step, path, nid, 1u), A.rk0, A.rk1);
         const float L = -logf(uni23(b.x));
         if (es <= L) {
             place(M, Xn, Zn, es / L, bw, ei);
@@ -137,43 +187,47 @@ struct WalkerF32 {
         return false;
     }
 
-    __device__ __forceinline__ int substep(const ModelDev &M, const WalkArgs &A, uint32_t path,
-                                           uint32_t wa, uint32_t wb, ExitInfo<float> &ei) {
-        const float u0 = uni23(wa), u1 = uni23(wb);
-        const float r = sqrtf(fmaxf(A.f_cdt * __log2f(u0), 0.f));
+    // One Euler step driven by the Philox words (wa, wb); sub = 0 or 1 within
+    // the pair.  Returns true when the walk reached the boundary.
+    __device__ __forceinline__ bool substep(const ModelDev &M, const WalkArgs &A, uint32_t path,
+                                            uint32_t wa, uint32_t wb, uint32_t sub,
+                                            ExitInfo<float> &ei) {
+        const float u0 = uni23(wa);
+        const float r = sqrtf(fmaxf(A.f_cdt * __log2f(u0), 0.f));  // sqrt(-2 ln(u0) dt)
         float sn, cs;
-        __sincosf(fmaf(u1, 6.28318530718f, -3.14159265359f), &sn, &cs);
-        // cos(2 pi u1) = -cs, sin(2 pi u1) = -sn
+        // angle 2 pi (u1 - 1/2): cos(2 pi u1) = -cs, sin(2 pi u1) = -sn
+        __sincosf(fmaf(one_plus(wb), 6.28318530718f, -9.42477796077f), &sn, &cs);
         const float Xn = fmaf(-r, cs, X);
         const float Zn = fmaf(-r, sn, Z);
         const float dn = fminf(M.fhw - fabsf(Xn), M.fhh - fabsf(Zn));
-        if (dn <= 0.f) {
-            overshoot(M, Xn, Zn, ei);
-            return 1;
-        }
         if (dmin * dn <= A.f_bthr) {
-            if (bridge(M, A, path, Xn, Zn, ei)) return 1;
+            if (near_wall(M, A, path, n + sub, Xn, Zn, ei)) {
+                ei.nocc = n + sub;
+                return true;
+            }
         }
-        const int m = material(M, Xn, Zn);
-        count(m);
+        occ.add(material(M, Xn, Zn));
         X = Xn;
         Z = Zn;
         dmin = dn;
-        mcur = m;
-        ++n;
+        return false;
+    }
+
+    // Two Euler steps from one Philox call.  0 running, 1 exited, 2 truncated
+    // (max_steps is even, so a walk is only truncated after a pair).
+    __device__ __forceinline__ int iterate(const ModelDev &M, const WalkArgs &A, uint32_t path,
+                                           ExitInfo<float> &ei) {
+        const uint4 w = philox_rk_pre(n >> 1, 0u, pre_x, pre_y, A.rk0, A.rk1);
+        if (substep(M, A, path, w.x, w.y, 0u, ei)) return 1;
+        if (substep(M, A, path, w.z, w.w, 1u, ei)) return 1;
+        n += 2;
         if (n >= A.max_steps) {
             ei.x = X; ei.z = Z; ei.th = 0.f; ei.wall = 0;
+            ei.mlast = material(M, X, Z);
+            ei.nocc = n;
             return 2;
         }
         return 0;
-    }
-
-    __device__ __forceinline__ int iterate(const ModelDev &M, const WalkArgs &A, uint32_t path,
-                                           ExitInfo<float> &ei) {
-        const uint4 w = philox4x32_10_pre(n >> 1, 0u, pre_x, pre_y, A.key0, A.key1);
-        const int r = substep(M, A, path, w.x, w.y, ei);
-        if (r) return r;
-        return substep(M, A, path, w.z, w.w, ei);
     }
 
     __device__ static void to_abs(const ModelDev &M, float X, float Z, double &x, double &z) {
@@ -238,21 +292,21 @@ struct WalkerF32 {
     }
 };
 
-template <int KMAX, int GEO>
+template <int KMAX, int GEO, int NS>
 static cudaError_t launch_one(const ModelDev &M, const WalkArgs &A, int grid, int block,
                               cudaStream_t s) {
     const size_t sm = shared_bytes<float, KMAX>(block / 32);
-    auto k = walk_kernel<WalkerF32<KMAX, GEO>>;
+    auto k = walk_kernel<WalkerF32<KMAX, GEO, NS>>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k<<<grid, block, sm, s>>>(M, A);
     return cudaGetLastError();
 }
 
-template <int KMAX, int GEO>
+template <int KMAX, int GEO, int NS>
 static int occ_one(int block) {
     const size_t sm = shared_bytes<float, KMAX>(block / 32);
-    auto k = walk_kernel<WalkerF32<KMAX, GEO>>;
+    auto k = walk_kernel<WalkerF32<KMAX, GEO, NS>>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
         return 0;
     int n = 0;
@@ -260,26 +314,32 @@ static int occ_one(int block) {
     return n;
 }
 
+// Kernel variants: materials K <= KMAX in {2, 3, 4, 8}; geometry raster, or
+// shapes with at most NS in {0, 1, 4, 16}.
+#define SDD_NS_CASES(FN, KM, ...)                                               \
+    if (geo == GEO_RASTER) return FN<KM, GEO_RASTER, 0>(__VA_ARGS__);           \
+    if (ns <= 0) return FN<KM, GEO_SHAPES, 0>(__VA_ARGS__);                     \
+    if (ns <= 1) return FN<KM, GEO_SHAPES, 1>(__VA_ARGS__);                     \
+    if (ns <= 4) return FN<KM, GEO_SHAPES, 4>(__VA_ARGS__);                     \
+    return FN<KM, GEO_SHAPES, 16>(__VA_ARGS__);
+
 #define SDD_DISPATCH(FN, ...)                                                   \
-    switch (kmax * 2 + geo) {                                                   \
-    case 4: return FN<2, GEO_SHAPES>(__VA_ARGS__);                              \
-    case 5: return FN<2, GEO_RASTER>(__VA_ARGS__);                              \
-    case 6: return FN<3, GEO_SHAPES>(__VA_ARGS__);                              \
-    case 7: return FN<3, GEO_RASTER>(__VA_ARGS__);                              \
-    case 8: return FN<4, GEO_SHAPES>(__VA_ARGS__);                              \
-    case 9: return FN<4, GEO_RASTER>(__VA_ARGS__);                              \
-    case 16: return FN<8, GEO_SHAPES>(__VA_ARGS__);                             \
-    case 17: return FN<8, GEO_RASTER>(__VA_ARGS__);                             \
+    switch (kmax) {                                                             \
+    case 2: { SDD_NS_CASES(FN, 2, __VA_ARGS__) }                                \
+    case 3: { SDD_NS_CASES(FN, 3, __VA_ARGS__) }                                \
+    case 4: { SDD_NS_CASES(FN, 4, __VA_ARGS__) }                                \
+    case 8: { SDD_NS_CASES(FN, 8, __VA_ARGS__) }                                \
     default: break;                                                             \
     }
 
 cudaError_t launch_walk_f32(int kmax, int geo, const ModelDev &M, const WalkArgs &A, int grid,
                             int block, cudaStream_t s) {
+    const int ns = M.n_shapes;
     SDD_DISPATCH(launch_one, M, A, grid, block, s)
     return cudaErrorInvalidValue;
 }
 
-int occupancy_f32(int kmax, int geo, int block) {
+int occupancy_f32(int kmax, int geo, int ns, int block) {
     SDD_DISPATCH(occ_one, block)
     return 0;
 }

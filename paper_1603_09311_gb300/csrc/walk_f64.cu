@@ -62,6 +62,11 @@ struct WalkerF64 {
         }
     }
 
+    __device__ __forceinline__ void counts(uint32_t *c) const {
+#pragma unroll
+        for (int j = 0; j < (KMAX > 1 ? KMAX - 1 : 1); ++j) c[j] = cnt[j];
+    }
+
     __device__ __forceinline__ void count(int m) {
 #pragma unroll
         for (int j = 1; j < KMAX; ++j) cnt[j - 1] += (m == j) ? 1u : 0u;
@@ -112,6 +117,8 @@ struct WalkerF64 {
                 }
             }
             place(M, x, z, xn, zn, best, bw, ei);
+            ei.mlast = mcur;
+            ei.nocc = n;
             return 1;
         }
         double best = 2.0 * d[0] * dn[0] / A.dt;
@@ -127,6 +134,8 @@ struct WalkerF64 {
             const double L = -log(uni32(b.x));
             if (best <= L) {
                 place(M, x, z, xn, zn, best / L, bw, ei);
+                ei.mlast = mcur;
+                ei.nocc = n;
                 return 1;
             }
         }
@@ -138,6 +147,8 @@ struct WalkerF64 {
         ++n;
         if (n >= A.max_steps) {
             ei.x = x; ei.z = z; ei.th = 0.0; ei.wall = 0;
+            ei.mlast = mcur;
+            ei.nocc = n;
             return 2;
         }
         return 0;

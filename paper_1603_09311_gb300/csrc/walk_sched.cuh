@@ -62,6 +62,46 @@ __device__ __forceinline__ uint4 philox4x32_10_pre(uint32_t c0, uint32_t c3, uin
     return c;
 }
 
+// 32 x 32 -> 64-bit product as one wide multiply.
+__device__ __forceinline__ void mul_wide(uint32_t a, uint32_t b, uint32_t &lo, uint32_t &hi) {
+    uint64_t p;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(b));
+    lo = (uint32_t)p;
+    hi = (uint32_t)(p >> 32);
+}
+
+// Philox4x32-10 with the ten round keys given (rk0[r] = k0 + r 0x9E3779B9,
+// rk1[r] = k1 + r 0xBB67AE85); with counter words 1..3 fixed for a walk the
+// first round's product of word 2 is precomputed (pre_x = hi ^ c1 ^ rk0[0],
+// pre_y = lo of 0xCD9E8D57 * c2).
+__device__ __forceinline__ uint4 philox_rk_pre(uint32_t c0, uint32_t c3, uint32_t pre_x,
+                                               uint32_t pre_y, const uint32_t (&rk0)[10],
+                                               const uint32_t (&rk1)[10]) {
+    uint32_t lo0, hi0;
+    mul_wide(0xD2511F53u, c0, lo0, hi0);
+    uint4 c = make_uint4(pre_x, pre_y, hi0 ^ c3 ^ rk1[0], lo0);
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        uint32_t l0, h0, l1, h1;
+        mul_wide(0xD2511F53u, c.x, l0, h0);
+        mul_wide(0xCD9E8D57u, c.z, l1, h1);
+        c = make_uint4(h1 ^ c.y ^ rk0[r], l1, h0 ^ c.w ^ rk1[r], l0);
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const uint32_t (&rk0)[10],
+                                           const uint32_t (&rk1)[10]) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t l0, h0, l1, h1;
+        mul_wide(0xD2511F53u, c.x, l0, h0);
+        mul_wide(0xCD9E8D57u, c.z, l1, h1);
+        c = make_uint4(h1 ^ c.y ^ rk0[r], l1, h0 ^ c.w ^ rk1[r], l0);
+    }
+    return c;
+}
+
 // Shared-memory layout of one CTA: model tables, then for each warp its
 // exit-record ring, its scheduler state and its lanes' FP64 sums.
 template <class Real, int KMAX>
@@ -111,6 +151,8 @@ template <class Real>
 struct ExitInfo {
     Real x, z, th;  // exit point (walker coordinates) and hit fraction
     int wall;       // 0..3
+    int mlast;      // material of the last point inside
+    uint32_t nocc;  // occupation steps (all steps but the exiting one)
 };
 
 // Scheduler kernel.  W is a walker type providing
@@ -118,7 +160,7 @@ struct ExitInfo {
 //   start(M, A, x0, z0, path, node_id)  -- begin a walk
 //   iterate(M, A, path, ExitInfo&) -> 0 running, 1 exited, 2 truncated
 //     (two Euler steps per call)
-//   fields n, cnt[KMAX-1], mcur
+//   counts(c): steps spent in materials 1..KMAX-1 (at the exit)
 //   static sample(M, T, e, x, z, th, wall, mlast, counts, dt) -> double2
 //   static to_abs(M, x, z, ax, az)
 template <class W>
@@ -314,13 +356,15 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
             R.x[slot] = ei.x;
             R.z[slot] = ei.z;
             R.th[slot] = ei.th;
-            R.meta[slot] = (uint32_t)ei.wall | ((uint32_t)w.mcur << 2) | ((uint32_t)tag << 5) |
+            R.meta[slot] = (uint32_t)ei.wall | ((uint32_t)ei.mlast << 2) | ((uint32_t)tag << 5) |
                            ((uint32_t)tr << 6);
-            R.n[slot] = w.n;
+            R.n[slot] = ei.nocc;
             R.path[slot] = path;
+            uint32_t c[KMAX > 1 ? KMAX - 1 : 1];
+            w.counts(c);
 #pragma unroll
-            for (int j = 1; j < KMAX; ++j) R.cnt[j - 1][slot] = w.cnt[j - 1];
-            S.steps[lane] += (unsigned long long)w.n + (tr ? 0ull : 1ull);
+            for (int j = 1; j < KMAX; ++j) R.cnt[j - 1][slot] = c[j - 1];
+            S.steps[lane] += (unsigned long long)ei.nocc + (tr ? 0ull : 1ull);
             active = false;
         }
         const unsigned t1 = __ballot_sync(kFull, st != 0 && tag == 1);

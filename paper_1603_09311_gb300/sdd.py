@@ -68,7 +68,8 @@ class sdd_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_uint64), ("walks", ctypes.c_uint64),
                 ("truncated", ctypes.c_uint64), ("kernel_ms", ctypes.c_double),
                 ("launches", ctypes.c_int32), ("items", ctypes.c_int32),
-                ("grid", ctypes.c_int32), ("block", ctypes.c_int32)]
+                ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64)]
 
 
 P = ctypes.POINTER

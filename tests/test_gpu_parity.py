@@ -7,7 +7,7 @@ oracle's, its exit point and hit fraction to 1e-12, and the node means to
 1e-10 relative to the largest |g| (last-ulp differences of log/sin/cos
 between the two math libraries are the only source of difference).
 
-FP32 mode (same streams, uniform rule (floor(w/2^9) + 1/2) 2^-23, FP32
+FP32 mode (same streams, uniform rule (w mod 2^23 + 1/2) 2^-23, FP32
 positions): node means within 4 combined standard errors + 1e-4 of the
 oracle's on the same streams.
 """

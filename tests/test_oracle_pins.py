@@ -38,12 +38,12 @@ def test_philox_known_answers(ctr, key, want):
 
 
 def test_uniform_rules_open_interval():
-    # (w + 1/2) 2^-32 and (floor(w/2^9) + 1/2) 2^-23: never 0 or 1
+    # (w + 1/2) 2^-32 and (w mod 2^23 + 1/2) 2^-23: never 0 or 1
     assert O.uniform(0, 32) == 2.0 ** -33
     assert O.uniform(0xFFFFFFFF, 32) == 1.0 - 2.0 ** -33
     assert O.uniform(0, 23) == 2.0 ** -24
     assert O.uniform(0xFFFFFFFF, 23) == 1.0 - 2.0 ** -24
-    assert O.uniform(511, 23) == 2.0 ** -24 and O.uniform(512, 23) == 3 * 2.0 ** -24
+    assert O.uniform(1, 23) == 3 * 2.0 ** -24 and O.uniform(1 << 23, 23) == 2.0 ** -24
 
 
 @pytest.mark.parametrize("urule", [32, 23])
