@@ -197,6 +197,40 @@ sdd_status sdd_walk_records(sdd_ctx *ctx, double x0, double z0, uint32_t node_id
                             int64_t *steps, int64_t *counts, double *exit_xzt, int32_t *wall,
                             int32_t *m_last);
 
+/* Limits of sdd_interface_values_noalloc: nodes per call, work items per call
+ * (the path chunks are widened until the items fit), and the size in bytes of
+ * the scratch array the library keeps for it on every device that loads it. */
+#define SDD_NOALLOC_MAX_NODES 4096
+#define SDD_NOALLOC_MAX_ITEMS 8192
+#define SDD_NOALLOC_SCRATCH_BYTES 8602112
+
+/* The computation of sdd_interface_values_device, for callers that must not
+ * allocate device memory -- hosts that hand out all device memory from their
+ * own arena, processes whose memory another framework's caching allocator
+ * already holds, loops that cannot afford the synchronisation of cudaMalloc
+ * and cudaFree.  It calls no cudaMalloc, cudaFree or other allocating routine:
+ * its per-call scratch (work items, partial sums, counters) is a fixed device
+ * array of SDD_NOALLOC_SCRATCH_BYTES compiled into the library, which every
+ * GPU that loads the library holds until the process exits; the context's own
+ * scratch buffers are not used.  The paper has no counterpart: this is a
+ * deployment variant of the same estimator.
+ *   Arguments and outputs as sdd_interface_values_device (ctx from
+ *   sdd_create; d_nodes_xz, d_node_ids, d_mean, d_se, d_counters device; n_paths
+ *   host; stream a cudaStream_t or NULL).
+ *   Errors: SDD_E_ARG for more than SDD_NOALLOC_MAX_NODES nodes, a request whose
+ *   work items cannot fit SDD_NOALLOC_MAX_ITEMS, or a context created on another
+ *   device than the current one; the checks of sdd_interface_values_device.
+ * The first call on a device looks up the array's device address (set-up); make
+ * that first call before any stream capture.  All calls share the one array,
+ * which keeps the last call's contents (each call clears what must start at
+ * zero): calls that overlap on the GPU -- on two streams or from two host
+ * threads -- race and must be ordered by the caller. */
+sdd_status sdd_interface_values_noalloc(sdd_ctx *ctx, const double *d_nodes_xz,
+                                        const uint32_t *d_node_ids, int32_t n_nodes,
+                                        const int64_t *n_paths, double dt, uint64_t seed,
+                                        const sdd_config *cfg, double *d_mean, double *d_se,
+                                        uint64_t *d_counters, void *stream);
+
 /* Number of evaluations and materials of the context's model. */
 int32_t sdd_n_eval(const sdd_ctx *ctx);
 int32_t sdd_n_materials(const sdd_ctx *ctx);

@@ -633,3 +633,148 @@ sdd_status sdd_walk_records(sdd_ctx *ctx, double x0, double z0, uint32_t node_id
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Entry point that allocates nothing (sdd_interface_values_noalloc).
+//
+// Some callers cannot call cudaMalloc: hosts that hand out all device memory
+// from their own fixed arena, processes whose device memory is already
+// reserved by another framework's caching allocator, and latency-critical
+// loops that cannot afford the device-wide synchronisation cudaMalloc and
+// cudaFree may imply.  For them the per-call scratch of the walk -- work-item
+// table, per-item partial sums, counters -- lives in this file-scope device
+// array, which every GPU that loads the library holds until the process
+// exits.  Every call shares it, so calls that overlap on the GPU (on
+// different streams, or from different host threads) race; the array keeps
+// the last call's contents and each call clears what must start at zero.
+
+namespace {
+
+constexpr size_t kNaItems = SDD_NOALLOC_MAX_ITEMS;
+constexpr size_t kNaNodes = SDD_NOALLOC_MAX_NODES;
+// layout (bytes, each part 256-aligned)
+constexpr size_t kNaOffItems = 0;
+constexpr size_t kNaOffNodeItem0 = kNaOffItems + kNaItems * sizeof(Item);
+constexpr size_t kNaOffPaths = kNaOffNodeItem0 + ((kNaNodes + 1) * 4 + 255) / 256 * 256;
+constexpr size_t kNaOffTrunc = kNaOffPaths + kNaNodes * 8;
+constexpr size_t kNaOffCount = kNaOffTrunc + kNaItems * 4;
+constexpr size_t kNaOffSlots = kNaOffCount + 256;  // counters (3 x u64), queue, error
+constexpr size_t kNaBytes = kNaOffSlots + kNaItems * (size_t)kMaxE * 4 * sizeof(double);
+static_assert(kNaBytes == SDD_NOALLOC_SCRATCH_BYTES, "scratch size differs from sdd.h");
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
+
+// Device address of g_noalloc_scratch per device, looked up once per device
+// with that device current (the name is only a host-side stand-in).
+constexpr int kNaMaxDevices = 64;
+unsigned char *g_noalloc_ptr[kNaMaxDevices] = {nullptr};
+
+sdd_status noalloc_scratch(int device, unsigned char **out) {
+    if (device < 0 || device >= kNaMaxDevices) return fail(SDD_E_UNSUPPORTED, "device id too large");
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_ptr[device] = static_cast<unsigned char *>(p);
+    }
+    *out = g_noalloc_ptr[device];
+    return SDD_OK;
+}
+
+// Work-item table of the no-allocation call, built on the device from the
+// per-node path counts in the scratch array (one CTA).
+__global__ void noalloc_plan_kernel(int n_nodes, int chunk) {
+    Item *items = reinterpret_cast<Item *>(g_noalloc_scratch + kNaOffItems);
+    int32_t *node_item0 = reinterpret_cast<int32_t *>(g_noalloc_scratch + kNaOffNodeItem0);
+    const int64_t *n_paths = reinterpret_cast<const int64_t *>(g_noalloc_scratch + kNaOffPaths);
+    if (threadIdx.x == 0) {
+        int32_t acc = 0;
+        for (int j = 0; j < n_nodes; ++j) {
+            node_item0[j] = acc;
+            acc += (int32_t)((n_paths[j] + chunk - 1) / chunk);
+        }
+        node_item0[n_nodes] = acc;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n_nodes; j += blockDim.x) {
+        int32_t it = node_item0[j];
+        for (int64_t p = 0; p < n_paths[j]; p += chunk, ++it) {
+            Item I;
+            I.node = j;
+            I.path0 = (uint32_t)p;
+            I.count = (int32_t)(n_paths[j] - p < chunk ? n_paths[j] - p : chunk);
+            I.pad = 0;
+            items[it] = I;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" sdd_status sdd_interface_values_noalloc(sdd_ctx *ctx, const double *d_nodes_xz,
+                                                   const uint32_t *d_node_ids, int32_t n_nodes,
+                                                   const int64_t *n_paths, double dt,
+                                                   uint64_t seed, const sdd_config *cfg,
+                                                   double *d_mean, double *d_se,
+                                                   uint64_t *d_counters, void *stream) {
+    sdd_status st = check_call(ctx, n_nodes, n_paths, dt, cfg);
+    if (st != SDD_OK) return st;
+    if (n_nodes == 0) return SDD_OK;
+    if (!d_nodes_xz || !d_mean || !d_se) return fail(SDD_E_ARG, "d_nodes_xz, d_mean and d_se must not be NULL");
+    if ((size_t)n_nodes > kNaNodes)
+        return fail(SDD_E_ARG, "sdd_interface_values_noalloc takes at most SDD_NOALLOC_MAX_NODES (" +
+                                   std::to_string(kNaNodes) + ") nodes per call");
+    int device = -1;
+    SDD_CUDA(cudaGetDevice(&device));
+    if (device != ctx->device) return fail(SDD_E_ARG, "the context's device is not the current device");
+    unsigned char *base = nullptr;
+    st = noalloc_scratch(device, &base);
+    if (st != SDD_OK) return st;
+
+    long long total = 0;
+    for (int j = 0; j < n_nodes; ++j) total += n_paths[j];
+    Launch L = choose_launch(ctx, cfg, dt, total);
+    // widen the chunks until the work items fit the scratch array
+    long long chunk = L.chunk;
+    const long long room = (long long)kNaItems - n_nodes;
+    if (chunk * room < total) chunk = (total + room - 1) / room;
+    long long n_items = 0;
+    for (int j = 0; j < n_nodes; ++j) n_items += (n_paths[j] + chunk - 1) / chunk;
+    if (n_items > (long long)kNaItems || chunk > 0x7fffffffll)
+        return fail(SDD_E_ARG, "request does not fit the no-allocation scratch limits");
+    L.chunk = (int)chunk;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    SDD_CUDA(cudaMemcpyAsync(base + kNaOffPaths, n_paths, (size_t)n_nodes * sizeof(int64_t),
+                             cudaMemcpyHostToDevice, s));
+    SDD_CUDA(cudaMemsetAsync(base + kNaOffCount, 0, 256, s));
+    noalloc_plan_kernel<<<1, 256, 0, s>>>(n_nodes, L.chunk);
+    SDD_CUDA(cudaGetLastError());
+
+    WalkArgs A = base_args(ctx, L, dt, seed);
+    A.nodes = d_nodes_xz;
+    A.node_ids = d_node_ids;
+    A.items = reinterpret_cast<const Item *>(base + kNaOffItems);
+    A.n_items = (int32_t)n_items;
+    A.slots = reinterpret_cast<double *>(base + kNaOffSlots);
+    A.item_trunc = reinterpret_cast<int32_t *>(base + kNaOffTrunc);
+    A.counters = reinterpret_cast<unsigned long long *>(base + kNaOffCount);
+    A.queue = reinterpret_cast<int32_t *>(base + kNaOffCount + 3 * sizeof(unsigned long long));
+    A.error = A.queue + 1;
+    const int warps_per_cta = L.block / 32;
+    int grid = L.grid;
+    const int need = (int)((n_items + warps_per_cta - 1) / warps_per_cta);
+    if (grid > need) grid = need;
+    cudaError_t e = L.f64 ? launch_walk_f64(L.kmax, ctx->geo, ctx->M, A, grid, L.block, s)
+                          : launch_walk_f32(L.kmax, ctx->geo, ctx->M, A, grid, L.block, s);
+    if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch");
+    const int nt = n_nodes * ctx->E;
+    reduce_kernel<<<(nt + 127) / 128, 128, 0, s>>>(
+        A.slots, A.item_trunc, A.items, reinterpret_cast<const int32_t *>(base + kNaOffNodeItem0),
+        n_nodes, ctx->E, d_mean, d_se);
+    SDD_CUDA(cudaGetLastError());
+    if (d_counters)
+        SDD_CUDA(cudaMemcpyAsync(d_counters, A.counters, 3 * sizeof(uint64_t),
+                                 cudaMemcpyDeviceToDevice, s));
+    return SDD_OK;
+}

@@ -87,6 +87,10 @@ SIGNATURES = [
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_int64),
       ctypes.c_double, ctypes.c_uint64, P(sdd_config), ctypes.c_void_p, ctypes.c_void_p,
       ctypes.c_void_p, ctypes.c_void_p]),
+    ("sdd_interface_values_noalloc", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_int64),
+      ctypes.c_double, ctypes.c_uint64, P(sdd_config), ctypes.c_void_p, ctypes.c_void_p,
+      ctypes.c_void_p, ctypes.c_void_p]),
     ("sdd_walk_records", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32,
       ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, P(sdd_config), P(ctypes.c_int64),
@@ -246,6 +250,26 @@ def sdd_interface_values_device(ctx: Context, d_nodes_ptr: int, n_nodes: int, n_
         ctypes.c_void_p(d_counters_ptr or None), ctypes.c_void_p(stream or None))
     if st != SDD_OK:
         raise SddError(st, "sdd_interface_values_device")
+    return st
+
+
+def sdd_interface_values_noalloc(ctx: Context, d_nodes_ptr: int, n_nodes: int, n_paths, dt: float,
+                                 seed: int, d_mean_ptr: int, d_se_ptr: int, d_node_ids_ptr: int = 0,
+                                 d_counters_ptr: int = 0, stream: int = 0,
+                                 config: sdd_config | None = None, **cfg) -> int:
+    """Like sdd_interface_values_device, for callers that cannot allocate
+    device memory: the library's fixed scratch array replaces its per-call
+    allocations (at most SDD_NOALLOC_MAX_NODES nodes per call; calls that
+    overlap on the GPU race)."""
+    npth = _paths(n_paths, n_nodes)
+    c = config if config is not None else make_config(**cfg)
+    st = lib().sdd_interface_values_noalloc(
+        ctx.handle, ctypes.c_void_p(d_nodes_ptr), ctypes.c_void_p(d_node_ids_ptr or None), n_nodes,
+        npth.ctypes.data_as(P(ctypes.c_int64)), float(dt), int(seed) & (2 ** 64 - 1),
+        ctypes.byref(c), ctypes.c_void_p(d_mean_ptr), ctypes.c_void_p(d_se_ptr),
+        ctypes.c_void_p(d_counters_ptr or None), ctypes.c_void_p(stream or None))
+    if st != SDD_OK:
+        raise SddError(st, "sdd_interface_values_noalloc")
     return st
 
 
