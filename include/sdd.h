@@ -151,9 +151,12 @@ void sdd_destroy(sdd_ctx *ctx);
  *   node_ids  host, [n_nodes] RNG node ids, or NULL for 0..n_nodes-1
  *   n_paths   host, [n_nodes] walks per node, 1 .. 2^31-1
  *   dt        Euler time step (standard Brownian clock), > 0
- *   seed      64-bit Philox4x32-10 key; walk (node id i, path r) uses
- *             counters (n>>1, r, i, 0) for its normals and (n, r, i, 1) for
- *             its bridge uniforms, so results do not depend on the launch
+ *   seed      64-bit Philox4x32-10 key; step n of walk (node id i, path r)
+ *             uses the two words of counter (n>>1, r, i, 0) (words 0,1 for even
+ *             n, 2,3 for odd n): SDD_FP32 takes its two normals from their low
+ *             23 bits and its bridge uniform from the other 18 bits; SDD_FP64
+ *             takes its normals from the full words and its bridge uniform
+ *             from counter (n, r, i, 1).  Results do not depend on the launch
  *   cfg       options, or NULL for defaults
  *   mean      host out, [n_nodes][n_eval][2] (re, im) sample means
  *   se        host out, [n_nodes][n_eval][2] standard errors of re and im

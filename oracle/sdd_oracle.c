@@ -37,11 +37,13 @@
  *      Carlo estimator of Sec. 3.1).
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key =
- * the 64-bit seed, counter = (n>>1, r, node, 0) for the normals of step n
- * (words 0,1 for even n, words 2,3 for odd n) and (n, r, node, 1) word 0 for
- * the bridge uniform of step n.  A 32-bit word w becomes a uniform in (0,1)
- * by u = (w + 1/2) 2^-32 (urule 32) or u = (w mod 2^23 + 1/2) 2^-23
- * (urule 23, the rule of the single-precision walk).
+ * the 64-bit seed, counter = (n>>1, r, node, 0) for the two words (a, b) of
+ * step n (words 0,1 for even n, words 2,3 for odd n).  urule 32 (the
+ * double-precision stream): normals from u = (w + 1/2) 2^-32 of a and b, the
+ * bridge uniform from word 0 of counter (n, r, node, 1).  urule 23 (the
+ * single-precision stream): normals from u = (w mod 2^23 + 1/2) 2^-23, the
+ * bridge uniform from the remaining 18 bits, ((a>>23) 2^9 + (b>>23) + 1/2) 2^-18.
+ * The paper fixes no random-number mapping; these are the library's.
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -shared -fPIC.
  */
@@ -126,16 +128,24 @@ static void seed_key(uint64_t seed, uint32_t key[2])
     key[1] = (uint32_t)(seed >> 32);
 }
 
-/* The two standard normals driving step n of walk (node, path). */
-void orc_normals(uint64_t seed, uint32_t node, uint32_t path, int64_t n, int urule,
-                 double *w0, double *w1)
+/* The two Philox words of step n of walk (node, path). */
+static void step_words(uint64_t seed, uint32_t node, uint32_t path, int64_t n, uint32_t *a,
+                       uint32_t *b)
 {
     uint32_t key[2], ctr[4], x[4];
     seed_key(seed, key);
     ctr[0] = (uint32_t)(n >> 1); ctr[1] = path; ctr[2] = node; ctr[3] = 0;
     orc_philox4x32_10(ctr, key, x);
-    uint32_t a = (n & 1) ? x[2] : x[0];
-    uint32_t b = (n & 1) ? x[3] : x[1];
+    *a = (n & 1) ? x[2] : x[0];
+    *b = (n & 1) ? x[3] : x[1];
+}
+
+/* The two standard normals driving step n of walk (node, path). */
+void orc_normals(uint64_t seed, uint32_t node, uint32_t path, int64_t n, int urule,
+                 double *w0, double *w1)
+{
+    uint32_t a, b;
+    step_words(seed, node, path, n, &a, &b);
     double u0 = orc_uniform(a, urule);
     double u1 = orc_uniform(b, urule);
     /* Box-Muller (1958): radius sqrt(-2 ln u0), angle 2 pi u1 */
@@ -145,9 +155,17 @@ void orc_normals(uint64_t seed, uint32_t node, uint32_t path, int64_t n, int uru
     *w1 = rho * sin(ang);
 }
 
-/* The uniform U_gamma of the Brownian-bridge test of step n. */
+/* The uniform U_gamma of the Brownian-bridge test of step n.  urule 23: the
+ * 18 bits of the step's two words that its normals leave unused,
+ * U = ((a >> 23) * 2^9 + (b >> 23) + 1/2) 2^-18.  urule 32: word 0 of the
+ * Philox call with counter (n, path, node, 1). */
 double orc_bridge_uniform(uint64_t seed, uint32_t node, uint32_t path, int64_t n, int urule)
 {
+    if (urule == 23) {
+        uint32_t a, b;
+        step_words(seed, node, path, n, &a, &b);
+        return ((double)(((a >> 23) << 9) | (b >> 23)) + 0.5) * (1.0 / 262144.0);
+    }
     uint32_t key[2], ctr[4], x[4];
     seed_key(seed, key);
     ctr[0] = (uint32_t)n; ctr[1] = path; ctr[2] = node; ctr[3] = 1;

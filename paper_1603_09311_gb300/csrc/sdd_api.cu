@@ -184,7 +184,12 @@ void build_model(const sdd_model_desc *m, ModelDev &M) {
                 }
             }
         }
+        if (m->n_shapes == 0) M.gcode = GC_LAYER;
+        else if (m->n_shapes == 1) M.gcode = m->shapes[0].kind == SDD_SHAPE_RECT ? GC_RECT1 : GC_TRI1;
+        else if (m->n_shapes <= 4) M.gcode = GC_SHAPES4;
+        else M.gcode = GC_SHAPES16;
     } else {
+        M.gcode = GC_RASTER;
         M.nx = m->nx;
         M.nz = m->nz;
         M.sx = (double)m->nx / (d.x_max - d.x_min);
@@ -292,7 +297,7 @@ Launch choose_launch(const sdd_ctx *ctx, const sdd_config *cfg, double dt, long 
     L.kmax = kmax_for(ctx->K);
     L.block = (cfg && cfg->block_threads) ? cfg->block_threads : 256;
     int occ = L.f64 ? occupancy_f64(L.kmax, ctx->geo, L.block)
-                    : occupancy_f32(L.kmax, ctx->geo, ctx->M.n_shapes, L.block);
+                    : occupancy_f32(L.kmax, ctx->M.gcode, L.block);
     if (occ < 1) occ = 1;
     if (cfg && cfg->ctas_per_sm > 0 && cfg->ctas_per_sm < occ) occ = cfg->ctas_per_sm;
     L.grid = ctx->n_sm * occ;
@@ -359,8 +364,9 @@ WalkArgs base_args(sdd_ctx *ctx, const Launch &L, double dt, uint64_t seed) {
     A.sdt = std::sqrt(dt);
     A.f_cdt = (float)(-2.0 * std::log(2.0) * dt);
     A.f_c2dt = (float)(2.0 / dt);
-    // 2 d d' / dt <= -ln U <= 24 ln 2 for U >= 2^-24; 1e-3 margin for rounding
-    A.f_bthr = (float)(24.0 * std::log(2.0) * dt / 2.0 * 1.001);
+    // single-precision bridge uniforms are >= 2^-19, so a hit needs
+    // 2 d d' / dt <= -ln U <= 19 ln 2; 1e-3 margin for rounding
+    A.f_bthr = (float)(19.0 * std::log(2.0) * dt / 2.0 * 1.001);
     A.key0 = (uint32_t)(seed & 0xffffffffu);
     A.key1 = (uint32_t)(seed >> 32);
     for (int r = 0; r < 10; ++r) {

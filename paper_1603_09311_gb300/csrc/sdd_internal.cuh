@@ -17,6 +17,13 @@ constexpr int kRing = 64;  // exit records buffered per warp
 
 enum Geo : int { GEO_SHAPES = 0, GEO_RASTER = 1 };
 
+// Material-lookup programs of the single-precision walk, chosen per model so
+// that the common cases run without loops or branches: the layered
+// background alone, exactly one rectangle, exactly one triangle, up to 4 or
+// up to 16 shapes (unrolled, guarded), or the int8 raster.
+enum GeoCode : int { GC_LAYER = 0, GC_RECT1 = 1, GC_TRI1 = 2, GC_SHAPES4 = 3, GC_SHAPES16 = 4,
+                     GC_RASTER = 5 };
+
 // One work item: paths [path0, path0 + count) of node `node`.
 struct Item {
     int32_t node;
@@ -51,6 +58,7 @@ struct ModelDev {
     int32_t K, E, Epad;
     int32_t bg_air, bg_earth;
     int32_t n_shapes;
+    int32_t gcode;  // GeoCode of the model
     ShapeDev shapes[kMaxShapes];
     const int8_t *raster;
     int32_t nx, nz;
@@ -76,7 +84,7 @@ struct WalkArgs {
     double sdt;                // sqrt(dt)
     float f_cdt;               // -2 ln(2) dt: squared step radius = f_cdt * log2(u0)
     float f_c2dt;              // 2 / dt
-    float f_bthr;              // bridge filter: d d' above this cannot hit
+    float f_bthr;              // bridge filter: d d' above this cannot hit (single precision)
     uint32_t key0, key1;       // Philox key (seed)
     uint32_t rk0[10], rk1[10]; // the key of each Philox round (key bumped by the Weyl constants)
     uint32_t max_steps;
@@ -100,7 +108,7 @@ cudaError_t launch_walk_f32(int kmax, int geo, const ModelDev &M, const WalkArgs
 cudaError_t launch_walk_f64(int kmax, int geo, const ModelDev &M, const WalkArgs &A, int grid,
                             int block, cudaStream_t s);
 // Largest number of resident CTAs per SM for a configuration.
-int occupancy_f32(int kmax, int geo, int n_shapes, int block);
+int occupancy_f32(int kmax, int gcode, int block);
 int occupancy_f64(int kmax, int geo, int block);
 size_t smem_bytes(bool f64, int kmax, int block);
 

@@ -10,8 +10,9 @@
 //   r^2 = -2 ln(u0) dt,  beta' = beta + r (cos 2 pi u1, sin 2 pi u1),
 // then the boundary rule of the first-exit-time estimate: overshoot ->
 // theta = d / (d + |d'|) on the first wall reached; else the Brownian-bridge
-// test 2 d d' / dt <= -ln U_gamma with one uniform per step; else the step's
-// time goes to the material of beta' (Sec. 3.1, no regime change for TE).
+// test 2 d d' / dt <= -ln U_gamma with one uniform per step (18 spare bits of
+// the step's Philox words); else the step's time goes to the material of
+// beta' (Sec. 3.1, no regime change for TE).
 //
 // The walk runs in centred coordinates X = x - xc, Z = z - zc, so the
 // distance to the nearer wall of each pair is h - |X|.  Two steps share one
@@ -79,9 +80,9 @@ struct Occupancy {
     }
 };
 
-// NS: compile-time bound on the number of shapes (GEO_SHAPES); the shape
-// loop is unrolled so every shape parameter is an immediate constant operand.
-template <int KMAX_, int GEO, int NS>
+// GC: the material-lookup program (GeoCode).  Shape parameters are read
+// with compile-time indices, so every one is an immediate constant operand.
+template <int KMAX_, int GC>
 struct WalkerF32 {
     using Real = float;
     static constexpr int KMAX = KMAX_;
@@ -91,33 +92,39 @@ struct WalkerF32 {
     Occupancy<KMAX> occ;
     uint32_t nid, pre_x, pre_y;
 
+    __device__ __forceinline__ static bool in_rect(const ShapeDev &S, float X, float Z) {
+        return X >= S.f[0] && X < S.f[1] && Z >= S.f[2] && Z < S.f[3];
+    }
+    __device__ __forceinline__ static bool in_tri(const ShapeDev &S, float X, float Z) {
+        return fmaf(S.f[0], X, fmaf(S.f[1], Z, S.f[2])) >= 0.f &&
+               fmaf(S.f[3], X, fmaf(S.f[4], Z, S.f[5])) >= 0.f &&
+               fmaf(S.f[6], X, fmaf(S.f[7], Z, S.f[8])) >= 0.f;
+    }
+
     __device__ __forceinline__ static int material(const ModelDev &M, float X, float Z) {
-        if (GEO == GEO_RASTER) {
+        if (GC == GC_RASTER) {
             // round(v - 1/2) = floor(v) for v = (X + hw) sx >= 0 (magic-number rounding)
             int ix = __float_as_int(fmaf(X, M.fsx, M.fox) + 12582912.0f) - 0x4B400000;
             int iz = __float_as_int(fmaf(Z, M.fsz, M.foz) + 12582912.0f) - 0x4B400000;
             ix = min(ix, M.nx - 1);
             iz = min(iz, M.nz - 1);
             return (int)__ldg(M.raster + iz * M.nx + ix);
-        } else {
-            int m = (Z >= M.fzs) ? M.bg_earth : M.bg_air;
-#pragma unroll
-            for (int s = 0; s < NS; ++s) {
-                if (s < M.n_shapes) {
-                    const ShapeDev &S = M.shapes[s];
-                    bool in;
-                    if (S.kind == 0) {
-                        in = X >= S.f[0] && X < S.f[1] && Z >= S.f[2] && Z < S.f[3];
-                    } else {
-                        in = fmaf(S.f[0], X, fmaf(S.f[1], Z, S.f[2])) >= 0.f &&
-                             fmaf(S.f[3], X, fmaf(S.f[4], Z, S.f[5])) >= 0.f &&
-                             fmaf(S.f[6], X, fmaf(S.f[7], Z, S.f[8])) >= 0.f;
-                    }
-                    m = in ? S.mat : m;
-                }
-            }
-            return m;
         }
+        const int m = (Z >= M.fzs) ? M.bg_earth : M.bg_air;
+        if (GC == GC_LAYER) return m;
+        if (GC == GC_RECT1) return in_rect(M.shapes[0], X, Z) ? M.shapes[0].mat : m;
+        if (GC == GC_TRI1) return in_tri(M.shapes[0], X, Z) ? M.shapes[0].mat : m;
+        constexpr int NS = GC == GC_SHAPES4 ? 4 : kMaxShapes;
+        int r = m;
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            if (s < M.n_shapes) {
+                const ShapeDev &S = M.shapes[s];
+                const bool in = S.kind == 0 ? in_rect(S, X, Z) : in_tri(S, X, Z);
+                r = in ? S.mat : r;
+            }
+        }
+        return r;
     }
 
     __device__ __forceinline__ void counts(uint32_t *c) const { occ.counts(c); }
@@ -151,10 +158,12 @@ struct WalkerF32 {
     // theta_w = d_w / (d_w - d'_w) over the walls with d'_w <= 0, smallest
     // first, ties to the first of left, right, top, bottom.  Both inside: the
     // Brownian-bridge test with one uniform for all walls, hit iff
-    // 2 d_w d'_w / dt <= -ln U for the smallest product.
-    __device__ __forceinline__ bool near_wall(const ModelDev &M, const WalkArgs &A, uint32_t path,
-                                           uint32_t step, float Xn, float Zn,
-                                           ExitInfo<float> &ei) const {
+    // 2 d_w d'_w / dt <= -ln U for the smallest product.  U is made of the 18
+    // bits of the step's two Philox words that the normals leave unused:
+    // U = (high 9 bits of wa : high 9 bits of wb + 1/2) 2^-18.
+    __device__ __forceinline__ bool near_wall(const ModelDev &M, const WalkArgs &A, float Xn,
+                                              float Zn, uint32_t wa, uint32_t wb,
+                                              ExitInfo<float> &ei) const {
         const float d[4] = {X + M.fhw, M.fhw - X, Z + M.fhh, M.fhh - Z};
         const float e[4] = {Xn + M.fhw, M.fhw - Xn, Zn + M.fhh, M.fhh - Zn};
         if (e[0] <= 0.f || e[1] <= 0.f || e[2] <= 0.f || e[3] <= 0.f) {
@@ -178,8 +187,8 @@ struct WalkerF32 {
             if (p < best) { best = p; bw = w; }
         }
         const float es = best * A.f_c2dt;
-        const uint4 b = philox_rk(make_uint4(step, path, nid, 1u), A.rk0, A.rk1);
-        const float L = -logf(uni23(b.x));
+        const uint32_t u18 = ((wa >> 23) << 9) | (wb >> 23);
+        const float L = -logf(fmaf((float)u18, 3.814697265625e-06f, 1.9073486328125e-06f));
         if (es <= L) {
             place(M, Xn, Zn, es / L, bw, ei);
             return true;
@@ -201,7 +210,7 @@ struct WalkerF32 {
         const float Zn = fmaf(-r, sn, Z);
         const float dn = fminf(M.fhw - fabsf(Xn), M.fhh - fabsf(Zn));
         if (dmin * dn <= A.f_bthr) {
-            if (near_wall(M, A, path, n + sub, Xn, Zn, ei)) {
+            if (near_wall(M, A, Xn, Zn, wa, wb, ei)) {
                 ei.nocc = n + sub;
                 return true;
             }
@@ -292,21 +301,21 @@ struct WalkerF32 {
     }
 };
 
-template <int KMAX, int GEO, int NS>
+template <int KMAX, int GC>
 static cudaError_t launch_one(const ModelDev &M, const WalkArgs &A, int grid, int block,
                               cudaStream_t s) {
     const size_t sm = shared_bytes<float, KMAX>(block / 32);
-    auto k = walk_kernel<WalkerF32<KMAX, GEO, NS>>;
+    auto k = walk_kernel<WalkerF32<KMAX, GC>>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     k<<<grid, block, sm, s>>>(M, A);
     return cudaGetLastError();
 }
 
-template <int KMAX, int GEO, int NS>
+template <int KMAX, int GC>
 static int occ_one(int block) {
     const size_t sm = shared_bytes<float, KMAX>(block / 32);
-    auto k = walk_kernel<WalkerF32<KMAX, GEO, NS>>;
+    auto k = walk_kernel<WalkerF32<KMAX, GC>>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
         return 0;
     int n = 0;
@@ -314,32 +323,35 @@ static int occ_one(int block) {
     return n;
 }
 
-// Kernel variants: materials K <= KMAX in {2, 3, 4, 8}; geometry raster, or
-// shapes with at most NS in {0, 1, 4, 16}.
-#define SDD_NS_CASES(FN, KM, ...)                                               \
-    if (geo == GEO_RASTER) return FN<KM, GEO_RASTER, 0>(__VA_ARGS__);           \
-    if (ns <= 0) return FN<KM, GEO_SHAPES, 0>(__VA_ARGS__);                     \
-    if (ns <= 1) return FN<KM, GEO_SHAPES, 1>(__VA_ARGS__);                     \
-    if (ns <= 4) return FN<KM, GEO_SHAPES, 4>(__VA_ARGS__);                     \
-    return FN<KM, GEO_SHAPES, 16>(__VA_ARGS__);
-
-#define SDD_DISPATCH(FN, ...)                                                   \
-    switch (kmax) {                                                             \
-    case 2: { SDD_NS_CASES(FN, 2, __VA_ARGS__) }                                \
-    case 3: { SDD_NS_CASES(FN, 3, __VA_ARGS__) }                                \
-    case 4: { SDD_NS_CASES(FN, 4, __VA_ARGS__) }                                \
-    case 8: { SDD_NS_CASES(FN, 8, __VA_ARGS__) }                                \
+// Kernel variants: materials K <= KMAX in {2, 3, 4, 8} x the six lookup programs.
+#define SDD_GC_CASES(FN, KM, ...)                                               \
+    switch (gcode) {                                                            \
+    case GC_LAYER: return FN<KM, GC_LAYER>(__VA_ARGS__);                        \
+    case GC_RECT1: return FN<KM, GC_RECT1>(__VA_ARGS__);                        \
+    case GC_TRI1: return FN<KM, GC_TRI1>(__VA_ARGS__);                          \
+    case GC_SHAPES4: return FN<KM, GC_SHAPES4>(__VA_ARGS__);                    \
+    case GC_SHAPES16: return FN<KM, GC_SHAPES16>(__VA_ARGS__);                  \
+    case GC_RASTER: return FN<KM, GC_RASTER>(__VA_ARGS__);                      \
     default: break;                                                             \
     }
 
-cudaError_t launch_walk_f32(int kmax, int geo, const ModelDev &M, const WalkArgs &A, int grid,
+#define SDD_DISPATCH(FN, ...)                                                   \
+    switch (kmax) {                                                             \
+    case 2: SDD_GC_CASES(FN, 2, __VA_ARGS__) break;                             \
+    case 3: SDD_GC_CASES(FN, 3, __VA_ARGS__) break;                             \
+    case 4: SDD_GC_CASES(FN, 4, __VA_ARGS__) break;                             \
+    case 8: SDD_GC_CASES(FN, 8, __VA_ARGS__) break;                             \
+    default: break;                                                             \
+    }
+
+cudaError_t launch_walk_f32(int kmax, int /*geo*/, const ModelDev &M, const WalkArgs &A, int grid,
                             int block, cudaStream_t s) {
-    const int ns = M.n_shapes;
+    const int gcode = M.gcode;
     SDD_DISPATCH(launch_one, M, A, grid, block, s)
     return cudaErrorInvalidValue;
 }
 
-int occupancy_f32(int kmax, int geo, int ns, int block) {
+int occupancy_f32(int kmax, int gcode, int block) {
     SDD_DISPATCH(occ_one, block)
     return 0;
 }

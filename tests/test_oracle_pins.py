@@ -65,9 +65,14 @@ def test_box_muller_normals_are_standard(urule):
     assert w_even != w_odd
 
 
-def test_bridge_uniform_stream_is_uniform():
-    u = np.array([O.bridge_uniform(3, 0, p, n) for p in range(40) for n in range(250)])
+@pytest.mark.parametrize("urule", [32, 23])
+def test_bridge_uniform_stream_is_uniform(urule):
+    u = np.array([O.bridge_uniform(3, 0, p, n, urule) for p in range(40) for n in range(250)])
     assert stats.kstest(u, "uniform").pvalue > 1e-4
+    assert u.min() > 0 and u.max() < 1
+    # independent of the same step's normals (23: disjoint bits of the same words)
+    z = np.array([O.normals(3, 0, p, n, urule)[0] for p in range(40) for n in range(250)])
+    assert abs(np.corrcoef(u, z)[0, 1]) < 5 / np.sqrt(len(u))
 
 
 def test_material_rules():
