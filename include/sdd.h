@@ -186,6 +186,24 @@ sdd_status sdd_interface_values_device(sdd_ctx *ctx, const double *d_nodes_xz,
                                        const sdd_config *cfg, double *d_mean, double *d_se,
                                        uint64_t *d_counters, void *stream);
 
+/* Interface-node values at a target standard error, host buffers,
+ * synchronous.  Each node first runs paths 0 .. n_pilot-1; from their sample
+ * variance it gets N = clamp(ceil(max_e (var_re + var_im) / target_se^2),
+ * n_pilot, n_max) walks in all, and paths n_pilot .. N-1 are run in a second
+ * launch.  The sums of the two phases are added in fixed order, so the result
+ * equals sdd_interface_values with n_paths = N up to FP64 summation order.
+ *   n_pilot, n_max  2 <= n_pilot <= n_max <= 2^31-1
+ *   target_se       complex standard error aimed at, sqrt(var_re + var_im)/sqrt(N)
+ *   n_used          host out, [n_nodes] N of each node, nullable
+ * Other arguments as sdd_interface_values.  A node reaching n_max may stay
+ * above target_se; compare se with target_se to count the nodes that met it. */
+sdd_status sdd_interface_values_target(sdd_ctx *ctx, const double *nodes_xz,
+                                       const uint32_t *node_ids, int32_t n_nodes,
+                                       int64_t n_pilot, int64_t n_max, double target_se,
+                                       double dt, uint64_t seed, const sdd_config *cfg,
+                                       double *mean, double *se, int64_t *n_used,
+                                       sdd_stats *stats);
+
 /* Per-path records of walks (node id, paths p0 .. p0+count-1) started at
  * (x0, z0), host buffers, synchronous -- the individual steps of Sec. 3.1
  * for comparison path by path:

@@ -188,6 +188,13 @@ void build_model(const sdd_model_desc *m, ModelDev &M) {
         else if (m->n_shapes == 1) M.gcode = m->shapes[0].kind == SDD_SHAPE_RECT ? GC_RECT1 : GC_TRI1;
         else if (m->n_shapes <= 4) M.gcode = GC_SHAPES4;
         else M.gcode = GC_SHAPES16;
+        if (M.gcode == GC_RECT1) {
+            // a vertical contact: the rectangle is the whole earth right of x0
+            const sdd_shape &S = m->shapes[0];
+            if (S.v[1] >= d.x_max && S.v[2] == 0.0 && S.v[3] >= d.z_max &&
+                (float)(S.v[1] - M.xc) >= M.fhw && (float)(S.v[3] - M.zc) >= M.fhh)
+                M.gcode = GC_CONTACT;
+        }
     } else {
         M.gcode = GC_RASTER;
         M.nx = m->nx;
@@ -243,6 +250,28 @@ __global__ void reduce_kernel(const double *__restrict__ slots, const int32_t *_
     mean[2 * t + 1] = mi;
     se[2 * t] = sqrt(vr / N);
     se[2 * t + 1] = sqrt(vi / N);
+}
+
+// Raw per-node sums (sum re, sum im, sum re^2, sum im^2 per evaluation, and the
+// number of walks that reached the boundary), items of each node in order.
+__global__ void sums_kernel(const double *__restrict__ slots, const int32_t *__restrict__ trunc,
+                            const Item *__restrict__ items, const int32_t *__restrict__ node_item0,
+                            int n_nodes, int E, double *__restrict__ sums, long long *__restrict__ nvalid) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_nodes * E) return;
+    const int j = t / E, e = t % E;
+    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    long long nv = 0;
+    for (int it = node_item0[j]; it < node_item0[j + 1]; ++it) {
+        const double *o = slots + ((size_t)it * E + e) * 4;
+        s0 += o[0]; s1 += o[1]; s2 += o[2]; s3 += o[3];
+        nv += items[it].count - trunc[it];
+    }
+    sums[4 * t + 0] = s0;
+    sums[4 * t + 1] = s1;
+    sums[4 * t + 2] = s2;
+    sums[4 * t + 3] = s3;
+    if (e == 0) nvalid[j] = nv;
 }
 
 struct Plan {
@@ -354,6 +383,26 @@ Plan plan_cached(sdd_ctx *ctx, int32_t n_nodes, const int64_t *n_paths, int chun
             ctx->plan_offset = p_offset;
         }
     }
+    return P;
+}
+
+// Items for paths [begin[j], begin[j] + count[j]) of every node.
+Plan plan_ranges(int32_t n_nodes, const int64_t *begin, const int64_t *count, int chunk) {
+    Plan P;
+    P.node_item0.resize(n_nodes + 1);
+    for (int j = 0; j < n_nodes; ++j) {
+        P.node_item0[j] = (int32_t)P.items.size();
+        for (int64_t p = 0; p < count[j]; p += chunk) {
+            Item I;
+            I.node = j;
+            I.path0 = (uint32_t)(begin[j] + p);
+            I.count = (int32_t)std::min<int64_t>(chunk, count[j] - p);
+            I.pad = 0;
+            P.items.push_back(I);
+        }
+        P.total_paths += count[j];
+    }
+    P.node_item0[n_nodes] = (int32_t)P.items.size();
     return P;
 }
 
@@ -783,4 +832,153 @@ extern "C" sdd_status sdd_interface_values_noalloc(sdd_ctx *ctx, const double *d
         SDD_CUDA(cudaMemcpyAsync(d_counters, A.counters, 3 * sizeof(uint64_t),
                                  cudaMemcpyDeviceToDevice, s));
     return SDD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Adaptive path counts (sdd_interface_values_target).
+
+namespace {
+
+// Walks of one phase, and the raw per-node sums of the phase on the host.
+sdd_status run_phase(sdd_ctx *ctx, const Plan &P, const Launch &L, const WalkArgs &A0,
+                     int32_t n_nodes, std::vector<double> &sums, std::vector<long long> &nvalid,
+                     unsigned long long cnt[3], float *ms) {
+    sums.assign((size_t)n_nodes * ctx->E * 4, 0.0);
+    nvalid.assign(n_nodes, 0);
+    cnt[0] = cnt[1] = cnt[2] = 0;
+    *ms = 0.f;
+    if (P.items.empty()) return SDD_OK;
+    cudaStream_t s = ctx->stream;
+    sdd_status st = run(ctx, P, L, A0, s, true, false, nullptr, nullptr, n_nodes);
+    if (st != SDD_OK) return st;
+    const size_t ni = P.items.size();
+    SDD_CUDA(ctx->mean.ensure(sums.size() * sizeof(double)));
+    SDD_CUDA(ctx->se.ensure((size_t)n_nodes * sizeof(long long)));
+    const Item *d_items = (const Item *)ctx->items.p;
+    const int32_t *d_i0 = (const int32_t *)(reinterpret_cast<unsigned char *>(ctx->items.p) + ni * sizeof(Item));
+    const int nt = n_nodes * ctx->E;
+    sums_kernel<<<(nt + 127) / 128, 128, 0, s>>>((const double *)ctx->slots.p, (const int32_t *)ctx->trunc.p,
+                                                d_items, d_i0, n_nodes, ctx->E, (double *)ctx->mean.p,
+                                                (long long *)ctx->se.p);
+    SDD_CUDA(cudaGetLastError());
+    SDD_CUDA(cudaMemcpyAsync(sums.data(), ctx->mean.p, sums.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SDD_CUDA(cudaMemcpyAsync(nvalid.data(), ctx->se.p, (size_t)n_nodes * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    SDD_CUDA(cudaMemcpyAsync(cnt, ctx->counters.p, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    SDD_CUDA(cudaStreamSynchronize(s));
+    SDD_CUDA(cudaEventElapsedTime(ms, ctx->ev0, ctx->ev1));
+    return SDD_OK;
+}
+
+// mean and standard error of each component from the raw sums
+void finish(const double *q, long long nv, double *mean, double *se) {
+    const double N = (double)nv;
+    double mr = nan(""), mi = nan(""), vr = nan(""), vi = nan("");
+    if (nv > 0) { mr = q[0] / N; mi = q[1] / N; }
+    if (nv > 1) {
+        vr = std::max((q[2] - q[0] * mr) / (N - 1.0), 0.0);
+        vi = std::max((q[3] - q[1] * mi) / (N - 1.0), 0.0);
+    }
+    mean[0] = mr; mean[1] = mi;
+    se[0] = std::sqrt(vr / N); se[1] = std::sqrt(vi / N);
+}
+
+}  // namespace
+
+extern "C" sdd_status sdd_interface_values_target(sdd_ctx *ctx, const double *nodes_xz,
+                                                  const uint32_t *node_ids, int32_t n_nodes,
+                                                  int64_t n_pilot, int64_t n_max, double target_se,
+                                                  double dt, uint64_t seed, const sdd_config *cfg,
+                                                  double *mean, double *se, int64_t *n_used,
+                                                  sdd_stats *stats) {
+    if (!(target_se > 0.0) || !std::isfinite(target_se)) return fail(SDD_E_ARG, "target_se must be finite and > 0");
+    if (n_pilot < 2 || n_max < n_pilot || n_max > 0x7fffffffll)
+        return fail(SDD_E_ARG, "need 2 <= n_pilot <= n_max <= 2^31-1");
+    std::vector<int64_t> pilot((size_t)std::max(n_nodes, 0), n_pilot);
+    sdd_status st = check_call(ctx, n_nodes, pilot.data(), dt, cfg);
+    if (st != SDD_OK) return st;
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (n_nodes == 0) return SDD_OK;
+    if (!nodes_xz || !mean || !se) return fail(SDD_E_ARG, "nodes_xz, mean and se must not be NULL");
+    st = check_nodes(ctx, nodes_xz, n_nodes);
+    if (st != SDD_OK) return st;
+    cudaStream_t s = ctx->stream;
+    SDD_CUDA(ctx->nodes.ensure((size_t)n_nodes * 2 * sizeof(double)));
+    SDD_CUDA(cudaMemcpyAsync(ctx->nodes.p, nodes_xz, (size_t)n_nodes * 2 * sizeof(double),
+                             cudaMemcpyHostToDevice, s));
+    const int E = ctx->E;
+    std::vector<int64_t> begin((size_t)n_nodes, 0), extra((size_t)n_nodes, 0);
+
+    // phase 1: the pilot walks of every node
+    Launch L = choose_launch(ctx, cfg, dt, (long long)n_pilot * n_nodes);
+    WalkArgs A = base_args(ctx, L, dt, seed);
+    A.nodes = (const double *)ctx->nodes.p;
+    if (node_ids) {
+        SDD_CUDA(ctx->node_ids.ensure((size_t)n_nodes * sizeof(uint32_t)));
+        SDD_CUDA(cudaMemcpyAsync(ctx->node_ids.p, node_ids, (size_t)n_nodes * sizeof(uint32_t),
+                                 cudaMemcpyHostToDevice, s));
+        A.node_ids = (const uint32_t *)ctx->node_ids.p;
+    }
+    ctx->plan_valid = false;
+    Plan P1 = plan_ranges(n_nodes, begin.data(), pilot.data(), L.chunk);
+    std::vector<double> s1, s2;
+    std::vector<long long> v1, v2;
+    unsigned long long c1[3], c2[3];
+    float ms1 = 0.f, ms2 = 0.f;
+    st = run_phase(ctx, P1, L, A, n_nodes, s1, v1, c1, &ms1);
+    if (st != SDD_OK) return st;
+
+    // path count each node needs: N = clamp(ceil(max_e (var_re + var_im) / se^2), n_pilot, n_max)
+    long long total2 = 0;
+    for (int j = 0; j < n_nodes; ++j) {
+        double need = 0.0;
+        for (int e = 0; e < E; ++e) {
+            double m[2], sd[2];
+            finish(&s1[((size_t)j * E + e) * 4], v1[j], m, sd);
+            const double var = (sd[0] * sd[0] + sd[1] * sd[1]) * (double)v1[j];
+            if (std::isfinite(var)) need = std::max(need, var);
+        }
+        double N = std::ceil(need / (target_se * target_se));
+        if (!(N >= (double)n_pilot)) N = (double)n_pilot;
+        if (N > (double)n_max) N = (double)n_max;
+        begin[j] = n_pilot;
+        extra[j] = (int64_t)N - n_pilot;
+        total2 += extra[j];
+        if (n_used) n_used[j] = (int64_t)N;
+    }
+
+    // phase 2: the remaining walks, paths n_pilot .. N-1 of each node
+    if (total2 > 0) {
+        L = choose_launch(ctx, cfg, dt, total2);
+        WalkArgs A2 = base_args(ctx, L, dt, seed);
+        A2.nodes = A.nodes;
+        A2.node_ids = A.node_ids;
+        Plan P2 = plan_ranges(n_nodes, begin.data(), extra.data(), L.chunk);
+        st = run_phase(ctx, P2, L, A2, n_nodes, s2, v2, c2, &ms2);
+        if (st != SDD_OK) return st;
+    } else {
+        s2.assign(s1.size(), 0.0);
+        v2.assign(n_nodes, 0);
+        c2[0] = c2[1] = c2[2] = 0;
+    }
+    for (int j = 0; j < n_nodes; ++j)
+        for (int e = 0; e < E; ++e) {
+            const size_t o = ((size_t)j * E + e) * 4;
+            double q[4];
+            for (int k = 0; k < 4; ++k) q[k] = s1[o + k] + s2[o + k];
+            finish(q, v1[j] + v2[j], mean + ((size_t)j * E + e) * 2, se + ((size_t)j * E + e) * 2);
+        }
+    ctx->plan_valid = false;
+    if (stats) {
+        stats->steps = c1[0] + c2[0];
+        stats->walks = c1[1] + c2[1];
+        stats->truncated = c1[2] + c2[2];
+        stats->kernel_ms = (double)ms1 + (double)ms2;
+        stats->launches = total2 > 0 ? 4 : 2;
+        stats->items = (int32_t)P1.items.size();
+        stats->grid = L.grid;
+        stats->block = L.block;
+        stats->h2d_bytes = (uint64_t)n_nodes * 2 * sizeof(double);
+        stats->d2h_bytes = (uint64_t)(s1.size() * 8 + n_nodes * 8) * (total2 > 0 ? 2 : 1);
+    }
+    return (c1[2] + c2[2]) ? SDD_E_TRUNCATED : SDD_OK;
 }

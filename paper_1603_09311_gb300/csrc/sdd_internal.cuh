@@ -21,8 +21,11 @@ enum Geo : int { GEO_SHAPES = 0, GEO_RASTER = 1 };
 // that the common cases run without loops or branches: the layered
 // background alone, exactly one rectangle, exactly one triangle, up to 4 or
 // up to 16 shapes (unrolled, guarded), or the int8 raster.
+// GC_CONTACT is one rectangle [x0, >= x_max) x [0, >= z_max): the earth split
+// by a vertical contact at x0 (the quarter-space model), tested with two
+// compares; it takes the same decisions as GC_RECT1 on every inside point.
 enum GeoCode : int { GC_LAYER = 0, GC_RECT1 = 1, GC_TRI1 = 2, GC_SHAPES4 = 3, GC_SHAPES16 = 4,
-                     GC_RASTER = 5 };
+                     GC_RASTER = 5, GC_CONTACT = 6 };
 
 // One work item: paths [path0, path0 + count) of node `node`.
 struct Item {

@@ -113,6 +113,7 @@ struct WalkerF32 {
         const int m = (Z >= M.fzs) ? M.bg_earth : M.bg_air;
         if (GC == GC_LAYER) return m;
         if (GC == GC_RECT1) return in_rect(M.shapes[0], X, Z) ? M.shapes[0].mat : m;
+        if (GC == GC_CONTACT) return (Z >= M.fzs && X >= M.shapes[0].f[0]) ? M.shapes[0].mat : m;
         if (GC == GC_TRI1) return in_tri(M.shapes[0], X, Z) ? M.shapes[0].mat : m;
         constexpr int NS = GC == GC_SHAPES4 ? 4 : kMaxShapes;
         int r = m;
@@ -202,7 +203,8 @@ struct WalkerF32 {
                                             uint32_t wa, uint32_t wb, uint32_t sub,
                                             ExitInfo<float> &ei) {
         const float u0 = uni23(wa);
-        const float r = sqrtf(fmaxf(A.f_cdt * __log2f(u0), 0.f));  // sqrt(-2 ln(u0) dt)
+        // sqrt(-2 ln(u0) dt); |.| only guards the last-ulp sign of lg2 near u0 = 1
+        const float r = sqrtf(fabsf(A.f_cdt * __log2f(u0)));
         float sn, cs;
         // angle 2 pi (u1 - 1/2): cos(2 pi u1) = -cs, sin(2 pi u1) = -sn
         __sincosf(fmaf(one_plus(wb), 6.28318530718f, -9.42477796077f), &sn, &cs);
@@ -332,6 +334,7 @@ static int occ_one(int block) {
     case GC_SHAPES4: return FN<KM, GC_SHAPES4>(__VA_ARGS__);                    \
     case GC_SHAPES16: return FN<KM, GC_SHAPES16>(__VA_ARGS__);                  \
     case GC_RASTER: return FN<KM, GC_RASTER>(__VA_ARGS__);                      \
+    case GC_CONTACT: return FN<KM, GC_CONTACT>(__VA_ARGS__);                    \
     default: break;                                                             \
     }
 

@@ -87,6 +87,10 @@ SIGNATURES = [
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_int64),
       ctypes.c_double, ctypes.c_uint64, P(sdd_config), ctypes.c_void_p, ctypes.c_void_p,
       ctypes.c_void_p, ctypes.c_void_p]),
+    ("sdd_interface_values_target", ctypes.c_int,
+     [ctypes.c_void_p, P(ctypes.c_double), P(ctypes.c_uint32), ctypes.c_int32, ctypes.c_int64,
+      ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.c_uint64, P(sdd_config),
+      P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int64), P(sdd_stats)]),
     ("sdd_interface_values_noalloc", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_int64),
       ctypes.c_double, ctypes.c_uint64, P(sdd_config), ctypes.c_void_p, ctypes.c_void_p,
@@ -234,6 +238,31 @@ def sdd_interface_values(ctx: Context, nodes, n_paths, dt: float, seed: int, nod
     stats = {f: getattr(st_out, f) for f, _ in sdd_stats._fields_}
     stats["status"] = st
     return mean[..., 0] + 1j * mean[..., 1], se, stats
+
+
+def sdd_interface_values_target(ctx: Context, nodes, n_pilot: int, n_max: int, target_se: float,
+                                dt: float, seed: int, node_ids=None,
+                                config: sdd_config | None = None, **cfg):
+    """Adaptive path counts: returns (mean complex [n][E], se [n][E][2],
+    n_used [n], stats dict)."""
+    nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64).reshape(-1, 2))
+    n = nodes.shape[0]
+    mean = np.zeros((n, ctx.E, 2))
+    se = np.zeros((n, ctx.E, 2))
+    used = np.zeros(n, dtype=np.int64)
+    st_out = sdd_stats()
+    ids = None if node_ids is None else np.ascontiguousarray(np.asarray(node_ids, dtype=np.uint32))
+    c = config if config is not None else make_config(**cfg)
+    st = lib().sdd_interface_values_target(
+        ctx.handle, _dp(nodes), None if ids is None else ids.ctypes.data_as(P(ctypes.c_uint32)), n,
+        int(n_pilot), int(n_max), float(target_se), float(dt), int(seed) & (2 ** 64 - 1),
+        ctypes.byref(c), _dp(mean), _dp(se), used.ctypes.data_as(P(ctypes.c_int64)),
+        ctypes.byref(st_out))
+    if st not in (SDD_OK, SDD_E_TRUNCATED):
+        raise SddError(st, "sdd_interface_values_target")
+    stats = {f: getattr(st_out, f) for f, _ in sdd_stats._fields_}
+    stats["status"] = st
+    return mean[..., 0] + 1j * mean[..., 1], se, used, stats
 
 
 def sdd_interface_values_device(ctx: Context, d_nodes_ptr: int, n_nodes: int, n_paths, dt: float,

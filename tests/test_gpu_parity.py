@@ -212,3 +212,28 @@ def test_full_size_quarterspace_sampled_nodes():
         d = mean[j] - r["mean"][0]
         assert np.all(np.abs(d.real) <= tol[..., 0]) and np.all(np.abs(d.imag) <= tol[..., 1])
     assert np.all(np.isfinite(mean)) and np.all(se > 0)
+
+
+def test_target_se_equals_fixed_counts_and_meets_target():
+    # adaptive path counts: pilot, then top-up to N = var / se^2; the result
+    # must be the fixed-count evaluation with n_paths = N (same walks), and
+    # each node not capped at n_max must meet the target
+    w = I.scaled(I.workload("quarterspace"), n_nodes=8, dt=1e-3)
+    ctx = sdd.sdd_create(w["model"])
+    target, n_pilot, n_max = 4e-3, 2000, 60000
+    mean, se, used, st = sdd.sdd_interface_values_target(ctx, w["nodes"], n_pilot, n_max, target,
+                                                         w["dt"], 21)
+    assert np.all(used >= n_pilot) and np.all(used <= n_max)
+    assert st["walks"] == used.sum()
+    se_c = np.sqrt((se ** 2).sum(-1))[:, 0]
+    free = used < n_max
+    # N comes from the pilot's variance, itself an estimate (relative s.d. about
+    # sqrt(2 / n_pilot) times the kurtosis factor, a few percent here): allow 15 %
+    assert np.all(se_c[free] <= target * 1.15)
+    fixed, fse, fst = sdd.sdd_interface_values(ctx, w["nodes"], used, w["dt"], 21)
+    assert np.allclose(mean, fixed, rtol=0, atol=1e-12)
+    assert np.allclose(se, fse, rtol=1e-9, atol=0)
+    ref = O.interface_values(w["model"], w["nodes"], used, w["dt"], 21, urule=23)
+    tol = FP32_NSE * np.sqrt(se ** 2 + ref["se"] ** 2) + FP32_ABS
+    d = mean - ref["mean"]
+    assert np.all(np.abs(d.real) <= tol[..., 0]) and np.all(np.abs(d.imag) <= tol[..., 1])
