@@ -154,6 +154,78 @@ def cpu_baseline(w, seconds_target: float = 15.0):
             "seconds": el}
 
 
+def serving(sdd, n_requests: int, seed: int = 5):
+    """Serving run: a Poisson stream of random raster requests (16-1024 nodes,
+    target complex SE 1e-3, pilot 4096, cap 1e6 walks per node, dt 1e-3).
+    Closed loop for capacity, open loop at 0.7 x capacity for p50/p99
+    latency, and the same arrivals served one request per launch, in order."""
+    rng = np.random.default_rng(seed)
+    reqs = [I.random_request(rng, i) for i in range(n_requests)]
+    for r in reqs:
+        r["node_ids"] = np.arange(len(r["nodes"]), dtype=np.uint32) + np.uint32(4096 * r["id"])
+    kw = dict(target_se=1e-3, n_pilot=4096, n_max=1_000_000)
+
+    def make_server():
+        return sdd.Server(domain=I.DOMAIN, nx=I.RASTER_NX, nz=I.RASTER_NZ, dt=1e-3, seed=seed,
+                          max_requests=64, n_streams=2, max_batch_models=64)
+
+    def open_loop(srv, arrivals):
+        t0 = time.perf_counter()
+        pending, done_at, k = {}, {}, 0
+        while len(done_at) < len(reqs):
+            now = time.perf_counter() - t0
+            while k < len(reqs) and arrivals[k] <= now:
+                rid = srv.submit(reqs[k]["model"], reqs[k]["nodes"], node_ids=reqs[k]["node_ids"], **kw)
+                if rid is None:
+                    break  # no slot: retry on the next pass
+                pending[rid] = k
+                k += 1
+            for rid in [r for r in pending if srv.poll(r)]:
+                done_at[pending.pop(rid)] = time.perf_counter() - t0
+                srv.result(rid)
+            time.sleep(0.0002)
+        lat = np.array([done_at[i] - arrivals[i] for i in range(len(reqs))])
+        return lat, max(done_at.values())
+
+    srv = make_server()
+    # closed loop: every request at t = 0
+    lat_c, span_c = open_loop(srv, np.zeros(len(reqs)))
+    cap = len(reqs) / span_c
+    st0 = srv.stats()
+    # open loop at 0.7 x capacity
+    arr = np.cumsum(np.random.default_rng(seed + 1).exponential(1.0 / (0.7 * cap), len(reqs)))
+    arr -= arr[0]
+    lat, span = open_loop(srv, arr)
+    st1 = srv.stats()
+    srv.close()
+    steps = st1["steps"] - st0["steps"]
+    # baseline: one request per launch, served in arrival order on the same arrivals
+    service = []
+    for r in reqs:
+        ctx = sdd.sdd_create(r["model"])
+        t = time.perf_counter()
+        sdd.sdd_interface_values_target(ctx, r["nodes"], kw["n_pilot"], kw["n_max"], kw["target_se"],
+                                        1e-3, seed, node_ids=r["node_ids"])
+        service.append(time.perf_counter() - t)
+        ctx.close()
+    free_at, base_lat = 0.0, []
+    for a, s_ in zip(arr, service):
+        start = max(a, free_at)
+        free_at = start + s_
+        base_lat.append(free_at - a)
+    base_lat = np.array(base_lat)
+    return {"requests": len(reqs), "arrivals": "Poisson at 0.7 x closed-loop capacity",
+            "capacity_req_per_s": cap, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "steps_per_s": steps / span, "launches": int(st1["launches"] - st0["launches"]),
+            "baseline_one_request_per_launch": {
+                "capacity_req_per_s": len(reqs) / sum(service),
+                "p50_ms": 1e3 * float(np.percentile(base_lat, 50)),
+                "p99_ms": 1e3 * float(np.percentile(base_lat, 99))},
+            "workload": "random raster requests (1024x768 int8, 1-4 shapes), 16-1024 nodes, "
+                        "target SE 1e-3, pilot 4096, cap 1e6, dt 1e-3"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -196,6 +268,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sdd", choices=["sdd", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=24,
+                    help="requests of the serving measurement (0 skips it)")
     ap.add_argument("--small", action="store_true",
                     help="16 nodes x 1e5 walks of the same workload (for profiler captures)")
     args = ap.parse_args()
@@ -338,6 +412,8 @@ def main():
             "clocks": clocks,
             "gpu_launches": 2 * args.steps,
         }
+        if args.serve_requests > 0 and world == 1 and not args.small:
+            line["serving"] = serving(sdd, args.serve_requests)
         if not args.no_cpu_baseline and world == 1:
             cb = cpu_baseline(w)
             cb.pop("seconds", None)

@@ -204,6 +204,29 @@ sdd_status sdd_interface_values_target(sdd_ctx *ctx, const double *nodes_xz,
                                        double *mean, double *se, int64_t *n_used,
                                        sdd_stats *stats);
 
+/* One model's share of a batched launch. */
+typedef struct {
+    sdd_ctx *ctx;               /* the model (created by sdd_create) */
+    const double *nodes_xz;     /* host, [n_nodes][2] */
+    const uint32_t *node_ids;   /* host, [n_nodes] RNG node ids, or NULL for 0..n_nodes-1 */
+    int32_t n_nodes;
+    const int64_t *n_paths;     /* host, [n_nodes] */
+    double *mean;               /* host out, [n_nodes][n_eval][2] */
+    double *se;                 /* host out, [n_nodes][n_eval][2] */
+} sdd_batch_entry;
+
+/* Interface-node values of several models in ONE launch of the persistent
+ * walk kernel, host buffers, synchronous (the estimator of Sec. 3.1 for each
+ * entry).  The models must be raster models on the same device with the same
+ * domain, raster size, n_eval and g_kind; 1..256 entries.  Walk (node id i,
+ * path r) of an entry uses the same Philox stream as in sdd_interface_values
+ * with the same seed, so each entry's result equals its result computed
+ * alone, up to FP64 summation order.  The first entry's context lends its
+ * scratch buffers.  Errors: SDD_E_ARG (mismatched models, bad nodes),
+ * SDD_E_UNSUPPORTED (non-raster model, SDD_FP64). */
+sdd_status sdd_batch_values(const sdd_batch_entry *entries, int32_t n_entries, double dt,
+                            uint64_t seed, const sdd_config *cfg, sdd_stats *stats);
+
 /* Per-path records of walks (node id, paths p0 .. p0+count-1) started at
  * (x0, z0), host buffers, synchronous -- the individual steps of Sec. 3.1
  * for comparison path by path:
@@ -251,6 +274,101 @@ sdd_status sdd_interface_values_noalloc(sdd_ctx *ctx, const double *d_nodes_xz,
                                         const int64_t *n_paths, double dt, uint64_t seed,
                                         const sdd_config *cfg, double *d_mean, double *d_se,
                                         uint64_t *d_counters, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching.
+ *
+ * A server evaluates requests -- one raster model and its interface nodes
+ * each -- on one device.  Requests are admitted while a slot (and, with
+ * max_bytes, device memory) is free; a worker thread packs the runnable work
+ * of all admitted requests (the pilot or fixed-count walks of new requests,
+ * the top-up walks of requests whose pilot has finished) into launches of
+ * the persistent walk kernel over many models, with up to n_streams launches
+ * in flight, so new requests start while earlier ones are still on the GPU.
+ * Every walk uses the server's seed and the request's node ids as Philox
+ * stream, so a request's result does not depend on what it was batched with
+ * (up to FP64 summation order).  All requests must match the server's
+ * domain, raster size, n_eval and g_kind.
+ * ---------------------------------------------------------------------- */
+typedef struct sdd_server sdd_server;
+
+typedef struct {
+    sdd_domain domain;        /* every request's domain */
+    int32_t nx, nz;           /* every request's raster size */
+    int32_t n_eval;           /* every request's number of evaluations */
+    int32_t g_kind;           /* every request's boundary-data kind */
+    int32_t max_requests;     /* admission slots: admitted and not yet collected, 1..4096 */
+    int64_t max_bytes;        /* device bytes admitted requests may hold; 0 = slots only */
+    int32_t n_streams;        /* batched launches in flight at once, 1..8 */
+    int32_t max_batch_models; /* requests per launch, 1..256 */
+    double dt;                /* Euler time step of every walk */
+    uint64_t seed;            /* Philox key of every walk */
+    sdd_config launch;        /* launch options; precision must be SDD_FP32 */
+} sdd_server_config;
+
+typedef struct {
+    const sdd_model_desc *model; /* raster model, copied at submission */
+    const double *nodes_xz;      /* host, [n_nodes][2], copied */
+    const uint32_t *node_ids;    /* host, [n_nodes] or NULL for 0..n_nodes-1, copied */
+    int32_t n_nodes;             /* 1..65536 */
+    const int64_t *n_paths;      /* host, [n_nodes] fixed walk counts, or NULL for ... */
+    double target_se;            /* ... adaptive counts at this complex standard error */
+    int64_t n_pilot, n_max;      /* adaptive: pilot walks and cap per node */
+} sdd_request_desc;
+
+typedef struct {
+    double queue_us;    /* submission to its first launch */
+    double latency_us;  /* submission to completion */
+    uint64_t walks;     /* walks run for the request */
+    uint64_t truncated; /* of which reached max_steps */
+    int32_t launches;   /* batched launches the request took part in */
+    int32_t status;     /* SDD_OK, SDD_E_TRUNCATED, SDD_E_CANCELLED or an error */
+} sdd_request_stats;
+
+typedef struct {
+    uint64_t submitted, refused, completed, cancelled;
+    uint64_t launches;          /* batched launches */
+    uint64_t steps, walks;      /* Euler steps and walks of all launches */
+    double gpu_busy_ms;         /* sum of the launches' walk-kernel times */
+    int32_t in_flight;          /* admitted, not yet collected */
+    int64_t bytes_in_use;       /* device bytes held by admitted requests */
+} sdd_server_stats;
+
+/* Create a server on the current device: worker thread, n_streams streams,
+ * a raster arena of max_requests x nx x nz bytes and per-stream scratch.
+ * Errors: SDD_E_ARG, SDD_E_OOM, SDD_E_CUDA. */
+sdd_status sdd_server_create(const sdd_server_config *cfg, sdd_server **out);
+
+/* Stop the worker (running launches finish first) and free everything;
+ * requests not collected are discarded.  NULL is allowed. */
+void sdd_server_destroy(sdd_server *srv);
+
+/* Admit a request; *id identifies it.  SDD_E_BUSY when no slot or not enough
+ * of max_bytes is free (nothing is kept; retry later), SDD_E_ARG when the
+ * request does not match the server or is malformed. */
+sdd_status sdd_server_submit(sdd_server *srv, const sdd_request_desc *req, uint64_t *id);
+
+/* *done = 1 once the request has finished (or was cancelled). */
+sdd_status sdd_server_poll(sdd_server *srv, uint64_t id, int32_t *done);
+
+/* Block until the request finishes or timeout_ms passes (< 0: no limit);
+ * SDD_E_TIMEOUT if it did not finish in time. */
+sdd_status sdd_server_wait(sdd_server *srv, uint64_t id, int64_t timeout_ms);
+
+/* Copy a finished request's results and free its slot: mean and se
+ * [n_nodes][n_eval][2], n_used [n_nodes] (nullable), stats (nullable).
+ * Returns the request's status (SDD_OK, SDD_E_TRUNCATED, SDD_E_CANCELLED, ...);
+ * SDD_E_BUSY if it has not finished; SDD_E_ARG for an unknown id. */
+sdd_status sdd_server_result(sdd_server *srv, uint64_t id, double *mean, double *se,
+                             int64_t *n_used, sdd_request_stats *stats);
+
+/* Cancel a request: if it is not on the GPU it ends at once, otherwise when
+ * its launch ends; its results are then discarded.  Collect it with
+ * sdd_server_result to free its slot. */
+sdd_status sdd_server_cancel(sdd_server *srv, uint64_t id);
+
+/* Counters of the server since its creation. */
+sdd_status sdd_server_get_stats(sdd_server *srv, sdd_server_stats *out);
 
 /* Number of evaluations and materials of the context's model. */
 int32_t sdd_n_eval(const sdd_ctx *ctx);

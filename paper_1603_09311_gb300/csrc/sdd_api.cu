@@ -4,7 +4,13 @@
 #include <complex>
 #include <cstdio>
 #include <algorithm>
+#include <chrono>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
 #include <string>
 #include <vector>
 
@@ -66,6 +72,7 @@ struct sdd_ctx {
     // per-call scratch
     DevBuf items, slots, trunc, counters, queue, err, nodes, node_ids, mean, se;
     DevBuf rec_steps, rec_counts, rec_exit, rec_wall, rec_mlast;
+    DevBuf batch_models;  // model table of batched launches owned by this context
     Item *h_items = nullptr;  // pinned staging of the item table
     size_t h_items_cap = 0;
     cudaEvent_t items_done = nullptr;  // last copy out of h_items finished
@@ -320,13 +327,15 @@ struct Launch {
     int64_t max_steps;
 };
 
-Launch choose_launch(const sdd_ctx *ctx, const sdd_config *cfg, double dt, long long total_paths) {
+Launch choose_launch(const sdd_ctx *ctx, const sdd_config *cfg, double dt, long long total_paths,
+                     int kmax_override = 0, int gcode_override = -1) {
     Launch L;
     L.f64 = cfg && cfg->precision == SDD_FP64;
-    L.kmax = kmax_for(ctx->K);
+    L.kmax = kmax_override ? kmax_override : kmax_for(ctx->K);
     L.block = (cfg && cfg->block_threads) ? cfg->block_threads : 256;
+    const int gcode = gcode_override >= 0 ? gcode_override : ctx->M.gcode;
     int occ = L.f64 ? occupancy_f64(L.kmax, ctx->geo, L.block)
-                    : occupancy_f32(L.kmax, ctx->M.gcode, L.block);
+                    : occupancy_f32(L.kmax, gcode, L.block);
     if (occ < 1) occ = 1;
     if (cfg && cfg->ctas_per_sm > 0 && cfg->ctas_per_sm < occ) occ = cfg->ctas_per_sm;
     L.grid = ctx->n_sm * occ;
@@ -355,7 +364,7 @@ Plan plan_items(int32_t n_nodes, const int64_t *n_paths, int chunk, uint32_t p_o
             I.node = j;
             I.path0 = p_offset + (uint32_t)p;
             I.count = (int32_t)std::min<int64_t>(chunk, n_paths[j] - p);
-            I.pad = 0;
+            I.model = 0;
             P.items.push_back(I);
         }
         P.total_paths += n_paths[j];
@@ -397,7 +406,7 @@ Plan plan_ranges(int32_t n_nodes, const int64_t *begin, const int64_t *count, in
             I.node = j;
             I.path0 = (uint32_t)(begin[j] + p);
             I.count = (int32_t)std::min<int64_t>(chunk, count[j] - p);
-            I.pad = 0;
+            I.model = 0;
             P.items.push_back(I);
         }
         P.total_paths += count[j];
@@ -428,7 +437,9 @@ WalkArgs base_args(sdd_ctx *ctx, const Launch &L, double dt, uint64_t seed) {
 
 // Upload the item table (through pinned staging) and launch walk + reduce.
 sdd_status run(sdd_ctx *ctx, const Plan &P, const Launch &L, WalkArgs A, cudaStream_t s,
-               bool timed, bool do_reduce, double *d_mean, double *d_se, int n_nodes) {
+               bool timed, bool do_reduce, double *d_mean, double *d_se, int n_nodes,
+               const ModelDev *model = nullptr) {
+    const ModelDev &MD = model ? *model : ctx->M;
     const size_t ni = P.items.size();
     if (ni == 0) return SDD_OK;
     SDD_CUDA(ctx->items.ensure(ni * sizeof(Item) + (n_nodes + 1) * sizeof(int32_t)));
@@ -470,8 +481,8 @@ sdd_status run(sdd_ctx *ctx, const Plan &P, const Launch &L, WalkArgs A, cudaStr
     const int need = (int)((ni + warps_per_cta - 1) / warps_per_cta);
     if (grid > need) grid = need;
     if (timed) SDD_CUDA(cudaEventRecord(ctx->ev0, s));
-    cudaError_t e = L.f64 ? launch_walk_f64(L.kmax, ctx->geo, ctx->M, A, grid, L.block, s)
-                          : launch_walk_f32(L.kmax, ctx->geo, ctx->M, A, grid, L.block, s);
+    cudaError_t e = L.f64 ? launch_walk_f64(L.kmax, ctx->geo, MD, A, grid, L.block, s)
+                          : launch_walk_f32(L.kmax, ctx->geo, MD, A, grid, L.block, s);
     if (e != cudaSuccess) return cuda_fail(e, "walk kernel launch");
     if (timed) SDD_CUDA(cudaEventRecord(ctx->ev1, s));
     if (do_reduce) {
@@ -548,7 +559,8 @@ void sdd_destroy(sdd_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->raster, &c->items, &c->slots, &c->trunc, &c->counters, &c->queue,
                       &c->err, &c->nodes, &c->node_ids, &c->mean, &c->se, &c->rec_steps,
-                      &c->rec_counts, &c->rec_exit, &c->rec_wall, &c->rec_mlast};
+                      &c->rec_counts, &c->rec_exit, &c->rec_wall, &c->rec_mlast,
+                      &c->batch_models};
     for (DevBuf *b : bufs) b->release();
     if (c->h_items) cudaFreeHost(c->h_items);
     if (c->items_done) cudaEventDestroy(c->items_done);
@@ -758,7 +770,7 @@ __global__ void noalloc_plan_kernel(int n_nodes, int chunk) {
             I.node = j;
             I.path0 = (uint32_t)p;
             I.count = (int32_t)(n_paths[j] - p < chunk ? n_paths[j] - p : chunk);
-            I.pad = 0;
+            I.model = 0;
             items[it] = I;
         }
     }
@@ -981,4 +993,701 @@ extern "C" sdd_status sdd_interface_values_target(sdd_ctx *ctx, const double *no
         stats->d2h_bytes = (uint64_t)(s1.size() * 8 + n_nodes * 8) * (total2 > 0 ? 2 : 1);
     }
     return (c1[2] + c2[2]) ? SDD_E_TRUNCATED : SDD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched launches over several models (sdd_batch_values).
+
+namespace {
+
+sdd_status check_batch(const sdd_batch_entry *en, int32_t n, double dt, const sdd_config *cfg) {
+    if (!en || n < 1 || n > kMaxBatchModels) return fail(SDD_E_ARG, "need 1..256 batch entries");
+    if (cfg && cfg->precision == SDD_FP64) return fail(SDD_E_UNSUPPORTED, "batched launches run the FP32 walk");
+    const sdd_ctx *c0 = en[0].ctx;
+    for (int i = 0; i < n; ++i) {
+        const sdd_ctx *c = en[i].ctx;
+        sdd_status st = check_call(const_cast<sdd_ctx *>(c), en[i].n_nodes, en[i].n_paths, dt, cfg);
+        if (st != SDD_OK) return st;
+        if (c->geo != GEO_RASTER) return fail(SDD_E_UNSUPPORTED, "batched launches need raster models");
+        if (c->M.nx != c0->M.nx || c->M.nz != c0->M.nz || c->M.xmin != c0->M.xmin ||
+            c->M.xmax != c0->M.xmax || c->M.zmin != c0->M.zmin || c->M.zmax != c0->M.zmax ||
+            c->E != c0->E || c->M.g_kind != c0->M.g_kind || c->device != c0->device)
+            return fail(SDD_E_ARG, "batched models must share device, domain, raster size, n_eval and g_kind");
+        if (en[i].n_nodes > 0 && (!en[i].nodes_xz || !en[i].mean || !en[i].se))
+            return fail(SDD_E_ARG, "entry nodes_xz, mean and se must not be NULL");
+        st = check_nodes(c, en[i].nodes_xz, en[i].n_nodes);
+        if (st != SDD_OK) return st;
+    }
+    return SDD_OK;
+}
+
+}  // namespace
+
+extern "C" sdd_status sdd_batch_values(const sdd_batch_entry *entries, int32_t n_entries, double dt,
+                                       uint64_t seed, const sdd_config *cfg, sdd_stats *stats) {
+    sdd_status st = check_batch(entries, n_entries, dt, cfg);
+    if (st != SDD_OK) return st;
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    sdd_ctx *own = entries[0].ctx;
+    // concatenated nodes, ids and path counts; model index per node
+    std::vector<double> nodes;
+    std::vector<uint32_t> ids;
+    std::vector<int64_t> paths;
+    std::vector<int32_t> node_model, first(n_entries + 1);
+    int Kmax = 1;
+    for (int i = 0; i < n_entries; ++i) {
+        const sdd_batch_entry &e = entries[i];
+        first[i] = (int32_t)paths.size();
+        for (int j = 0; j < e.n_nodes; ++j) {
+            nodes.push_back(e.nodes_xz[2 * j]);
+            nodes.push_back(e.nodes_xz[2 * j + 1]);
+            ids.push_back(e.node_ids ? e.node_ids[j] : (uint32_t)j);
+            paths.push_back(e.n_paths[j]);
+            node_model.push_back(i);
+        }
+        Kmax = std::max(Kmax, e.ctx->K);
+    }
+    const int32_t n_nodes = (int32_t)paths.size();
+    first[n_entries] = n_nodes;
+    if (n_nodes == 0) return SDD_OK;
+    long long total = 0;
+    for (int64_t p : paths) total += p;
+    const Launch L = choose_launch(own, cfg, dt, total, kmax_for(Kmax), GC_RASTER_MULTI);
+    Plan P = plan_items(n_nodes, paths.data(), L.chunk, 0);
+    for (Item &I : P.items) I.model = node_model[I.node];
+    own->plan_valid = false;
+
+    std::vector<BatchModel> table(n_entries);
+    for (int i = 0; i < n_entries; ++i) {
+        const sdd_ctx *c = entries[i].ctx;
+        BatchModel &B = table[i];
+        std::memset(&B, 0, sizeof(B));
+        B.raster = c->M.raster;
+        B.K = c->K;
+        for (int k = 0; k < c->E * c->K; ++k) B.kappa[k] = c->M.kappa[k];
+        for (int k = 0; k < c->E; ++k) B.ev[k] = c->M.ev[k];
+    }
+    cudaStream_t s = own->stream;
+    const size_t ob = (size_t)n_nodes * own->E * 2 * sizeof(double);
+    SDD_CUDA(own->batch_models.ensure(table.size() * sizeof(BatchModel)));
+    SDD_CUDA(own->nodes.ensure(nodes.size() * sizeof(double)));
+    SDD_CUDA(own->node_ids.ensure(ids.size() * sizeof(uint32_t)));
+    SDD_CUDA(own->mean.ensure(ob));
+    SDD_CUDA(own->se.ensure(ob));
+    SDD_CUDA(cudaMemcpyAsync(own->batch_models.p, table.data(), table.size() * sizeof(BatchModel),
+                             cudaMemcpyHostToDevice, s));
+    SDD_CUDA(cudaMemcpyAsync(own->nodes.p, nodes.data(), nodes.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    SDD_CUDA(cudaMemcpyAsync(own->node_ids.p, ids.data(), ids.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    ModelDev Mb = own->M;
+    Mb.gcode = GC_RASTER_MULTI;
+    Mb.K = Kmax;
+    WalkArgs A = base_args(own, L, dt, seed);
+    A.nodes = (const double *)own->nodes.p;
+    A.node_ids = (const uint32_t *)own->node_ids.p;
+    A.models = (const BatchModel *)own->batch_models.p;
+    st = run(own, P, L, A, s, true, true, (double *)own->mean.p, (double *)own->se.p, n_nodes, &Mb);
+    if (st != SDD_OK) return st;
+    std::vector<double> hm(ob / sizeof(double)), hs(ob / sizeof(double));
+    unsigned long long cnt[3] = {0, 0, 0};
+    SDD_CUDA(cudaMemcpyAsync(hm.data(), own->mean.p, ob, cudaMemcpyDeviceToHost, s));
+    SDD_CUDA(cudaMemcpyAsync(hs.data(), own->se.p, ob, cudaMemcpyDeviceToHost, s));
+    SDD_CUDA(cudaMemcpyAsync(cnt, own->counters.p, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    SDD_CUDA(cudaStreamSynchronize(s));
+    const size_t per = (size_t)own->E * 2;
+    for (int i = 0; i < n_entries; ++i) {
+        const size_t o = (size_t)first[i] * per, nb = (size_t)(first[i + 1] - first[i]) * per;
+        if (nb == 0) continue;
+        std::memcpy(entries[i].mean, hm.data() + o, nb * sizeof(double));
+        std::memcpy(entries[i].se, hs.data() + o, nb * sizeof(double));
+    }
+    if (stats) {
+        float ms = 0.f;
+        SDD_CUDA(cudaEventElapsedTime(&ms, own->ev0, own->ev1));
+        stats->steps = cnt[0];
+        stats->walks = cnt[1];
+        stats->truncated = cnt[2];
+        stats->kernel_ms = ms;
+        stats->launches = 2;
+        stats->items = (int32_t)P.items.size();
+        stats->grid = L.grid;
+        stats->block = L.block;
+        stats->h2d_bytes = table.size() * sizeof(BatchModel) + nodes.size() * 8 + ids.size() * 4 +
+                           P.items.size() * sizeof(Item);
+        stats->d2h_bytes = 2 * ob + sizeof(cnt);
+    }
+    return cnt[2] ? SDD_E_TRUNCATED : SDD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Serving (sdd_server_*): admission, continuous batching, completion.
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double us_since(Clock::time_point a, Clock::time_point b) {
+    return std::chrono::duration<double, std::micro>(b - a).count();
+}
+
+struct SrvRequest {
+    uint64_t id = 0;
+    int slot = -1;                 // raster arena slot
+    int64_t bytes = 0;
+    BatchModel bm;                 // rates and boundary constants (raster set per slot)
+    int K = 1;
+    std::vector<double> nodes;
+    std::vector<uint32_t> ids;
+    std::vector<int64_t> fixed;    // fixed counts, empty when adaptive
+    double target_se = 0.0;
+    int64_t n_pilot = 0, n_max = 0;
+    int phase = 0;                 // 0 first walks pending, 1 running, 2 top-up pending, 3 running, 4 finished
+    std::vector<int64_t> begin, count;
+    std::vector<double> sums;      // [n][E][4]
+    std::vector<long long> nvalid;
+    std::vector<int64_t> n_used;
+    bool cancelled = false;
+    sdd_status status = SDD_OK;
+    uint64_t walks = 0, truncated = 0;
+    int launches = 0;
+    Clock::time_point t_submit, t_first, t_done;
+    bool started = false;
+};
+
+struct SrvPart {
+    SrvRequest *r;
+    int32_t node0, n;
+};
+
+struct SrvLane {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool busy = false;
+    DevBuf items, slots, trunc, counters, queue, err, nodes, ids, models, sums, nvalid;
+    double *h_sums = nullptr;
+    long long *h_nvalid = nullptr;
+    unsigned long long *h_cnt = nullptr;
+    size_t h_cap_nodes = 0;
+    std::vector<SrvPart> parts;
+    int32_t n_nodes = 0;
+    uint64_t walks = 0;
+};
+
+}  // namespace
+
+struct sdd_server {
+    sdd_server_config cfg;
+    int device = 0;
+    sdd_ctx *tmpl = nullptr;       // a context with the server's model shape (launch planning)
+    DevBuf arena;                  // max_requests rasters of nx * nz bytes
+    std::vector<int> free_slots;
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    std::map<uint64_t, SrvRequest *> reqs;
+    std::deque<SrvRequest *> runnable;
+    std::vector<SrvLane> lanes;
+    std::thread worker;
+    bool stop = false;
+    uint64_t next_id = 1;
+    int64_t bytes_in_use = 0;
+    sdd_server_stats st{};
+    std::string worker_error;
+};
+
+namespace {
+
+int64_t request_bytes(const sdd_server *srv, int32_t n_nodes) {
+    const int E = srv->cfg.n_eval;
+    return (int64_t)srv->cfg.nx * srv->cfg.nz + (int64_t)n_nodes * (16 + 4 + 8 + 8 + 32 * E) +
+           (int64_t)sizeof(BatchModel);
+}
+
+// Queue the walks of the requests' current phases as one batched launch.
+sdd_status srv_launch(sdd_server *srv, SrvLane &L, std::vector<SrvRequest *> &batch) {
+    const int E = srv->cfg.n_eval;
+    std::vector<double> nodes;
+    std::vector<uint32_t> ids;
+    std::vector<int64_t> begin, count;
+    std::vector<int32_t> node_model;
+    std::vector<BatchModel> table;
+    L.parts.clear();
+    int Kmax = 1;
+    for (size_t m = 0; m < batch.size(); ++m) {
+        SrvRequest *r = batch[m];
+        const int32_t n = (int32_t)r->ids.size();
+        L.parts.push_back({r, (int32_t)ids.size(), n});
+        for (int j = 0; j < n; ++j) {
+            nodes.push_back(r->nodes[2 * j]);
+            nodes.push_back(r->nodes[2 * j + 1]);
+            ids.push_back(r->ids[j]);
+            begin.push_back(r->begin[j]);
+            count.push_back(r->count[j]);
+            node_model.push_back((int32_t)m);
+        }
+        table.push_back(r->bm);
+        Kmax = std::max(Kmax, r->K);
+    }
+    const int32_t n_nodes = (int32_t)ids.size();
+    L.n_nodes = n_nodes;
+    long long total = 0;
+    for (int64_t c : count) total += c;
+    L.walks = (uint64_t)total;
+    const Launch La = choose_launch(srv->tmpl, &srv->cfg.launch, srv->cfg.dt, total, kmax_for(Kmax),
+                                    GC_RASTER_MULTI);
+    Plan P = plan_ranges(n_nodes, begin.data(), count.data(), La.chunk);
+    for (Item &I : P.items) I.model = node_model[I.node];
+    const size_t ni = P.items.size();
+    cudaStream_t s = L.s;
+    SDD_CUDA(L.items.ensure(ni * sizeof(Item) + (n_nodes + 1) * sizeof(int32_t)));
+    SDD_CUDA(L.slots.ensure(std::max<size_t>(ni, 1) * (size_t)E * 4 * sizeof(double)));
+    SDD_CUDA(L.trunc.ensure(std::max<size_t>(ni, 1) * sizeof(int32_t)));
+    SDD_CUDA(L.counters.ensure(3 * sizeof(unsigned long long)));
+    SDD_CUDA(L.queue.ensure(sizeof(int32_t)));
+    SDD_CUDA(L.err.ensure(sizeof(int32_t)));
+    SDD_CUDA(L.nodes.ensure(nodes.size() * sizeof(double)));
+    SDD_CUDA(L.ids.ensure(ids.size() * sizeof(uint32_t)));
+    SDD_CUDA(L.models.ensure(table.size() * sizeof(BatchModel)));
+    SDD_CUDA(L.sums.ensure((size_t)n_nodes * E * 4 * sizeof(double)));
+    SDD_CUDA(L.nvalid.ensure((size_t)n_nodes * sizeof(long long)));
+    if ((size_t)n_nodes > L.h_cap_nodes) {
+        if (L.h_sums) cudaFreeHost(L.h_sums);
+        if (L.h_nvalid) cudaFreeHost(L.h_nvalid);
+        L.h_sums = nullptr;
+        L.h_nvalid = nullptr;
+        L.h_cap_nodes = 0;
+        SDD_CUDA(cudaMallocHost((void **)&L.h_sums, (size_t)n_nodes * E * 4 * sizeof(double)));
+        SDD_CUDA(cudaMallocHost((void **)&L.h_nvalid, (size_t)n_nodes * sizeof(long long)));
+        L.h_cap_nodes = n_nodes;
+    }
+    std::vector<unsigned char> hi(ni * sizeof(Item) + (n_nodes + 1) * sizeof(int32_t));
+    std::memcpy(hi.data(), P.items.data(), ni * sizeof(Item));
+    std::memcpy(hi.data() + ni * sizeof(Item), P.node_item0.data(), (n_nodes + 1) * sizeof(int32_t));
+    SDD_CUDA(cudaMemcpyAsync(L.items.p, hi.data(), hi.size(), cudaMemcpyHostToDevice, s));
+    SDD_CUDA(cudaMemcpyAsync(L.nodes.p, nodes.data(), nodes.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    SDD_CUDA(cudaMemcpyAsync(L.ids.p, ids.data(), ids.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    SDD_CUDA(cudaMemcpyAsync(L.models.p, table.data(), table.size() * sizeof(BatchModel), cudaMemcpyHostToDevice, s));
+    SDD_CUDA(cudaMemsetAsync(L.queue.p, 0, sizeof(int32_t), s));
+    SDD_CUDA(cudaMemsetAsync(L.counters.p, 0, 3 * sizeof(unsigned long long), s));
+    WalkArgs A = base_args(srv->tmpl, La, srv->cfg.dt, srv->cfg.seed);
+    A.items = (const Item *)L.items.p;
+    A.n_items = (int32_t)ni;
+    A.nodes = (const double *)L.nodes.p;
+    A.node_ids = (const uint32_t *)L.ids.p;
+    A.slots = (double *)L.slots.p;
+    A.item_trunc = (int32_t *)L.trunc.p;
+    A.counters = (unsigned long long *)L.counters.p;
+    A.queue = (int32_t *)L.queue.p;
+    A.error = (int32_t *)L.err.p;
+    A.models = (const BatchModel *)L.models.p;
+    ModelDev Mb = srv->tmpl->M;
+    Mb.gcode = GC_RASTER_MULTI;
+    Mb.K = Kmax;
+    const int wpc = La.block / 32;
+    int grid = La.grid;
+    const int need = (int)((ni + wpc - 1) / wpc);
+    if (grid > need) grid = need;
+    SDD_CUDA(cudaEventRecord(L.ev0, s));
+    if (ni > 0) {
+        cudaError_t e = launch_walk_f32(La.kmax, GEO_RASTER, Mb, A, grid, La.block, s);
+        if (e != cudaSuccess) return cuda_fail(e, "batched walk launch");
+    }
+    SDD_CUDA(cudaEventRecord(L.ev1, s));
+    const int nt = n_nodes * E;
+    sums_kernel<<<(nt + 127) / 128, 128, 0, s>>>(A.slots, A.item_trunc, A.items,
+                                                reinterpret_cast<const int32_t *>((const unsigned char *)L.items.p + ni * sizeof(Item)),
+                                                n_nodes, E, (double *)L.sums.p, (long long *)L.nvalid.p);
+    SDD_CUDA(cudaGetLastError());
+    SDD_CUDA(cudaMemcpyAsync(L.h_sums, L.sums.p, (size_t)n_nodes * E * 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    SDD_CUDA(cudaMemcpyAsync(L.h_nvalid, L.nvalid.p, (size_t)n_nodes * sizeof(long long), cudaMemcpyDeviceToHost, s));
+    SDD_CUDA(cudaMemcpyAsync(L.h_cnt, L.counters.p, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    L.busy = true;
+    return SDD_OK;
+}
+
+// Mean and SE of a finished request (sums in fixed order: pilot, then top-up).
+void srv_finish(sdd_server *srv, SrvRequest *r) {
+    r->phase = 4;
+    r->t_done = Clock::now();
+    if (r->cancelled) r->status = SDD_E_CANCELLED;
+    else if (r->status == SDD_OK && r->truncated) r->status = SDD_E_TRUNCATED;
+    srv->st.completed += 1;
+    if (r->cancelled) srv->st.cancelled += 1;
+}
+
+// A launch ended: fold its per-node sums into its requests.
+void srv_complete(sdd_server *srv, SrvLane &L) {
+    const int E = srv->cfg.n_eval;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, L.ev0, L.ev1);
+    srv->st.gpu_busy_ms += ms;
+    srv->st.launches += 1;
+    srv->st.steps += L.h_cnt[0];
+    srv->st.walks += L.h_cnt[1];
+    for (const SrvPart &pt : L.parts) {
+        SrvRequest *r = pt.r;
+        r->launches += 1;
+        for (int j = 0; j < pt.n; ++j) {
+            const long long nv = L.h_nvalid[pt.node0 + j];
+            r->walks += (uint64_t)r->count[j];
+            r->truncated += (uint64_t)(r->count[j] - nv);
+            r->nvalid[j] += nv;
+            for (int q = 0; q < E * 4; ++q)
+                r->sums[(size_t)j * E * 4 + q] += L.h_sums[((size_t)pt.node0 + j) * E * 4 + q];
+        }
+        if (r->cancelled) {
+            srv_finish(srv, r);
+            continue;
+        }
+        if (r->phase == 1 && r->fixed.empty()) {
+            // adaptive: size each node from its pilot variance
+            long long extra_total = 0;
+            for (int j = 0; j < pt.n; ++j) {
+                double need = 0.0;
+                for (int e = 0; e < E; ++e) {
+                    double m[2], sd[2];
+                    finish(&r->sums[((size_t)j * E + e) * 4], r->nvalid[j], m, sd);
+                    const double var = (sd[0] * sd[0] + sd[1] * sd[1]) * (double)r->nvalid[j];
+                    if (std::isfinite(var)) need = std::max(need, var);
+                }
+                double N = std::ceil(need / (r->target_se * r->target_se));
+                if (!(N >= (double)r->n_pilot)) N = (double)r->n_pilot;
+                if (N > (double)r->n_max) N = (double)r->n_max;
+                r->n_used[j] = (int64_t)N;
+                r->begin[j] = r->n_pilot;
+                r->count[j] = (int64_t)N - r->n_pilot;
+                extra_total += r->count[j];
+            }
+            if (extra_total > 0) {
+                r->phase = 2;
+                srv->runnable.push_back(r);
+                continue;
+            }
+        }
+        srv_finish(srv, r);
+    }
+    L.parts.clear();
+    L.busy = false;
+}
+
+void srv_worker(sdd_server *srv) {
+    cudaSetDevice(srv->device);
+    std::unique_lock<std::mutex> lk(srv->mu);
+    while (true) {
+        bool progress = false;
+        for (SrvLane &L : srv->lanes) {
+            if (L.busy && cudaEventQuery(L.ev1) == cudaSuccess && cudaStreamQuery(L.s) == cudaSuccess) {
+                srv_complete(srv, L);
+                progress = true;
+            }
+        }
+        if (progress) srv->done_cv.notify_all();
+        if (srv->stop) {
+            bool any_busy = false;
+            for (SrvLane &L : srv->lanes) any_busy |= L.busy;
+            if (!any_busy) break;
+        }
+        for (SrvLane &L : srv->lanes) {
+            if (L.busy || srv->runnable.empty() || srv->stop) continue;
+            std::vector<SrvRequest *> batch;
+            while (!srv->runnable.empty() && (int)batch.size() < srv->cfg.max_batch_models) {
+                SrvRequest *r = srv->runnable.front();
+                srv->runnable.pop_front();
+                if (r->cancelled) {
+                    srv_finish(srv, r);
+                    progress = true;
+                    continue;
+                }
+                r->phase = r->phase == 0 ? 1 : 3;
+                if (!r->started) {
+                    r->started = true;
+                    r->t_first = Clock::now();
+                }
+                batch.push_back(r);
+            }
+            if (batch.empty()) continue;
+            sdd_status st = srv_launch(srv, L, batch);
+            if (st != SDD_OK) {
+                srv->worker_error = g_last_error;
+                for (SrvRequest *r : batch) {
+                    r->status = st;
+                    srv_finish(srv, r);
+                }
+                L.busy = false;
+            }
+            progress = true;
+        }
+        if (progress) {
+            srv->done_cv.notify_all();
+            continue;
+        }
+        srv->cv.wait_for(lk, std::chrono::microseconds(50));
+    }
+}
+
+}  // namespace
+
+extern "C" sdd_status sdd_server_create(const sdd_server_config *cfg, sdd_server **out) {
+    if (!out) return fail(SDD_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!cfg) return fail(SDD_E_ARG, "cfg is NULL");
+    if (cfg->nx < 1 || cfg->nz < 1 || (long long)cfg->nx * cfg->nz > (1ll << 31))
+        return fail(SDD_E_ARG, "raster size out of range");
+    if (cfg->n_eval < 1 || cfg->n_eval > SDD_MAX_EVAL) return fail(SDD_E_ARG, "n_eval must be in 1..32");
+    if (cfg->max_requests < 1 || cfg->max_requests > 4096) return fail(SDD_E_ARG, "max_requests must be in 1..4096");
+    if (cfg->n_streams < 1 || cfg->n_streams > 8) return fail(SDD_E_ARG, "n_streams must be in 1..8");
+    if (cfg->max_batch_models < 1 || cfg->max_batch_models > kMaxBatchModels)
+        return fail(SDD_E_ARG, "max_batch_models must be in 1..256");
+    if (cfg->max_bytes < 0) return fail(SDD_E_ARG, "max_bytes < 0");
+    if (cfg->launch.precision != SDD_FP32) return fail(SDD_E_UNSUPPORTED, "the server runs the FP32 walk");
+    sdd_status st;
+    // a template model of the server's shape (one material, blank raster)
+    std::vector<int8_t> blank((size_t)cfg->nx * cfg->nz, 0);
+    std::vector<double> kap((size_t)cfg->n_eval, 0.0);
+    sdd_model_desc md;
+    std::memset(&md, 0, sizeof(md));
+    md.domain = cfg->domain;
+    md.n_materials = 1;
+    md.n_eval = cfg->n_eval;
+    md.kappa = kap.data();
+    md.raster = blank.data();
+    md.nx = cfg->nx;
+    md.nz = cfg->nz;
+    md.g_kind = cfg->g_kind;
+    sdd_server *srv = new (std::nothrow) sdd_server();
+    if (!srv) return fail(SDD_E_OOM, "host allocation failed");
+    srv->cfg = *cfg;
+    st = sdd_create(&md, &srv->tmpl);
+    if (st != SDD_OK) {
+        delete srv;
+        return st;
+    }
+    const int64_t np1 = 1;
+    st = check_call(srv->tmpl, 1, &np1, cfg->dt, &cfg->launch);
+    if (st != SDD_OK) {
+        sdd_server_destroy(srv);
+        return st;
+    }
+    srv->device = srv->tmpl->device;
+    cudaError_t e = srv->arena.ensure((size_t)cfg->max_requests * cfg->nx * cfg->nz);
+    if (e != cudaSuccess) {
+        sdd_server_destroy(srv);
+        return fail(SDD_E_OOM, "raster arena allocation failed");
+    }
+    for (int i = cfg->max_requests - 1; i >= 0; --i) srv->free_slots.push_back(i);
+    srv->lanes.resize(cfg->n_streams);
+    for (SrvLane &L : srv->lanes) {
+        e = cudaStreamCreateWithFlags(&L.s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreate(&L.ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&L.ev1);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&L.h_cnt, 3 * sizeof(unsigned long long));
+        if (e != cudaSuccess) {
+            sdd_server_destroy(srv);
+            return cuda_fail(e, "server stream setup");
+        }
+    }
+    srv->worker = std::thread(srv_worker, srv);
+    *out = srv;
+    return SDD_OK;
+}
+
+extern "C" void sdd_server_destroy(sdd_server *srv) {
+    if (!srv) return;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+    }
+    srv->cv.notify_all();
+    if (srv->worker.joinable()) srv->worker.join();
+    for (SrvLane &L : srv->lanes) {
+        if (L.s) cudaStreamSynchronize(L.s);
+        DevBuf *b[] = {&L.items, &L.slots, &L.trunc, &L.counters, &L.queue, &L.err, &L.nodes,
+                       &L.ids, &L.models, &L.sums, &L.nvalid};
+        for (DevBuf *x : b) x->release();
+        if (L.h_sums) cudaFreeHost(L.h_sums);
+        if (L.h_nvalid) cudaFreeHost(L.h_nvalid);
+        if (L.h_cnt) cudaFreeHost(L.h_cnt);
+        if (L.ev0) cudaEventDestroy(L.ev0);
+        if (L.ev1) cudaEventDestroy(L.ev1);
+        if (L.s) cudaStreamDestroy(L.s);
+    }
+    for (auto &kv : srv->reqs) delete kv.second;
+    srv->arena.release();
+    sdd_destroy(srv->tmpl);
+    delete srv;
+}
+
+extern "C" sdd_status sdd_server_submit(sdd_server *srv, const sdd_request_desc *req, uint64_t *id) {
+    if (!srv || !req || !id) return fail(SDD_E_ARG, "srv, req and id must not be NULL");
+    const sdd_model_desc *m = req->model;
+    sdd_status st = check_model(m);
+    if (st != SDD_OK) return st;
+    const sdd_server_config &c = srv->cfg;
+    if (!m->raster || m->nx != c.nx || m->nz != c.nz || m->n_eval != c.n_eval || m->g_kind != c.g_kind ||
+        m->domain.x_min != c.domain.x_min || m->domain.x_max != c.domain.x_max ||
+        m->domain.z_min != c.domain.z_min || m->domain.z_max != c.domain.z_max)
+        return fail(SDD_E_ARG, "request model does not match the server (raster, size, n_eval, g_kind, domain)");
+    if (req->n_nodes < 1 || req->n_nodes > 65536 || !req->nodes_xz)
+        return fail(SDD_E_ARG, "n_nodes must be in 1..65536 with nodes_xz");
+    if (req->n_paths) {
+        for (int j = 0; j < req->n_nodes; ++j)
+            if (req->n_paths[j] < 1 || req->n_paths[j] > 0x7fffffffll)
+                return fail(SDD_E_ARG, "n_paths must be in 1..2^31-1");
+    } else if (!(req->target_se > 0.0) || req->n_pilot < 2 || req->n_max < req->n_pilot ||
+               req->n_max > 0x7fffffffll) {
+        return fail(SDD_E_ARG, "adaptive requests need target_se > 0 and 2 <= n_pilot <= n_max <= 2^31-1");
+    }
+    st = check_nodes(srv->tmpl, req->nodes_xz, req->n_nodes);
+    if (st != SDD_OK) return st;
+    SrvRequest *r = new (std::nothrow) SrvRequest();
+    if (!r) return fail(SDD_E_OOM, "host allocation failed");
+    ModelDev md;
+    build_model(m, md);
+    std::memset(&r->bm, 0, sizeof(r->bm));
+    r->K = m->n_materials;
+    r->bm.K = m->n_materials;
+    for (int k = 0; k < md.E * md.K; ++k) r->bm.kappa[k] = md.kappa[k];
+    for (int k = 0; k < md.E; ++k) r->bm.ev[k] = md.ev[k];
+    const int n = req->n_nodes, E = c.n_eval;
+    r->nodes.assign(req->nodes_xz, req->nodes_xz + 2 * n);
+    r->ids.resize(n);
+    for (int j = 0; j < n; ++j) r->ids[j] = req->node_ids ? req->node_ids[j] : (uint32_t)j;
+    r->begin.assign(n, 0);
+    r->count.resize(n);
+    r->n_used.resize(n);
+    if (req->n_paths) {
+        r->fixed.assign(req->n_paths, req->n_paths + n);
+        for (int j = 0; j < n; ++j) r->count[j] = r->n_used[j] = req->n_paths[j];
+    } else {
+        r->target_se = req->target_se;
+        r->n_pilot = req->n_pilot;
+        r->n_max = req->n_max;
+        for (int j = 0; j < n; ++j) r->count[j] = r->n_used[j] = req->n_pilot;
+    }
+    r->sums.assign((size_t)n * E * 4, 0.0);
+    r->nvalid.assign(n, 0);
+    r->bytes = request_bytes(srv, n);
+    std::unique_lock<std::mutex> lk(srv->mu);
+    srv->st.submitted += 1;
+    if (srv->free_slots.empty() || (c.max_bytes > 0 && srv->bytes_in_use + r->bytes > c.max_bytes)) {
+        srv->st.refused += 1;
+        lk.unlock();
+        delete r;
+        return fail(SDD_E_BUSY, "no free slot or device memory; retry later");
+    }
+    r->slot = srv->free_slots.back();
+    srv->free_slots.pop_back();
+    srv->bytes_in_use += r->bytes;
+    lk.unlock();
+    // the slot is reserved: upload the raster without holding the lock
+    unsigned char *ras = (unsigned char *)srv->arena.p + (size_t)r->slot * c.nx * c.nz;
+    r->bm.raster = (const int8_t *)ras;
+    int prev = -1;
+    cudaError_t e = cudaGetDevice(&prev);
+    if (e == cudaSuccess && prev != srv->device) e = cudaSetDevice(srv->device);
+    if (e == cudaSuccess) e = cudaMemcpy(ras, m->raster, (size_t)c.nx * c.nz, cudaMemcpyHostToDevice);
+    if (prev >= 0 && prev != srv->device) cudaSetDevice(prev);
+    lk.lock();
+    if (e != cudaSuccess) {
+        srv->free_slots.push_back(r->slot);
+        srv->bytes_in_use -= r->bytes;
+        lk.unlock();
+        delete r;
+        return cuda_fail(e, "raster upload");
+    }
+    r->id = srv->next_id++;
+    r->t_submit = Clock::now();
+    srv->reqs[r->id] = r;
+    srv->runnable.push_back(r);
+    *id = r->id;
+    lk.unlock();
+    srv->cv.notify_all();
+    return SDD_OK;
+}
+
+extern "C" sdd_status sdd_server_poll(sdd_server *srv, uint64_t id, int32_t *done) {
+    if (!srv || !done) return fail(SDD_E_ARG, "srv and done must not be NULL");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(id);
+    if (it == srv->reqs.end()) return fail(SDD_E_ARG, "unknown request id");
+    *done = it->second->phase == 4 ? 1 : 0;
+    return SDD_OK;
+}
+
+extern "C" sdd_status sdd_server_wait(sdd_server *srv, uint64_t id, int64_t timeout_ms) {
+    if (!srv) return fail(SDD_E_ARG, "srv is NULL");
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(id);
+    if (it == srv->reqs.end()) return fail(SDD_E_ARG, "unknown request id");
+    SrvRequest *r = it->second;
+    auto pred = [&] { return r->phase == 4; };
+    if (timeout_ms < 0) {
+        srv->done_cv.wait(lk, pred);
+        return SDD_OK;
+    }
+    if (!srv->done_cv.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred))
+        return fail(SDD_E_TIMEOUT, "request not finished within the timeout");
+    return SDD_OK;
+}
+
+extern "C" sdd_status sdd_server_result(sdd_server *srv, uint64_t id, double *mean, double *se,
+                                        int64_t *n_used, sdd_request_stats *stats) {
+    if (!srv) return fail(SDD_E_ARG, "srv is NULL");
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(id);
+    if (it == srv->reqs.end()) return fail(SDD_E_ARG, "unknown request id");
+    SrvRequest *r = it->second;
+    if (r->phase != 4) return fail(SDD_E_BUSY, "request not finished");
+    const int E = srv->cfg.n_eval;
+    const int n = (int)r->ids.size();
+    if (r->status == SDD_OK || r->status == SDD_E_TRUNCATED) {
+        for (int j = 0; j < n; ++j)
+            for (int e = 0; e < E; ++e) {
+                const size_t o = (size_t)j * E + e;
+                double mm[2], ss[2];
+                finish(&r->sums[o * 4], r->nvalid[j], mm, ss);
+                if (mean) { mean[2 * o] = mm[0]; mean[2 * o + 1] = mm[1]; }
+                if (se) { se[2 * o] = ss[0]; se[2 * o + 1] = ss[1]; }
+            }
+        if (n_used)
+            for (int j = 0; j < n; ++j) n_used[j] = r->n_used[j];
+    }
+    if (stats) {
+        stats->queue_us = r->started ? us_since(r->t_submit, r->t_first) : 0.0;
+        stats->latency_us = us_since(r->t_submit, r->t_done);
+        stats->walks = r->walks;
+        stats->truncated = r->truncated;
+        stats->launches = r->launches;
+        stats->status = r->status;
+    }
+    const sdd_status result = r->status;
+    srv->free_slots.push_back(r->slot);
+    srv->bytes_in_use -= r->bytes;
+    srv->reqs.erase(it);
+    delete r;
+    return result;
+}
+
+extern "C" sdd_status sdd_server_cancel(sdd_server *srv, uint64_t id) {
+    if (!srv) return fail(SDD_E_ARG, "srv is NULL");
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(id);
+    if (it == srv->reqs.end()) return fail(SDD_E_ARG, "unknown request id");
+    SrvRequest *r = it->second;
+    if (r->phase == 4) return SDD_OK;
+    r->cancelled = true;
+    if (r->phase == 0 || r->phase == 2) {
+        // not on the GPU: end it now
+        srv->runnable.erase(std::remove(srv->runnable.begin(), srv->runnable.end(), r), srv->runnable.end());
+        srv_finish(srv, r);
+        srv->done_cv.notify_all();
+    }
+    return SDD_OK;
+}
+
+extern "C" sdd_status sdd_server_get_stats(sdd_server *srv, sdd_server_stats *out) {
+    if (!srv || !out) return fail(SDD_E_ARG, "srv and out must not be NULL");
+    std::lock_guard<std::mutex> lk(srv->mu);
+    *out = srv->st;
+    out->in_flight = (int32_t)srv->reqs.size();
+    out->bytes_in_use = srv->bytes_in_use;
+    return SDD_OK;
 }

@@ -24,15 +24,20 @@ enum Geo : int { GEO_SHAPES = 0, GEO_RASTER = 1 };
 // GC_CONTACT is one rectangle [x0, >= x_max) x [0, >= z_max): the earth split
 // by a vertical contact at x0 (the quarter-space model), tested with two
 // compares; it takes the same decisions as GC_RECT1 on every inside point.
+// GC_RASTER_MULTI serves a batch of raster models sharing the domain and the
+// raster size: each lane reads the raster of its walk's model.
 enum GeoCode : int { GC_LAYER = 0, GC_RECT1 = 1, GC_TRI1 = 2, GC_SHAPES4 = 3, GC_SHAPES16 = 4,
-                     GC_RASTER = 5, GC_CONTACT = 6 };
+                     GC_RASTER = 5, GC_CONTACT = 6, GC_RASTER_MULTI = 7 };
 
-// One work item: paths [path0, path0 + count) of node `node`.
+
+
+// One work item: paths [path0, path0 + count) of node `node` of model
+// `model` (the index into WalkArgs::models of a batched launch, else 0).
 struct Item {
     int32_t node;
     uint32_t path0;
     int32_t count;
-    int32_t pad;
+    int32_t model;
 };
 
 // A material shape.  f: single-precision copy in domain-centred coordinates
@@ -53,6 +58,16 @@ struct EvalDev {
     double kl_re, kl_im, kr_re, kr_im;
     double tl_re, tl_im, tr_re, tr_im;  // top-left, top-right corners
     double bl_re, bl_im, br_re, br_im;  // bottom-left, bottom-right corners
+};
+
+constexpr int kMaxBatchModels = 256;
+
+// Per-model data of a batched launch (device memory).
+struct BatchModel {
+    const int8_t *raster;
+    int32_t K, pad;
+    double kappa[kMaxE * kMaxK];  // [E][K] of this model
+    EvalDev ev[kMaxE];
 };
 
 struct ModelDev {
@@ -103,6 +118,7 @@ struct WalkArgs {
     double *rec_exit;          // [count][3]
     int32_t *rec_wall;
     int32_t *rec_mlast;
+    const BatchModel *models;  // batched launch: the models the items refer to
 };
 
 // Launchers (one per precision translation unit).

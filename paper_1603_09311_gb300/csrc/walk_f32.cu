@@ -91,6 +91,7 @@ struct WalkerF32 {
     uint32_t n;        // Euler steps accepted (even at the start of iterate)
     Occupancy<KMAX> occ;
     uint32_t nid, pre_x, pre_y;
+    const int8_t *rast;  // GC_RASTER_MULTI: the raster of this walk's model
 
     __device__ __forceinline__ static bool in_rect(const ShapeDev &S, float X, float Z) {
         return X >= S.f[0] && X < S.f[1] && Z >= S.f[2] && Z < S.f[3];
@@ -101,14 +102,14 @@ struct WalkerF32 {
                fmaf(S.f[6], X, fmaf(S.f[7], Z, S.f[8])) >= 0.f;
     }
 
-    __device__ __forceinline__ static int material(const ModelDev &M, float X, float Z) {
-        if (GC == GC_RASTER) {
+    __device__ __forceinline__ int material(const ModelDev &M, float X, float Z) const {
+        if (GC == GC_RASTER || GC == GC_RASTER_MULTI) {
             // round(v - 1/2) = floor(v) for v = (X + hw) sx >= 0 (magic-number rounding)
             int ix = __float_as_int(fmaf(X, M.fsx, M.fox) + 12582912.0f) - 0x4B400000;
             int iz = __float_as_int(fmaf(Z, M.fsz, M.foz) + 12582912.0f) - 0x4B400000;
             ix = min(ix, M.nx - 1);
             iz = min(iz, M.nz - 1);
-            return (int)__ldg(M.raster + iz * M.nx + ix);
+            return (int)__ldg((GC == GC_RASTER_MULTI ? rast : M.raster) + iz * M.nx + ix);
         }
         const int m = (Z >= M.fzs) ? M.bg_earth : M.bg_air;
         if (GC == GC_LAYER) return m;
@@ -131,7 +132,8 @@ struct WalkerF32 {
     __device__ __forceinline__ void counts(uint32_t *c) const { occ.counts(c); }
 
     __device__ __forceinline__ void start(const ModelDev &M, const WalkArgs &A, double x0,
-                                          double z0, uint32_t path, uint32_t node_id) {
+                                          double z0, uint32_t path, uint32_t node_id, int model) {
+        if (GC == GC_RASTER_MULTI) rast = A.models[model].raster;
         X = (float)(x0 - M.xc);
         Z = (float)(z0 - M.zc);
         dmin = fminf(M.fhw - fabsf(X), M.fhh - fabsf(Z));
@@ -261,14 +263,17 @@ struct WalkerF32 {
     }
 
     // Sample of one walk for evaluation e: g(exit) exp(-i (1/2) sum_m kappa_{e,m} T_m).
-    __device__ static double2 sample(const ModelDev &M, const SharedTables &T, int e, float X,
-                                     float Z, float th, int wall, int mlast, const uint32_t *c,
-                                     double dt) {
-        const double *kap = T.kappa + e * M.K;
+    __device__ static double2 sample(const ModelDev &M, const SharedTables &T, const WalkArgs &A,
+                                     int model, int e, float X, float Z, float th, int wall,
+                                     int mlast, const uint32_t *c) {
+        const double dt = A.dt;
+        const bool multi = GC == GC_RASTER_MULTI;
+        const int K = multi ? A.models[model].K : M.K;
+        const double *kap = (multi ? A.models[model].kappa : T.kappa) + e * K;
         double ph = 0.0;
 #pragma unroll
         for (int k = 0; k < KMAX; ++k)
-            if (k < M.K) ph = fma(kap[k], (double)c[k], ph);
+            if (k < K) ph = fma(kap[k], (double)c[k], ph);
         ph = fma(kap[mlast], (double)th, ph);
         ph *= 0.5 * dt;
         const double q = rint(ph * 0.15915494309189535);
@@ -285,7 +290,7 @@ struct WalkerF32 {
             gr = x * x - z * z;
             gi = 0.f;
         } else {
-            const EvalDev &E = T.ev[e];
+            const EvalDev &E = multi ? A.models[model].ev[e] : T.ev[e];
             if (wall == 0) {
                 column((float)E.kl_re, (float)E.kl_im, z, gr, gi);
             } else if (wall == 1) {
@@ -335,6 +340,7 @@ static int occ_one(int block) {
     case GC_SHAPES16: return FN<KM, GC_SHAPES16>(__VA_ARGS__);                  \
     case GC_RASTER: return FN<KM, GC_RASTER>(__VA_ARGS__);                      \
     case GC_CONTACT: return FN<KM, GC_CONTACT>(__VA_ARGS__);                    \
+    case GC_RASTER_MULTI: return FN<KM, GC_RASTER_MULTI>(__VA_ARGS__);          \
     default: break;                                                             \
     }
 

@@ -73,7 +73,7 @@ struct WalkerF64 {
     }
 
     __device__ __forceinline__ void start(const ModelDev &M, const WalkArgs &A, double x0,
-                                          double z0, uint32_t path, uint32_t node_id) {
+                                          double z0, uint32_t path, uint32_t node_id, int) {
         x = x0;
         z = z0;
         n = 0;
@@ -177,9 +177,10 @@ struct WalkerF64 {
         return make_double2(1.0 - kr * z, -(ki * z));
     }
 
-    __device__ static double2 sample(const ModelDev &M, const SharedTables &T, int e, double x,
-                                     double z, double th, int wall, int mlast, const uint32_t *c,
-                                     double dt) {
+    __device__ static double2 sample(const ModelDev &M, const SharedTables &T, const WalkArgs &A,
+                                     int, int e, double x, double z, double th, int wall, int mlast,
+                                     const uint32_t *c) {
+        const double dt = A.dt;
         const double *kap = T.kappa + e * M.K;
         double ph = 0.0;
 #pragma unroll

@@ -107,7 +107,7 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const uint32_t (&rk0)[10],
 template <class Real, int KMAX>
 struct Ring {
     Real x[kRing], z[kRing], th[kRing];
-    uint32_t meta[kRing];  // wall | m_last << 2 | tag << 5 | truncated << 6
+    uint32_t meta[kRing];  // wall | m_last << 2 | tag << 5 | truncated << 6 | model << 8
     uint32_t n[kRing];     // occupation steps (all steps but the exiting one)
     uint32_t path[kRing];
     uint32_t cnt[KMAX > 1 ? KMAX - 1 : 1][kRing];  // steps in materials 1..K-1
@@ -124,7 +124,7 @@ struct WarpState {
     int32_t item[2];   // item of accumulator set (-1: free)
     int32_t out[2];    // walks handed out and not yet ended
     int32_t ntr[2];    // truncated walks
-    int32_t disp_set, disp_rem;
+    int32_t disp_set, disp_rem, disp_model;
     uint32_t disp_next, nid;
     uint32_t head, tail;
     int32_t queue_empty;
@@ -157,11 +157,11 @@ struct ExitInfo {
 
 // Scheduler kernel.  W is a walker type providing
 //   using Real; static constexpr int KMAX;
-//   start(M, A, x0, z0, path, node_id)  -- begin a walk
+//   start(M, A, x0, z0, path, node_id, model)  -- begin a walk
 //   iterate(M, A, path, ExitInfo&) -> 0 running, 1 exited, 2 truncated
 //     (two Euler steps per call)
 //   counts(c): steps spent in materials 1..KMAX-1 (at the exit)
-//   static sample(M, T, e, x, z, th, wall, mlast, counts, dt) -> double2
+//   static sample(M, T, A, model, e, x, z, th, wall, mlast, counts) -> double2
 //   static to_abs(M, x, z, ax, az)
 template <class W>
 __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ ModelDev M,
@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
         S.item[0] = S.item[1] = -1;
         S.out[0] = S.out[1] = 0;
         S.ntr[0] = S.ntr[1] = 0;
-        S.disp_set = -1; S.disp_rem = 0; S.disp_next = 0; S.nid = 0;
+        S.disp_set = -1; S.disp_rem = 0; S.disp_model = 0; S.disp_next = 0; S.nid = 0;
         S.head = S.tail = 0;
         S.queue_empty = 0;
         S.nx0 = S.nz0 = 0.0;
@@ -202,6 +202,7 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
     W w;
     bool active = false;
     int tag = 0;
+    int model = 0;
     uint32_t path = 0;
 
     // Turn records [head, head + cnt) of the ring into samples; lane l
@@ -244,8 +245,8 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
                         A.rec_mlast[o] = (int)((meta >> 2) & 7u);
                     }
                 } else if (!tr) {
-                    const double2 v = W::sample(M, T, my_e, R.x[s], R.z[s], R.th[s],
-                                                (int)(meta & 3u), (int)((meta >> 2) & 7u), c, A.dt);
+                    const double2 v = W::sample(M, T, A, (int)(meta >> 8), my_e, R.x[s], R.z[s],
+                                                R.th[s], (int)(meta & 3u), (int)((meta >> 2) & 7u), c);
                     double *a0 = &S.acc[rt][0][lane];
                     a0[0] += v.x;
                     a0[32] += v.y;
@@ -307,6 +308,7 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
                     S.out[fs] = 0;
                     S.ntr[fs] = 0;
                     S.disp_set = fs;
+                    S.disp_model = I.model;
                     S.disp_next = I.path0;
                     S.disp_rem = I.count;
                     S.nx0 = A.nodes[2 * I.node];
@@ -324,8 +326,9 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
             if (mine) {
                 path = S.disp_next + (uint32_t)rank;
                 tag = S.disp_set;
+                model = S.disp_model;
                 active = true;
-                w.start(M, A, S.nx0, S.nz0, path, S.nid);
+                w.start(M, A, S.nx0, S.nz0, path, S.nid, model);
             }
             const unsigned got = __ballot_sync(kFull, mine);
             need &= ~got;
@@ -357,7 +360,7 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
             R.z[slot] = ei.z;
             R.th[slot] = ei.th;
             R.meta[slot] = (uint32_t)ei.wall | ((uint32_t)ei.mlast << 2) | ((uint32_t)tag << 5) |
-                           ((uint32_t)tr << 6);
+                           ((uint32_t)tr << 6) | ((uint32_t)model << 8);
             R.n[slot] = ei.nocc;
             R.path[slot] = path;
             uint32_t c[KMAX > 1 ? KMAX - 1 : 1];

@@ -64,12 +64,48 @@ class sdd_config(ctypes.Structure):
                 ("chunk_paths", ctypes.c_int32)]
 
 
+class sdd_batch_entry(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("nodes_xz", ctypes.POINTER(ctypes.c_double)),
+                ("node_ids", ctypes.POINTER(ctypes.c_uint32)), ("n_nodes", ctypes.c_int32),
+                ("n_paths", ctypes.POINTER(ctypes.c_int64)), ("mean", ctypes.POINTER(ctypes.c_double)),
+                ("se", ctypes.POINTER(ctypes.c_double))]
+
+
 class sdd_stats(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_uint64), ("walks", ctypes.c_uint64),
                 ("truncated", ctypes.c_uint64), ("kernel_ms", ctypes.c_double),
                 ("launches", ctypes.c_int32), ("items", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64)]
+
+
+class sdd_server_config(ctypes.Structure):
+    _fields_ = [("domain", sdd_domain), ("nx", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("n_eval", ctypes.c_int32), ("g_kind", ctypes.c_int32),
+                ("max_requests", ctypes.c_int32), ("max_bytes", ctypes.c_int64),
+                ("n_streams", ctypes.c_int32), ("max_batch_models", ctypes.c_int32),
+                ("dt", ctypes.c_double), ("seed", ctypes.c_uint64), ("launch", sdd_config)]
+
+
+class sdd_request_desc(ctypes.Structure):
+    _fields_ = [("model", ctypes.POINTER(sdd_model_desc)), ("nodes_xz", ctypes.POINTER(ctypes.c_double)),
+                ("node_ids", ctypes.POINTER(ctypes.c_uint32)), ("n_nodes", ctypes.c_int32),
+                ("n_paths", ctypes.POINTER(ctypes.c_int64)), ("target_se", ctypes.c_double),
+                ("n_pilot", ctypes.c_int64), ("n_max", ctypes.c_int64)]
+
+
+class sdd_request_stats(ctypes.Structure):
+    _fields_ = [("queue_us", ctypes.c_double), ("latency_us", ctypes.c_double),
+                ("walks", ctypes.c_uint64), ("truncated", ctypes.c_uint64),
+                ("launches", ctypes.c_int32), ("status", ctypes.c_int32)]
+
+
+class sdd_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("refused", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("cancelled", ctypes.c_uint64),
+                ("launches", ctypes.c_uint64), ("steps", ctypes.c_uint64), ("walks", ctypes.c_uint64),
+                ("gpu_busy_ms", ctypes.c_double), ("in_flight", ctypes.c_int32),
+                ("bytes_in_use", ctypes.c_int64)]
 
 
 P = ctypes.POINTER
@@ -95,10 +131,23 @@ SIGNATURES = [
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_int64),
       ctypes.c_double, ctypes.c_uint64, P(sdd_config), ctypes.c_void_p, ctypes.c_void_p,
       ctypes.c_void_p, ctypes.c_void_p]),
+    ("sdd_batch_values", ctypes.c_int,
+     [P(sdd_batch_entry), ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, P(sdd_config),
+      P(sdd_stats)]),
     ("sdd_walk_records", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32,
       ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, P(sdd_config), P(ctypes.c_int64),
       P(ctypes.c_int64), P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_int32)]),
+    ("sdd_server_create", ctypes.c_int, [P(sdd_server_config), P(ctypes.c_void_p)]),
+    ("sdd_server_destroy", None, [ctypes.c_void_p]),
+    ("sdd_server_submit", ctypes.c_int, [ctypes.c_void_p, P(sdd_request_desc), P(ctypes.c_uint64)]),
+    ("sdd_server_poll", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, P(ctypes.c_int32)]),
+    ("sdd_server_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64]),
+    ("sdd_server_result", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_uint64, P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int64),
+      P(sdd_request_stats)]),
+    ("sdd_server_cancel", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
+    ("sdd_server_get_stats", ctypes.c_int, [ctypes.c_void_p, P(sdd_server_stats)]),
     ("sdd_n_eval", ctypes.c_int32, [ctypes.c_void_p]),
     ("sdd_n_materials", ctypes.c_int32, [ctypes.c_void_p]),
     ("sdd_status_str", ctypes.c_char_p, [ctypes.c_int]),
@@ -302,6 +351,40 @@ def sdd_interface_values_noalloc(ctx: Context, d_nodes_ptr: int, n_nodes: int, n
     return st
 
 
+def sdd_batch_values(entries, dt: float, seed: int, config: sdd_config | None = None, **cfg):
+    """One launch over several raster models.  entries: list of dicts with
+    ctx, nodes, n_paths and optional node_ids.  Returns ([(mean, se)], stats)."""
+    arr = (sdd_batch_entry * len(entries))()
+    keep, outs = [], []
+    for i, e in enumerate(entries):
+        nodes = np.ascontiguousarray(np.asarray(e["nodes"], dtype=np.float64).reshape(-1, 2))
+        n = nodes.shape[0]
+        npth = _paths(e["n_paths"], n)
+        mean = np.zeros((n, e["ctx"].E, 2))
+        se = np.zeros((n, e["ctx"].E, 2))
+        ids = e.get("node_ids")
+        if ids is not None:
+            ids = np.ascontiguousarray(np.asarray(ids, dtype=np.uint32))
+        keep += [nodes, npth, ids]
+        outs.append((mean, se))
+        arr[i].ctx = e["ctx"].handle
+        arr[i].nodes_xz = _dp(nodes)
+        arr[i].node_ids = None if ids is None else ids.ctypes.data_as(P(ctypes.c_uint32))
+        arr[i].n_nodes = n
+        arr[i].n_paths = npth.ctypes.data_as(P(ctypes.c_int64))
+        arr[i].mean = _dp(mean)
+        arr[i].se = _dp(se)
+    st_out = sdd_stats()
+    c = config if config is not None else make_config(**cfg)
+    st = lib().sdd_batch_values(arr, len(entries), float(dt), int(seed) & (2 ** 64 - 1),
+                                ctypes.byref(c), ctypes.byref(st_out))
+    if st not in (SDD_OK, SDD_E_TRUNCATED):
+        raise SddError(st, "sdd_batch_values")
+    stats = {f: getattr(st_out, f) for f, _ in sdd_stats._fields_}
+    stats["status"] = st
+    return [(m[..., 0] + 1j * m[..., 1], s_) for m, s_ in outs], stats
+
+
 def sdd_walk_records(ctx: Context, x0: float, z0: float, node_id: int, p0: int, count: int,
                      dt: float, seed: int, config: sdd_config | None = None, **cfg):
     """Per-path records (steps, counts [count][K], exit [count][3], wall, m_last)."""
@@ -329,3 +412,107 @@ def sdd_status_str(status: int) -> str:
 
 def sdd_last_error() -> str:
     return lib().sdd_last_error().decode()
+
+
+class Server:
+    """A serving loop (sdd_server_*): admission, continuous batching into
+    multi-model launches, completion.  Requests are raster models that match
+    the server's domain, raster size, n_eval and g_kind."""
+
+    def __init__(self, domain, nx, nz, dt, seed, n_eval=1, g_kind=0, max_requests=64, max_bytes=0,
+                 n_streams=2, max_batch_models=64, **launch):
+        c = sdd_server_config()
+        c.domain = sdd_domain(*[float(v) for v in domain])
+        c.nx, c.nz, c.n_eval, c.g_kind = int(nx), int(nz), int(n_eval), int(g_kind)
+        c.max_requests, c.max_bytes = int(max_requests), int(max_bytes)
+        c.n_streams, c.max_batch_models = int(n_streams), int(max_batch_models)
+        c.dt, c.seed = float(dt), int(seed) & (2 ** 64 - 1)
+        c.launch = make_config(**launch)
+        self.n_eval = int(n_eval)
+        self.handle = ctypes.c_void_p()
+        st = lib().sdd_server_create(ctypes.byref(c), ctypes.byref(self.handle))
+        if st != SDD_OK:
+            raise SddError(st, "sdd_server_create")
+        self.pending = {}
+
+    def submit(self, model: dict, nodes, n_paths=None, target_se=0.0, n_pilot=0, n_max=0, node_ids=None):
+        """Returns the request id, or None when the server refused it (SDD_E_BUSY)."""
+        d, keep = make_desc(model)
+        nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64).reshape(-1, 2))
+        r = sdd_request_desc()
+        r.model = ctypes.pointer(d)
+        r.nodes_xz = _dp(nodes)
+        r.n_nodes = nodes.shape[0]
+        ids = None
+        if node_ids is not None:
+            ids = np.ascontiguousarray(np.asarray(node_ids, dtype=np.uint32))
+            r.node_ids = ids.ctypes.data_as(P(ctypes.c_uint32))
+        npth = None
+        if n_paths is not None:
+            npth = _paths(n_paths, nodes.shape[0])
+            r.n_paths = npth.ctypes.data_as(P(ctypes.c_int64))
+        r.target_se, r.n_pilot, r.n_max = float(target_se), int(n_pilot), int(n_max)
+        rid = ctypes.c_uint64()
+        st = lib().sdd_server_submit(self.handle, ctypes.byref(r), ctypes.byref(rid))
+        if st == SDD_E_BUSY:
+            return None
+        if st != SDD_OK:
+            raise SddError(st, "sdd_server_submit")
+        self.pending[rid.value] = nodes.shape[0]
+        return rid.value
+
+    def poll(self, rid: int) -> bool:
+        done = ctypes.c_int32()
+        st = lib().sdd_server_poll(self.handle, rid, ctypes.byref(done))
+        if st != SDD_OK:
+            raise SddError(st, "sdd_server_poll")
+        return bool(done.value)
+
+    def wait(self, rid: int, timeout_ms: int = -1) -> bool:
+        """True when finished, False on timeout."""
+        st = lib().sdd_server_wait(self.handle, rid, int(timeout_ms))
+        if st == SDD_E_TIMEOUT:
+            return False
+        if st != SDD_OK:
+            raise SddError(st, "sdd_server_wait")
+        return True
+
+    def result(self, rid: int):
+        """(status, mean complex [n][E], se [n][E][2], n_used [n], stats dict); frees the slot."""
+        n = self.pending[rid]
+        mean = np.zeros((n, self.n_eval, 2))
+        se = np.zeros((n, self.n_eval, 2))
+        used = np.zeros(n, dtype=np.int64)
+        rs = sdd_request_stats()
+        st = lib().sdd_server_result(self.handle, rid, _dp(mean), _dp(se),
+                                     used.ctypes.data_as(P(ctypes.c_int64)), ctypes.byref(rs))
+        if st == SDD_E_BUSY:
+            raise SddError(st, "sdd_server_result")
+        if st == SDD_E_ARG:
+            raise SddError(st, "sdd_server_result")
+        del self.pending[rid]
+        stats = {f: getattr(rs, f) for f, _ in sdd_request_stats._fields_}
+        return st, mean[..., 0] + 1j * mean[..., 1], se, used, stats
+
+    def cancel(self, rid: int) -> None:
+        st = lib().sdd_server_cancel(self.handle, rid)
+        if st != SDD_OK:
+            raise SddError(st, "sdd_server_cancel")
+
+    def stats(self) -> dict:
+        s = sdd_server_stats()
+        st = lib().sdd_server_get_stats(self.handle, ctypes.byref(s))
+        if st != SDD_OK:
+            raise SddError(st, "sdd_server_get_stats")
+        return {f: getattr(s, f) for f, _ in sdd_server_stats._fields_}
+
+    def close(self):
+        if self.handle:
+            lib().sdd_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -52,6 +52,9 @@ int main(void) {{
          sizeof(sdd_stats), sizeof(sdd_domain));
   printf("%zu %zu %zu %zu\\n", offsetof(sdd_model_desc, raster), offsetof(sdd_model_desc, g_coef),
          offsetof(sdd_config, chunk_paths), offsetof(sdd_stats, block));
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sdd_server_config), offsetof(sdd_server_config, launch),
+         sizeof(sdd_request_desc), offsetof(sdd_request_desc, n_max), sizeof(sdd_request_stats),
+         sizeof(sdd_server_stats), sizeof(sdd_batch_entry));
   return 0;
 }}''')
     exe = tmp_path / "probe"
@@ -60,7 +63,11 @@ int main(void) {{
     want = [ctypes.sizeof(sdd.sdd_model_desc), ctypes.sizeof(sdd.sdd_shape),
             ctypes.sizeof(sdd.sdd_config), ctypes.sizeof(sdd.sdd_stats), ctypes.sizeof(sdd.sdd_domain),
             sdd.sdd_model_desc.raster.offset, sdd.sdd_model_desc.g_coef.offset,
-            sdd.sdd_config.chunk_paths.offset, sdd.sdd_stats.block.offset]
+            sdd.sdd_config.chunk_paths.offset, sdd.sdd_stats.block.offset,
+            ctypes.sizeof(sdd.sdd_server_config), sdd.sdd_server_config.launch.offset,
+            ctypes.sizeof(sdd.sdd_request_desc), sdd.sdd_request_desc.n_max.offset,
+            ctypes.sizeof(sdd.sdd_request_stats), ctypes.sizeof(sdd.sdd_server_stats),
+            ctypes.sizeof(sdd.sdd_batch_entry)]
     assert [int(v) for v in out] == want
 
 

@@ -237,3 +237,34 @@ def test_target_se_equals_fixed_counts_and_meets_target():
     tol = FP32_NSE * np.sqrt(se ** 2 + ref["se"] ** 2) + FP32_ABS
     d = mean - ref["mean"]
     assert np.all(np.abs(d.real) <= tol[..., 0]) and np.all(np.abs(d.imag) <= tol[..., 1])
+
+
+def test_batched_models_equal_each_model_alone():
+    # several raster models (random serving requests, K up to 6) in one launch:
+    # each entry's walks keep their streams, so every entry equals its own
+    # evaluation alone up to FP64 summation order; one entry against the oracle
+    rng = np.random.default_rng(7)
+    entries = []
+    for i in range(5):
+        r = I.random_request(rng, i)
+        nodes = r["nodes"][:: max(1, len(r["nodes"]) // 9)][:9]
+        npth = np.array([1, 33, 700, 1500, 2049, 900, 1200, 64, 3000])[: len(nodes)]
+        entries.append({"ctx": sdd.sdd_create(r["model"]), "model": r["model"], "nodes": nodes,
+                        "n_paths": npth, "node_ids": np.arange(len(nodes)) + 50 * i})
+    outs, st = sdd.sdd_batch_values(entries, 1e-3, 77)
+    assert st["walks"] == sum(int(e["n_paths"].sum()) for e in entries)
+    for e, (m, s_) in zip(entries, outs):
+        ma, sa, _ = sdd.sdd_interface_values(e["ctx"], e["nodes"], e["n_paths"], 1e-3, 77,
+                                             node_ids=e["node_ids"])
+        scale = max(1.0, np.abs(ma[np.isfinite(ma)]).max())
+        ok = e["n_paths"] > 1
+        assert np.allclose(m[ok], ma[ok], rtol=0, atol=1e-12 * scale)
+        assert np.allclose(s_[ok], sa[ok], rtol=1e-9, atol=0)
+    e = entries[2]
+    ref = O.interface_values(e["model"], e["nodes"], e["n_paths"], 1e-3, 77, urule=23,
+                             node_id0=int(e["node_ids"][0]))
+    m, s_ = outs[2]
+    ok = e["n_paths"] > 1
+    tol = FP32_NSE * np.sqrt(s_ ** 2 + ref["se"] ** 2) + FP32_ABS
+    d = m - ref["mean"]
+    assert np.all(np.abs(d.real)[ok] <= tol[..., 0][ok]) and np.all(np.abs(d.imag)[ok] <= tol[..., 1][ok])
