@@ -334,8 +334,8 @@ Launch choose_launch(const sdd_ctx *ctx, const sdd_config *cfg, double dt, long 
     L.kmax = kmax_override ? kmax_override : kmax_for(ctx->K);
     L.block = (cfg && cfg->block_threads) ? cfg->block_threads : 256;
     const int gcode = gcode_override >= 0 ? gcode_override : ctx->M.gcode;
-    int occ = L.f64 ? occupancy_f64(L.kmax, ctx->geo, L.block)
-                    : occupancy_f32(L.kmax, gcode, L.block);
+    int occ = L.f64 ? occupancy_f64(L.kmax, ctx->geo, L.block, ctx->E, ctx->K)
+                    : occupancy_f32(L.kmax, gcode, L.block, ctx->E, std::max(ctx->K, L.kmax));
     if (occ < 1) occ = 1;
     if (cfg && cfg->ctas_per_sm > 0 && cfg->ctas_per_sm < occ) occ = cfg->ctas_per_sm;
     L.grid = ctx->n_sm * occ;

@@ -127,8 +127,8 @@ cudaError_t launch_walk_f32(int kmax, int geo, const ModelDev &M, const WalkArgs
 cudaError_t launch_walk_f64(int kmax, int geo, const ModelDev &M, const WalkArgs &A, int grid,
                             int block, cudaStream_t s);
 // Largest number of resident CTAs per SM for a configuration.
-int occupancy_f32(int kmax, int gcode, int block);
-int occupancy_f64(int kmax, int geo, int block);
+int occupancy_f32(int kmax, int gcode, int block, int E, int K);
+int occupancy_f64(int kmax, int geo, int block, int E, int K);
 size_t smem_bytes(bool f64, int kmax, int block);
 
 }  // namespace sdd

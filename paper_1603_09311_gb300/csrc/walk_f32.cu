@@ -32,10 +32,12 @@ __device__ __forceinline__ float uni23(uint32_t w) { return one_plus(w) - 0.9999
 // Occupation counters.  KMAX = 2: the step count of material 1.  KMAX = 3, 4:
 // power sums s_p = sum over steps of m^p (p = 1 .. KMAX-1), which determine
 // the counts of materials 1 .. KMAX-1 (a Vandermonde system, solved once at
-// the exit).  KMAX = 8: one counter per material.
+// the exit).  KMAX = 8: a per-lane histogram in shared memory, one shared
+// atomic add per step.
 template <int KMAX>
 struct Occupancy {
     uint32_t s[KMAX > 1 ? KMAX - 1 : 1];
+    __device__ __forceinline__ void bind(uint32_t) {}
     __device__ __forceinline__ void clear() {
 #pragma unroll
         for (int j = 0; j < (KMAX > 1 ? KMAX - 1 : 1); ++j) s[j] = 0;
@@ -76,6 +78,27 @@ struct Occupancy {
         } else {
 #pragma unroll
             for (int j = 0; j < KMAX - 1; ++j) c[j] = s[j];
+        }
+    }
+};
+
+template <>
+struct Occupancy<8> {
+    uint32_t base;  // shared address of hist[0][lane]; material m at base + 128 m
+    __device__ __forceinline__ void bind(uint32_t a) { base = a; }
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) asm volatile("st.shared.u32 [%0], %1;" ::"r"(base + 128u * j), "r"(0u));
+    }
+    __device__ __forceinline__ void add(int m) {
+        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(base + ((uint32_t)m << 7)), "r"(1u));
+    }
+    __device__ __forceinline__ void counts(uint32_t *c) const {
+#pragma unroll
+        for (int j = 1; j < 8; ++j) {
+            uint32_t v;
+            asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(base + 128u * j));
+            c[j - 1] = v;
         }
     }
 };
@@ -130,6 +153,7 @@ struct WalkerF32 {
     }
 
     __device__ __forceinline__ void counts(uint32_t *c) const { occ.counts(c); }
+    __device__ __forceinline__ void bind(uint32_t a) { occ.bind(a); }
 
     __device__ __forceinline__ void start(const ModelDev &M, const WalkArgs &A, double x0,
                                           double z0, uint32_t path, uint32_t node_id, int model) {
@@ -157,19 +181,21 @@ struct WalkerF32 {
         ei.mlast = material(M, X, Z);
     }
 
-    // The step (X, Z) -> (Xn, Zn) came within reach of a wall.  Overshoot:
+    // The step (X, Z) -> (Xn, Zn) came within reach of a wall (rare; taken by
+    // few lanes of a warp at a time, so kept short).  Overshoot (dn <= 0):
     // theta_w = d_w / (d_w - d'_w) over the walls with d'_w <= 0, smallest
     // first, ties to the first of left, right, top, bottom.  Both inside: the
-    // Brownian-bridge test with one uniform for all walls, hit iff
-    // 2 d_w d'_w / dt <= -ln U for the smallest product.  U is made of the 18
-    // bits of the step's two Philox words that the normals leave unused:
+    // Brownian-bridge test with one uniform for all walls: the walk touched a
+    // wall iff 2 d_w d'_w / dt <= -ln U for the smallest product, tested as
+    // U <= exp(-2 d_w d'_w / dt).  U is made of the 18 bits of the step's two
+    // Philox words that the normals leave unused:
     // U = (high 9 bits of wa : high 9 bits of wb + 1/2) 2^-18.
     __device__ __forceinline__ bool near_wall(const ModelDev &M, const WalkArgs &A, float Xn,
-                                              float Zn, uint32_t wa, uint32_t wb,
+                                              float Zn, float dn, uint32_t wa, uint32_t wb,
                                               ExitInfo<float> &ei) const {
         const float d[4] = {X + M.fhw, M.fhw - X, Z + M.fhh, M.fhh - Z};
         const float e[4] = {Xn + M.fhw, M.fhw - Xn, Zn + M.fhh, M.fhh - Zn};
-        if (e[0] <= 0.f || e[1] <= 0.f || e[2] <= 0.f || e[3] <= 0.f) {
+        if (dn <= 0.f) {
             float best = 2.0f;
             int bw = 0;
 #pragma unroll
@@ -182,21 +208,17 @@ struct WalkerF32 {
             place(M, Xn, Zn, best, bw, ei);
             return true;
         }
-        float best = d[0] * e[0];
-        int bw = 0;
-#pragma unroll
-        for (int w = 1; w < 4; ++w) {
-            const float p = d[w] * e[w];
-            if (p < best) { best = p; bw = w; }
-        }
-        const float es = best * A.f_c2dt;
+        const float p0 = d[0] * e[0], p1 = d[1] * e[1], p2 = d[2] * e[2], p3 = d[3] * e[3];
+        const float pmin = fminf(fminf(p0, p1), fminf(p2, p3));
+        const float es = pmin * A.f_c2dt;
         const uint32_t u18 = ((wa >> 23) << 9) | (wb >> 23);
-        const float L = -logf(fmaf((float)u18, 3.814697265625e-06f, 1.9073486328125e-06f));
-        if (es <= L) {
-            place(M, Xn, Zn, es / L, bw, ei);
-            return true;
-        }
-        return false;
+        const float U = fmaf((float)u18, 3.814697265625e-06f, 1.9073486328125e-06f);
+        if (U > __expf(-es)) return false;
+        // a hit: the wall of the smallest product (first in wall order) and
+        // the fraction theta = (2 d d' / dt) / (-ln U)
+        const int bw = p0 == pmin ? 0 : (p1 == pmin ? 1 : (p2 == pmin ? 2 : 3));
+        place(M, Xn, Zn, es / -logf(U), bw, ei);
+        return true;
     }
 
     // One Euler step driven by the Philox words (wa, wb); sub = 0 or 1 within
@@ -214,7 +236,7 @@ struct WalkerF32 {
         const float Zn = fmaf(-r, sn, Z);
         const float dn = fminf(M.fhw - fabsf(Xn), M.fhh - fabsf(Zn));
         if (dmin * dn <= A.f_bthr) {
-            if (near_wall(M, A, Xn, Zn, wa, wb, ei)) {
+            if (near_wall(M, A, Xn, Zn, dn, wa, wb, ei)) {
                 ei.nocc = n + sub;
                 return true;
             }
@@ -311,7 +333,7 @@ struct WalkerF32 {
 template <int KMAX, int GC>
 static cudaError_t launch_one(const ModelDev &M, const WalkArgs &A, int grid, int block,
                               cudaStream_t s) {
-    const size_t sm = shared_bytes<float, KMAX>(block / 32);
+    const size_t sm = shared_bytes<float, KMAX>(block / 32, M.E, M.K);
     auto k = walk_kernel<WalkerF32<KMAX, GC>>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -320,8 +342,8 @@ static cudaError_t launch_one(const ModelDev &M, const WalkArgs &A, int grid, in
 }
 
 template <int KMAX, int GC>
-static int occ_one(int block) {
-    const size_t sm = shared_bytes<float, KMAX>(block / 32);
+static int occ_one(int block, int E, int K) {
+    const size_t sm = shared_bytes<float, KMAX>(block / 32, E, K);
     auto k = walk_kernel<WalkerF32<KMAX, GC>>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
         return 0;
@@ -360,8 +382,8 @@ cudaError_t launch_walk_f32(int kmax, int /*geo*/, const ModelDev &M, const Walk
     return cudaErrorInvalidValue;
 }
 
-int occupancy_f32(int kmax, int gcode, int block) {
-    SDD_DISPATCH(occ_one, block)
+int occupancy_f32(int kmax, int gcode, int block, int E, int K) {
+    SDD_DISPATCH(occ_one, block, E, K)
     return 0;
 }
 

@@ -62,6 +62,8 @@ struct WalkerF64 {
         }
     }
 
+    __device__ __forceinline__ void bind(uint32_t) {}
+
     __device__ __forceinline__ void counts(uint32_t *c) const {
 #pragma unroll
         for (int j = 0; j < (KMAX > 1 ? KMAX - 1 : 1); ++j) c[j] = cnt[j];
@@ -217,7 +219,7 @@ struct WalkerF64 {
 template <int KMAX, int GEO>
 static cudaError_t launch_one(const ModelDev &M, const WalkArgs &A, int grid, int block,
                               cudaStream_t s) {
-    const size_t sm = shared_bytes<double, KMAX>(block / 32);
+    const size_t sm = shared_bytes<double, KMAX>(block / 32, M.E, M.K);
     auto k = walk_kernel<WalkerF64<KMAX, GEO>>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -226,8 +228,8 @@ static cudaError_t launch_one(const ModelDev &M, const WalkArgs &A, int grid, in
 }
 
 template <int KMAX, int GEO>
-static int occ_one(int block) {
-    const size_t sm = shared_bytes<double, KMAX>(block / 32);
+static int occ_one(int block, int E, int K) {
+    const size_t sm = shared_bytes<double, KMAX>(block / 32, E, K);
     auto k = walk_kernel<WalkerF64<KMAX, GEO>>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
         return 0;
@@ -255,8 +257,8 @@ cudaError_t launch_walk_f64(int kmax, int geo, const ModelDev &M, const WalkArgs
     return cudaErrorInvalidValue;
 }
 
-int occupancy_f64(int kmax, int geo, int block) {
-    SDD_DISPATCH(occ_one, block)
+int occupancy_f64(int kmax, int geo, int block, int E, int K) {
+    SDD_DISPATCH(occ_one, block, E, K)
     return 0;
 }
 

@@ -130,20 +130,28 @@ struct WarpState {
     int32_t queue_empty;
 };
 
+// The model's rates [E][K] and boundary constants [E], staged in shared
+// memory ahead of the warps' areas; sized by the model's E and K.
 struct SharedTables {
-    double kappa[kMaxE * kMaxK];
-    EvalDev ev[kMaxE];
+    double *kappa;
+    EvalDev *ev;
 };
+
+__host__ __device__ constexpr size_t tables_bytes(int E, int K) {
+    return ((size_t)E * K * sizeof(double) + 15) / 16 * 16 + (size_t)E * sizeof(EvalDev);
+}
 
 template <class Real, int KMAX>
 struct WarpSmem {
     Ring<Real, KMAX> ring;
     WarpState st;
+    uint32_t hist[KMAX == 8 ? 8 : 1][32];  // per-lane step counts of up to 8 materials
 };
 
+
 template <class Real, int KMAX>
-__host__ __device__ constexpr size_t shared_bytes(int warps) {
-    return sizeof(SharedTables) + (size_t)warps * sizeof(WarpSmem<Real, KMAX>);
+__host__ __device__ constexpr size_t shared_bytes(int warps, int E, int K) {
+    return (tables_bytes(E, K) + 15) / 16 * 16 + (size_t)warps * sizeof(WarpSmem<Real, KMAX>);
 }
 
 // Exit information handed from a walker to the scheduler.
@@ -161,6 +169,7 @@ struct ExitInfo {
 //   iterate(M, A, path, ExitInfo&) -> 0 running, 1 exited, 2 truncated
 //     (two Euler steps per call)
 //   counts(c): steps spent in materials 1..KMAX-1 (at the exit)
+//   bind(a): shared-memory address of the lane's occupancy histogram
 //   static sample(M, T, A, model, e, x, z, th, wall, mlast, counts) -> double2
 //   static to_abs(M, x, z, ax, az)
 template <class W>
@@ -169,9 +178,11 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
     using Real = typename W::Real;
     constexpr int KMAX = W::KMAX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SharedTables &T = *reinterpret_cast<SharedTables *>(smem_raw);
-    WarpSmem<Real, KMAX> &WS =
-        reinterpret_cast<WarpSmem<Real, KMAX> *>(smem_raw + sizeof(SharedTables))[threadIdx.x >> 5];
+    SharedTables T;
+    T.kappa = reinterpret_cast<double *>(smem_raw);
+    T.ev = reinterpret_cast<EvalDev *>(smem_raw + ((size_t)M.E * M.K * sizeof(double) + 15) / 16 * 16);
+    WarpSmem<Real, KMAX> &WS = reinterpret_cast<WarpSmem<Real, KMAX> *>(
+        smem_raw + (tables_bytes(M.E, M.K) + 15) / 16 * 16)[threadIdx.x >> 5];
     Ring<Real, KMAX> &R = WS.ring;
     WarpState &S = WS.st;
 
@@ -200,6 +211,7 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
 
     // per-lane walk state
     W w;
+    w.bind((uint32_t)__cvta_generic_to_shared(&WS.hist[0][lane]));
     bool active = false;
     int tag = 0;
     int model = 0;
@@ -349,9 +361,10 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
         if (active) st = w.iterate(M, A, path, ei);
         const unsigned em = __ballot_sync(kFull, st != 0);
         if (em == 0) continue;
+        const int nex = __popc(em);
+        if (st != 0) active = false;
 
         // 1. records of the walks that ended
-        const int nex = __popc(em);
         const uint32_t tail = S.tail;
         if (st != 0) {
             const int slot = (tail + __popc(em & lt_mask)) & (kRing - 1);
@@ -368,7 +381,6 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
 #pragma unroll
             for (int j = 1; j < KMAX; ++j) R.cnt[j - 1][slot] = c[j - 1];
             S.steps[lane] += (unsigned long long)ei.nocc + (tr ? 0ull : 1ull);
-            active = false;
         }
         const unsigned t1 = __ballot_sync(kFull, st != 0 && tag == 1);
         const unsigned tr0 = __ballot_sync(kFull, st == 2 && tag == 0);
