@@ -335,7 +335,8 @@ typedef struct {
 } sdd_server_stats;
 
 /* Create a server on the current device: worker thread, n_streams streams,
- * a raster arena of max_requests x nx x nz bytes and per-stream scratch.
+ * an arena of max_requests material maps (two-level tile form, at most
+ * about nx x nz + nx x nz / 64 bytes each) and per-stream scratch.
  * Errors: SDD_E_ARG, SDD_E_OOM, SDD_E_CUDA. */
 sdd_status sdd_server_create(const sdd_server_config *cfg, sdd_server **out);
 

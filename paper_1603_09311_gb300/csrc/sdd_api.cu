@@ -19,6 +19,30 @@
 
 using namespace sdd;
 
+void sdd::build_tiles(const int8_t *raster, int nx, int nz, std::vector<uint32_t> &coarse,
+                      std::vector<uint8_t> &pool) {
+    const int ntx = (nx + kTile - 1) / kTile, ntz = (nz + kTile - 1) / kTile;
+    coarse.assign((size_t)ntx * ntz, 0u);
+    pool.clear();
+    uint8_t cells[kTile * kTile];
+    for (int tz = 0; tz < ntz; ++tz)
+        for (int tx = 0; tx < ntx; ++tx) {
+            bool uniform = true;
+            for (int a = 0; a < kTile; ++a)
+                for (int b = 0; b < kTile; ++b) {
+                    const int iz = std::min(tz * kTile + a, nz - 1), ix = std::min(tx * kTile + b, nx - 1);
+                    cells[a * kTile + b] = (uint8_t)raster[(size_t)iz * nx + ix];
+                    uniform = uniform && cells[a * kTile + b] == cells[0];
+                }
+            if (uniform) {
+                coarse[(size_t)tz * ntx + tx] = kTileUniform | cells[0];
+            } else {
+                coarse[(size_t)tz * ntx + tx] = (uint32_t)(pool.size() / (kTile * kTile));
+                pool.insert(pool.end(), cells, cells + kTile * kTile);
+            }
+        }
+}
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -68,7 +92,7 @@ struct sdd_ctx {
     ModelDev M;
     int K = 0, E = 0;
     int geo = GEO_SHAPES;
-    DevBuf raster;
+    DevBuf raster, tiles;
     // per-call scratch
     DevBuf items, slots, trunc, counters, queue, err, nodes, node_ids, mean, se;
     DevBuf rec_steps, rec_counts, rec_exit, rec_wall, rec_mlast;
@@ -549,6 +573,24 @@ sdd_status sdd_create(const sdd_model_desc *model, sdd_ctx **out) {
                                                   : cuda_fail(e, "raster upload");
         }
         c->M.raster = (const int8_t *)c->raster.p;
+        std::vector<uint32_t> coarse;
+        std::vector<uint8_t> pool;
+        build_tiles(model->raster, model->nx, model->nz, coarse, pool);
+        const size_t cb = (coarse.size() * sizeof(uint32_t) + 255) / 256 * 256;
+        e = c->tiles.ensure(cb + pool.size() + 16);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(c->tiles.p, coarse.data(), coarse.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess && !pool.empty())
+            e = cudaMemcpy((unsigned char *)c->tiles.p + cb, pool.data(), pool.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            sdd_destroy(c);
+            return e == cudaErrorMemoryAllocation ? fail(SDD_E_OOM, "tile map allocation")
+                                                  : cuda_fail(e, "tile map upload");
+        }
+        c->M.tcoarse = (const uint32_t *)c->tiles.p;
+        c->M.tpool = (const uint8_t *)c->tiles.p + cb;
+        c->M.ntx = (model->nx + kTile - 1) / kTile;
+        c->M.tpool_off = (uint32_t)cb;
     }
     *out = c;
     return SDD_OK;
@@ -557,7 +599,7 @@ sdd_status sdd_create(const sdd_model_desc *model, sdd_ctx **out) {
 void sdd_destroy(sdd_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    DevBuf *bufs[] = {&c->raster, &c->items, &c->slots, &c->trunc, &c->counters, &c->queue,
+    DevBuf *bufs[] = {&c->raster, &c->tiles, &c->items, &c->slots, &c->trunc, &c->counters, &c->queue,
                       &c->err, &c->nodes, &c->node_ids, &c->mean, &c->se, &c->rec_steps,
                       &c->rec_counts, &c->rec_exit, &c->rec_wall, &c->rec_mlast,
                       &c->batch_models};
@@ -1063,6 +1105,8 @@ extern "C" sdd_status sdd_batch_values(const sdd_batch_entry *entries, int32_t n
         BatchModel &B = table[i];
         std::memset(&B, 0, sizeof(B));
         B.raster = c->M.raster;
+        B.tcoarse = c->M.tcoarse;
+        B.tpool = c->M.tpool;
         B.K = c->K;
         for (int k = 0; k < c->E * c->K; ++k) B.kappa[k] = c->M.kappa[k];
         for (int k = 0; k < c->E; ++k) B.ev[k] = c->M.ev[k];
@@ -1178,7 +1222,8 @@ struct sdd_server {
     sdd_server_config cfg;
     int device = 0;
     sdd_ctx *tmpl = nullptr;       // a context with the server's model shape (launch planning)
-    DevBuf arena;                  // max_requests rasters of nx * nz bytes
+    DevBuf arena;                  // max_requests tile maps of slot_bytes each
+    size_t coarse_bytes = 0, slot_bytes = 0;
     std::vector<int> free_slots;
     std::mutex mu;
     std::condition_variable cv, done_cv;
@@ -1197,7 +1242,7 @@ namespace {
 
 int64_t request_bytes(const sdd_server *srv, int32_t n_nodes) {
     const int E = srv->cfg.n_eval;
-    return (int64_t)srv->cfg.nx * srv->cfg.nz + (int64_t)n_nodes * (16 + 4 + 8 + 8 + 32 * E) +
+    return (int64_t)srv->slot_bytes + (int64_t)n_nodes * (16 + 4 + 8 + 8 + 32 * E) +
            (int64_t)sizeof(BatchModel);
 }
 
@@ -1467,7 +1512,10 @@ extern "C" sdd_status sdd_server_create(const sdd_server_config *cfg, sdd_server
         return st;
     }
     srv->device = srv->tmpl->device;
-    cudaError_t e = srv->arena.ensure((size_t)cfg->max_requests * cfg->nx * cfg->nz);
+    const size_t ntx = (cfg->nx + kTile - 1) / kTile, ntz = (cfg->nz + kTile - 1) / kTile;
+    srv->coarse_bytes = (ntx * ntz * sizeof(uint32_t) + 255) / 256 * 256;
+    srv->slot_bytes = srv->coarse_bytes + ntx * ntz * kTile * kTile;  // pool of every tile mixed at most
+    cudaError_t e = srv->arena.ensure((size_t)cfg->max_requests * srv->slot_bytes);
     if (e != cudaSuccess) {
         sdd_server_destroy(srv);
         return fail(SDD_E_OOM, "raster arena allocation failed");
@@ -1577,13 +1625,21 @@ extern "C" sdd_status sdd_server_submit(sdd_server *srv, const sdd_request_desc 
     srv->free_slots.pop_back();
     srv->bytes_in_use += r->bytes;
     lk.unlock();
-    // the slot is reserved: upload the raster without holding the lock
-    unsigned char *ras = (unsigned char *)srv->arena.p + (size_t)r->slot * c.nx * c.nz;
-    r->bm.raster = (const int8_t *)ras;
+    // the slot is reserved: build and upload the tile map without holding the lock
+    std::vector<uint32_t> coarse;
+    std::vector<uint8_t> pool;
+    build_tiles(m->raster, c.nx, c.nz, coarse, pool);
+    unsigned char *base = (unsigned char *)srv->arena.p + (size_t)r->slot * srv->slot_bytes;
+    r->bm.raster = nullptr;
+    r->bm.tcoarse = (const uint32_t *)base;
+    r->bm.tpool = base + srv->coarse_bytes;
     int prev = -1;
     cudaError_t e = cudaGetDevice(&prev);
     if (e == cudaSuccess && prev != srv->device) e = cudaSetDevice(srv->device);
-    if (e == cudaSuccess) e = cudaMemcpy(ras, m->raster, (size_t)c.nx * c.nz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(base, coarse.data(), coarse.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !pool.empty())
+        e = cudaMemcpy(base + srv->coarse_bytes, pool.data(), pool.size(), cudaMemcpyHostToDevice);
     if (prev >= 0 && prev != srv->device) cudaSetDevice(prev);
     lk.lock();
     if (e != cudaSuccess) {

@@ -6,6 +6,8 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 namespace sdd {
@@ -62,9 +64,18 @@ struct EvalDev {
 
 constexpr int kMaxBatchModels = 256;
 
+// Two-level form of an int8 raster, identical cell by cell: tiles of
+// kTile x kTile cells; coarse[tz][tx] = kTileUniform | material for a tile of
+// one material, else the index of the tile's kTile^2 cells in the pool.
+constexpr int kTileShift = 4;
+constexpr int kTile = 1 << kTileShift;
+constexpr uint32_t kTileUniform = 0x80000000u;
+
 // Per-model data of a batched launch (device memory).
 struct BatchModel {
     const int8_t *raster;
+    const uint32_t *tcoarse;
+    const uint8_t *tpool;
     int32_t K, pad;
     double kappa[kMaxE * kMaxK];  // [E][K] of this model
     EvalDev ev[kMaxE];
@@ -79,6 +90,11 @@ struct ModelDev {
     int32_t gcode;  // GeoCode of the model
     ShapeDev shapes[kMaxShapes];
     const int8_t *raster;
+    const uint32_t *tcoarse;  // two-level form of the raster (single-precision walk)
+    const uint8_t *tpool;
+    int32_t ntx;              // tiles per raster row
+    uint32_t tpool_off;       // bytes from the coarse table to the pool (same for every model
+                              // of a batch: the coarse table rounded up to 256 bytes)
     int32_t nx, nz;
     double sx, sz;  // nx / (xmax - xmin), nz / (zmax - zmin)
     int32_t g_kind;
@@ -120,6 +136,12 @@ struct WalkArgs {
     int32_t *rec_mlast;
     const BatchModel *models;  // batched launch: the models the items refer to
 };
+
+// Two-level tile map of an int8 raster [nz][nx] (host): coarse table
+// [ceil(nz/kTile)][ceil(nx/kTile)] and pool of mixed tiles (cells beyond the
+// raster edge repeat the nearest edge cell).
+void build_tiles(const int8_t *raster, int nx, int nz, std::vector<uint32_t> &coarse,
+                 std::vector<uint8_t> &pool);
 
 // Launchers (one per precision translation unit).
 cudaError_t launch_walk_f32(int kmax, int geo, const ModelDev &M, const WalkArgs &A, int grid,

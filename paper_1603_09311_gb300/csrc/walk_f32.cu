@@ -114,7 +114,7 @@ struct WalkerF32 {
     uint32_t n;        // Euler steps accepted (even at the start of iterate)
     Occupancy<KMAX> occ;
     uint32_t nid, pre_x, pre_y;
-    const int8_t *rast;  // GC_RASTER_MULTI: the raster of this walk's model
+    const uint32_t *tco;  // GC_RASTER_MULTI: the tile map of this walk's model
 
     __device__ __forceinline__ static bool in_rect(const ShapeDev &S, float X, float Z) {
         return X >= S.f[0] && X < S.f[1] && Z >= S.f[2] && Z < S.f[3];
@@ -132,7 +132,14 @@ struct WalkerF32 {
             int iz = __float_as_int(fmaf(Z, M.fsz, M.foz) + 12582912.0f) - 0x4B400000;
             ix = min(ix, M.nx - 1);
             iz = min(iz, M.nz - 1);
-            return (int)__ldg((GC == GC_RASTER_MULTI ? rast : M.raster) + iz * M.nx + ix);
+            // two-level lookup: the coarse entry (L1-resident) is the material of
+            // a uniform tile, else the tile's cells in the pool
+            const uint32_t *co = GC == GC_RASTER_MULTI ? tco : M.tcoarse;
+            const uint32_t c = __ldg(co + (iz >> kTileShift) * M.ntx + (ix >> kTileShift));
+            if (c & kTileUniform) return (int)(c & 0xffu);
+            const uint8_t *po = reinterpret_cast<const uint8_t *>(co) + M.tpool_off;
+            return (int)__ldg(po + ((size_t)c << (2 * kTileShift)) + ((iz & (kTile - 1)) << kTileShift) +
+                              (ix & (kTile - 1)));
         }
         const int m = (Z >= M.fzs) ? M.bg_earth : M.bg_air;
         if (GC == GC_LAYER) return m;
@@ -157,7 +164,7 @@ struct WalkerF32 {
 
     __device__ __forceinline__ void start(const ModelDev &M, const WalkArgs &A, double x0,
                                           double z0, uint32_t path, uint32_t node_id, int model) {
-        if (GC == GC_RASTER_MULTI) rast = A.models[model].raster;
+        if (GC == GC_RASTER_MULTI) tco = A.models[model].tcoarse;
         X = (float)(x0 - M.xc);
         Z = (float)(z0 - M.zc);
         dmin = fminf(M.fhw - fabsf(X), M.fhh - fabsf(Z));

@@ -268,3 +268,20 @@ def test_batched_models_equal_each_model_alone():
     tol = FP32_NSE * np.sqrt(s_ ** 2 + ref["se"] ** 2) + FP32_ABS
     d = m - ref["mean"]
     assert np.all(np.abs(d.real)[ok] <= tol[..., 0][ok]) and np.all(np.abs(d.imag)[ok] <= tol[..., 1][ok])
+
+
+def test_fp32_raster_walks_count_materials_like_the_oracle():
+    # the single-precision walk reads rasters through a two-level tile map;
+    # on the same streams its per-material step counts must equal the oracle's
+    # (which reads the raster cell by cell) for walks whose steps agree
+    rng = np.random.default_rng(5)
+    r = [I.random_request(rng, i) for i in range(4)][3]  # six materials
+    ctx = sdd.sdd_create(r["model"])
+    assert ctx.K == 6
+    for (x0, z0) in r["nodes"][:: max(1, len(r["nodes"]) // 3)][:3]:
+        g = sdd.sdd_walk_records(ctx, x0, z0, 9, 0, 3000, 1e-3, 31)
+        o = O.walk_records(r["model"], (x0, z0), 9, 0, 3000, 1e-3, 31, urule=23)
+        same = g["steps"] == o["steps"]
+        assert same.mean() >= 0.9
+        eq = np.all(g["counts"][same] == o["counts"][same], axis=1)
+        assert eq.mean() >= 0.95, eq.mean()
