@@ -167,7 +167,7 @@ def serving(sdd, n_requests: int, seed: int = 5):
 
     def make_server():
         return sdd.Server(domain=I.DOMAIN, nx=I.RASTER_NX, nz=I.RASTER_NZ, dt=1e-3, seed=seed,
-                          max_requests=64, n_streams=2, max_batch_models=64)
+                          max_requests=64, n_streams=4, max_batch_models=64)
 
     def open_loop(srv, arrivals):
         t0 = time.perf_counter()
@@ -214,14 +214,34 @@ def serving(sdd, n_requests: int, seed: int = 5):
         free_at = start + s_
         base_lat.append(free_at - a)
     base_lat = np.array(base_lat)
+    # the plain form: one node per launch (pilot + top-up per node), on the
+    # first requests only (it is far slower)
+    n_plain = min(3, len(reqs))
+    t_plain, nodes_plain = 0.0, 0
+    for r in reqs[:n_plain]:
+        ctx = sdd.sdd_create(r["model"])
+        t = time.perf_counter()
+        for j in range(len(r["nodes"])):
+            sdd.sdd_interface_values_target(ctx, r["nodes"][j:j + 1], kw["n_pilot"], kw["n_max"],
+                                            kw["target_se"], 1e-3, seed, node_ids=r["node_ids"][j:j + 1])
+        t_plain += time.perf_counter() - t
+        nodes_plain += len(r["nodes"])
+        ctx.close()
+    t_served = sum(service[:n_plain])
+    total_nodes = sum(len(r["nodes"]) for r in reqs)
     return {"requests": len(reqs), "arrivals": "Poisson at 0.7 x closed-loop capacity",
             "capacity_req_per_s": cap, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
             "p99_ms": 1e3 * float(np.percentile(lat, 99)),
             "steps_per_s": steps / span, "launches": int(st1["launches"] - st0["launches"]),
+            "node_solves_per_s": total_nodes / span,
             "baseline_one_request_per_launch": {
                 "capacity_req_per_s": len(reqs) / sum(service),
                 "p50_ms": 1e3 * float(np.percentile(base_lat, 50)),
                 "p99_ms": 1e3 * float(np.percentile(base_lat, 99))},
+            "baseline_one_node_per_launch": {
+                "requests": n_plain, "nodes": nodes_plain,
+                "node_solves_per_s": nodes_plain / t_plain,
+                "slowdown_vs_one_request_per_launch": t_plain / t_served},
             "workload": "random raster requests (1024x768 int8, 1-4 shapes), 16-1024 nodes, "
                         "target SE 1e-3, pilot 4096, cap 1e6, dt 1e-3"}
 
@@ -268,6 +288,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sdd", choices=["sdd", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--graph", action="store_true", help="run each step as a CUDA graph")
     ap.add_argument("--serve-requests", type=int, default=24,
                     help="requests of the serving measurement (0 skips it)")
     ap.add_argument("--small", action="store_true",
@@ -311,8 +333,14 @@ def main():
         sdd.sdd_interface_values_device(ctx, d_nodes.data_ptr(), n, w["n_paths"], w["dt"], seed,
                                         d_mean.data_ptr(), d_se.data_ptr(),
                                         d_node_ids_ptr=d_ids.data_ptr(),
-                                        d_counters_ptr=d_cnt[k].data_ptr(), stream=stream.cuda_stream)
+                                        d_counters_ptr=d_cnt[k].data_ptr(), stream=stream.cuda_stream,
+                                        use_graph=int(args.graph))
 
+    tuned = None
+    if not args.no_autotune:
+        # launch shape for this workload (untimed; the context keeps it)
+        cfg_t, rate_t = sdd.sdd_autotune(ctx, w["nodes"], w["n_paths"], w["dt"], w["seed"] + 999)
+        tuned = dict(cfg_t, walk_steps_per_s=rate_t)
     for i in range(args.warmup):
         step(w["seed"] + 1000 + i, i)
     torch.cuda.synchronize()
@@ -395,7 +423,9 @@ def main():
                        "walks_per_step": int(n * w["n_paths"][0]),
                        "steps_per_step": int(steps_done_one),
                        "l2": "flushed between steps (256 MB write)",
-                       "precision": "FP32 walk, FP64 sums"},
+                       "precision": "FP32 walk, FP64 sums",
+                       "launch": tuned if tuned else "default shape",
+                       "cuda_graph": bool(args.graph)},
             "node_solves": {"value": met * world / solve_s, "unit": "interface-node solves/s",
                             "target_se": 1e-3, "nodes_met": f"{met}/{n}", "pilot": 4096,
                             "n_max": 4_000_000, "walks_per_solve_set": walks_t,

@@ -123,6 +123,9 @@ typedef struct {
     int32_t block_threads; /* threads per CTA (multiple of 32, <= 256); 0 = auto */
     int32_t ctas_per_sm;   /* persistent CTAs per SM; 0 = occupancy limit */
     int32_t chunk_paths;   /* paths per work item; 0 = auto */
+    int32_t use_graph;     /* sdd_interface_values_device: 1 = run the device work as a
+                              CUDA graph cached in the context (updated in place on
+                              later calls, re-instantiated only when its shape changes) */
 } sdd_config;
 
 typedef struct {
@@ -227,6 +230,23 @@ typedef struct {
 sdd_status sdd_batch_values(const sdd_batch_entry *entries, int32_t n_entries, double dt,
                             uint64_t seed, const sdd_config *cfg, sdd_stats *stats);
 
+/* Pick the launch shape for a workload by timing it: threads per CTA in
+ * {128, 192, 256} x work items per warp in {2, 4, 6, 10, 16} (which sets the
+ * paths per work item), two runs each of sdd_interface_values on the given
+ * nodes.  The fastest shape is kept in the context and used by later calls
+ * whose block_threads and chunk_paths are automatic; with the environment
+ * variable SDD_TUNE_CACHE naming a file, it is also appended there and read
+ * by new contexts with the same device, lookup program, materials bound,
+ * evaluations, precision and decade of dt.
+ *   base   options whose block_threads and chunk_paths are 0, or NULL
+ *   best   out (nullable): base with the chosen block_threads and the
+ *          chunk_paths they give for this workload
+ *   best_steps_per_s  out (nullable): walk-steps/s of the chosen shape
+ * Library-level design choice: the paper has no launch shapes. */
+sdd_status sdd_autotune(sdd_ctx *ctx, const double *nodes_xz, int32_t n_nodes,
+                        const int64_t *n_paths, double dt, uint64_t seed, const sdd_config *base,
+                        sdd_config *best, double *best_steps_per_s);
+
 /* Per-path records of walks (node id, paths p0 .. p0+count-1) started at
  * (x0, z0), host buffers, synchronous -- the individual steps of Sec. 3.1
  * for comparison path by path:
@@ -280,11 +300,13 @@ sdd_status sdd_interface_values_noalloc(sdd_ctx *ctx, const double *d_nodes_xz,
  *
  * A server evaluates requests -- one raster model and its interface nodes
  * each -- on one device.  Requests are admitted while a slot (and, with
- * max_bytes, device memory) is free; a worker thread packs the runnable work
- * of all admitted requests (the pilot or fixed-count walks of new requests,
- * the top-up walks of requests whose pilot has finished) into launches of
- * the persistent walk kernel over many models, with up to n_streams launches
- * in flight, so new requests start while earlier ones are still on the GPU.
+ * max_bytes, device memory) is free.  Each phase of a request (its pilot or
+ * fixed-count walks, then the top-up walks sized from the pilot) is cut
+ * into pieces of whole nodes of at most max_batch_walks walks; a worker
+ * thread packs queued pieces, first in first out, into launches of the
+ * persistent walk kernel over many models, with up to n_streams launches in
+ * flight, so new requests start while earlier ones are still on the GPU and
+ * the tail of one launch overlaps the next.
  * Every walk uses the server's seed and the request's node ids as Philox
  * stream, so a request's result does not depend on what it was batched with
  * (up to FP64 summation order).  All requests must match the server's
@@ -301,6 +323,8 @@ typedef struct {
     int64_t max_bytes;        /* device bytes admitted requests may hold; 0 = slots only */
     int32_t n_streams;        /* batched launches in flight at once, 1..8 */
     int32_t max_batch_models; /* requests per launch, 1..256 */
+    int64_t max_batch_walks;  /* walks per launch; a request's phase is cut into pieces
+                                 of whole nodes to fit; 0 = 2^24 */
     double dt;                /* Euler time step of every walk */
     uint64_t seed;            /* Philox key of every walk */
     sdd_config launch;        /* launch options; precision must be SDD_FP32 */

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <complex>
 #include <cstdio>
+#include <cstdlib>
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -108,6 +109,10 @@ struct sdd_ctx {
     uint32_t plan_offset = 0;
     bool plan_valid = false;
     uint64_t last_h2d = 0;
+    cudaGraphExec_t graph_exec = nullptr;  // device work of the last graph-mode call
+    uint64_t graph_updates = 0, graph_instantiations = 0;
+    int tune_block = 0, tune_k = 0;        // autotuned threads per CTA, items per warp (0: none)
+    bool tune_file_read = false;
 };
 
 namespace {
@@ -351,12 +356,48 @@ struct Launch {
     int64_t max_steps;
 };
 
+// Key of a launch shape in the tuning cache file: device, lookup program,
+// materials bound, evaluations, precision and the decade of dt.
+std::string tune_key(const sdd_ctx *ctx, int kmax, int gcode, bool f64, double dt) {
+    char b[160];
+    std::snprintf(b, sizeof(b), "sm%d gc%d k%d e%d p%d dt%d", ctx->n_sm, gcode, kmax, ctx->E, f64 ? 1 : 0,
+                  (int)std::floor(std::log10(dt)));
+    return b;
+}
+
+// The tuned shape for this context from SDD_TUNE_CACHE (read once).
+void tune_from_file(sdd_ctx *ctx, int kmax, int gcode, bool f64, double dt) {
+    if (ctx->tune_file_read) return;
+    ctx->tune_file_read = true;
+    const char *path = std::getenv("SDD_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    const std::string key = tune_key(ctx, kmax, gcode, f64, dt);
+    char line[256];
+    while (std::fgets(line, sizeof(line), f)) {
+        int blk = 0, k = 0;
+        const char *bar = std::strchr(line, '|');
+        if (!bar) continue;
+        if (std::string(line, bar - line) == key && std::sscanf(bar + 1, "%d %d", &blk, &k) == 2 &&
+            blk >= 32 && blk <= 256 && blk % 32 == 0 && k >= 1 && k <= 64) {
+            ctx->tune_block = blk;
+            ctx->tune_k = k;
+        }
+    }
+    std::fclose(f);
+}
+
 Launch choose_launch(const sdd_ctx *ctx, const sdd_config *cfg, double dt, long long total_paths,
                      int kmax_override = 0, int gcode_override = -1) {
     Launch L;
     L.f64 = cfg && cfg->precision == SDD_FP64;
     L.kmax = kmax_override ? kmax_override : kmax_for(ctx->K);
-    L.block = (cfg && cfg->block_threads) ? cfg->block_threads : 256;
+    if (gcode_override < 0)
+        tune_from_file(const_cast<sdd_ctx *>(ctx), L.kmax, ctx->M.gcode, L.f64, dt);
+    const bool tuned = gcode_override < 0 && ctx->tune_block > 0;
+    L.block = (cfg && cfg->block_threads) ? cfg->block_threads : (tuned ? ctx->tune_block : 256);
+    const int items_per_warp = tuned ? ctx->tune_k : 6;
     const int gcode = gcode_override >= 0 ? gcode_override : ctx->M.gcode;
     int occ = L.f64 ? occupancy_f64(L.kmax, ctx->geo, L.block, ctx->E, ctx->K)
                     : occupancy_f32(L.kmax, gcode, L.block, ctx->E, std::max(ctx->K, L.kmax));
@@ -366,7 +407,7 @@ Launch choose_launch(const sdd_ctx *ctx, const sdd_config *cfg, double dt, long 
     const long long warps = (long long)L.grid * (L.block / 32);
     long long chunk = (cfg && cfg->chunk_paths) ? cfg->chunk_paths : 0;
     if (chunk == 0) {
-        chunk = (total_paths + warps * 6 - 1) / (warps * 6);
+        chunk = (total_paths + warps * items_per_warp - 1) / (warps * items_per_warp);
         chunk = (chunk + 31) / 32 * 32;
         if (chunk < 32) chunk = 32;
         if (chunk > 16384) chunk = 16384;
@@ -460,10 +501,8 @@ WalkArgs base_args(sdd_ctx *ctx, const Launch &L, double dt, uint64_t seed) {
 }
 
 // Upload the item table (through pinned staging) and launch walk + reduce.
-sdd_status run(sdd_ctx *ctx, const Plan &P, const Launch &L, WalkArgs A, cudaStream_t s,
-               bool timed, bool do_reduce, double *d_mean, double *d_se, int n_nodes,
-               const ModelDev *model = nullptr) {
-    const ModelDev &MD = model ? *model : ctx->M;
+// Scratch buffers and the item table of a plan (uploaded unless cached).
+sdd_status prepare(sdd_ctx *ctx, const Plan &P, int n_nodes, cudaStream_t s) {
     const size_t ni = P.items.size();
     if (ni == 0) return SDD_OK;
     SDD_CUDA(ctx->items.ensure(ni * sizeof(Item) + (n_nodes + 1) * sizeof(int32_t)));
@@ -491,6 +530,16 @@ sdd_status run(sdd_ctx *ctx, const Plan &P, const Launch &L, WalkArgs A, cudaStr
         ctx->last_h2d = hbytes;
         ctx->plan_valid = P.cacheable;
     }
+    return SDD_OK;
+}
+
+// Device work of a prepared plan: clear counters, walk, reduce.
+sdd_status enqueue(sdd_ctx *ctx, const Plan &P, const Launch &L, WalkArgs A, cudaStream_t s,
+                   bool timed, bool do_reduce, double *d_mean, double *d_se, int n_nodes,
+                   const ModelDev *model = nullptr) {
+    const ModelDev &MD = model ? *model : ctx->M;
+    const size_t ni = P.items.size();
+    if (ni == 0) return SDD_OK;
     SDD_CUDA(cudaMemsetAsync(ctx->queue.p, 0, sizeof(int32_t), s));
     SDD_CUDA(cudaMemsetAsync(ctx->counters.p, 0, 3 * sizeof(unsigned long long), s));
     A.items = (const Item *)ctx->items.p;
@@ -519,6 +568,14 @@ sdd_status run(sdd_ctx *ctx, const Plan &P, const Launch &L, WalkArgs A, cudaStr
         SDD_CUDA(cudaGetLastError());
     }
     return SDD_OK;
+}
+
+sdd_status run(sdd_ctx *ctx, const Plan &P, const Launch &L, WalkArgs A, cudaStream_t s,
+               bool timed, bool do_reduce, double *d_mean, double *d_se, int n_nodes,
+               const ModelDev *model = nullptr) {
+    sdd_status st = prepare(ctx, P, n_nodes, s);
+    if (st != SDD_OK) return st;
+    return enqueue(ctx, P, L, A, s, timed, do_reduce, d_mean, d_se, n_nodes, model);
 }
 
 }  // namespace
@@ -604,6 +661,7 @@ void sdd_destroy(sdd_ctx *c) {
                       &c->rec_counts, &c->rec_exit, &c->rec_wall, &c->rec_mlast,
                       &c->batch_models};
     for (DevBuf *b : bufs) b->release();
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->h_items) cudaFreeHost(c->h_items);
     if (c->items_done) cudaEventDestroy(c->items_done);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -687,11 +745,57 @@ sdd_status sdd_interface_values_device(sdd_ctx *ctx, const double *d_nodes_xz,
     WalkArgs A = base_args(ctx, L, dt, seed);
     A.nodes = d_nodes_xz;
     A.node_ids = d_node_ids;
-    st = run(ctx, P, L, A, s, false, true, d_mean, d_se, n_nodes);
+    if (!(cfg && cfg->use_graph)) {
+        st = run(ctx, P, L, A, s, false, true, d_mean, d_se, n_nodes);
+        if (st != SDD_OK) return st;
+        if (d_counters)
+            SDD_CUDA(cudaMemcpyAsync(d_counters, ctx->counters.p, 3 * sizeof(uint64_t),
+                                     cudaMemcpyDeviceToDevice, s));
+        return SDD_OK;
+    }
+    // graph mode: the item table goes up on the caller's stream; the device
+    // work is captured on the context's stream into a graph, the cached
+    // executable graph is updated in place (re-instantiated only when the
+    // captured work changes shape) and launched on the caller's stream
+    st = prepare(ctx, P, n_nodes, s);
     if (st != SDD_OK) return st;
-    if (d_counters)
-        SDD_CUDA(cudaMemcpyAsync(d_counters, ctx->counters.p, 3 * sizeof(uint64_t),
-                                 cudaMemcpyDeviceToDevice, s));
+    cudaGraph_t g = nullptr;
+    SDD_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    st = enqueue(ctx, P, L, A, ctx->stream, false, true, d_mean, d_se, n_nodes);
+    if (st == SDD_OK && d_counters) {
+        cudaError_t e = cudaMemcpyAsync(d_counters, ctx->counters.p, 3 * sizeof(uint64_t),
+                                        cudaMemcpyDeviceToDevice, ctx->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "counter copy");
+    }
+    cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+    if (st != SDD_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    bool updated = false;
+    if (ctx->graph_exec) {
+        cudaGraphExecUpdateResultInfo info;
+        updated = cudaGraphExecUpdate(ctx->graph_exec, g, &info) == cudaSuccess;
+        if (!updated) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(ctx->graph_exec);
+            ctx->graph_exec = nullptr;
+        }
+    }
+    if (!updated) {
+        e = cudaGraphInstantiate(&ctx->graph_exec, g, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            ctx->graph_exec = nullptr;
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        ctx->graph_instantiations += 1;
+    } else {
+        ctx->graph_updates += 1;
+    }
+    cudaGraphDestroy(g);
+    SDD_CUDA(cudaGraphLaunch(ctx->graph_exec, s));
     return SDD_OK;
 }
 
@@ -1175,16 +1279,17 @@ double us_since(Clock::time_point a, Clock::time_point b) {
 
 struct SrvRequest {
     uint64_t id = 0;
-    int slot = -1;                 // raster arena slot
+    int slot = -1;                 // arena slot (tile map)
     int64_t bytes = 0;
-    BatchModel bm;                 // rates and boundary constants (raster set per slot)
+    BatchModel bm;                 // tile map, rates and boundary constants
     int K = 1;
     std::vector<double> nodes;
     std::vector<uint32_t> ids;
     std::vector<int64_t> fixed;    // fixed counts, empty when adaptive
     double target_se = 0.0;
     int64_t n_pilot = 0, n_max = 0;
-    int phase = 0;                 // 0 first walks pending, 1 running, 2 top-up pending, 3 running, 4 finished
+    int phase = 0;                 // 0 first walks, 2 top-up walks, 4 finished
+    int pieces_left = 0;           // pieces of the current phase not yet folded in
     std::vector<int64_t> begin, count;
     std::vector<double> sums;      // [n][E][4]
     std::vector<long long> nvalid;
@@ -1197,9 +1302,17 @@ struct SrvRequest {
     bool started = false;
 };
 
+// Nodes [a, b) of a request's current phase, launched together.
+struct SrvPiece {
+    SrvRequest *r;
+    int32_t a, b;
+    int64_t walks;
+};
+
 struct SrvPart {
     SrvRequest *r;
-    int32_t node0, n;
+    int32_t node0;  // first node of the piece in the launch's node list
+    int32_t a, b;   // the piece's nodes in the request
 };
 
 struct SrvLane {
@@ -1228,7 +1341,8 @@ struct sdd_server {
     std::mutex mu;
     std::condition_variable cv, done_cv;
     std::map<uint64_t, SrvRequest *> reqs;
-    std::deque<SrvRequest *> runnable;
+    std::deque<SrvPiece> runnable;
+    int64_t batch_walks = 0;       // walk budget of one launch
     std::vector<SrvLane> lanes;
     std::thread worker;
     bool stop = false;
@@ -1246,30 +1360,62 @@ int64_t request_bytes(const sdd_server *srv, int32_t n_nodes) {
            (int64_t)sizeof(BatchModel);
 }
 
-// Queue the walks of the requests' current phases as one batched launch.
-sdd_status srv_launch(sdd_server *srv, SrvLane &L, std::vector<SrvRequest *> &batch) {
+// Cut a request's current phase into pieces of at most batch_walks walks
+// (whole nodes; nodes with no walks left out) and queue them.
+void srv_queue_phase(sdd_server *srv, SrvRequest *r) {
+    const int32_t n = (int32_t)r->ids.size();
+    int pieces = 0;
+    int32_t a = 0;
+    while (a < n) {
+        while (a < n && r->count[a] == 0) ++a;
+        if (a >= n) break;
+        int32_t b = a;
+        int64_t w = 0;
+        while (b < n && (b == a || w + r->count[b] <= srv->batch_walks)) {
+            w += r->count[b];
+            ++b;
+            while (b < n && r->count[b] == 0) ++b;
+        }
+        srv->runnable.push_back({r, a, b, w});
+        ++pieces;
+        a = b;
+    }
+    r->pieces_left = pieces;
+}
+
+// Queue one launch over the pieces: each piece's nodes with their current
+// ranges, one model-table entry per request.
+sdd_status srv_launch(sdd_server *srv, SrvLane &L, std::vector<SrvPiece> &batch) {
     const int E = srv->cfg.n_eval;
     std::vector<double> nodes;
     std::vector<uint32_t> ids;
     std::vector<int64_t> begin, count;
     std::vector<int32_t> node_model;
     std::vector<BatchModel> table;
+    std::map<SrvRequest *, int32_t> model_of;
     L.parts.clear();
     int Kmax = 1;
-    for (size_t m = 0; m < batch.size(); ++m) {
-        SrvRequest *r = batch[m];
-        const int32_t n = (int32_t)r->ids.size();
-        L.parts.push_back({r, (int32_t)ids.size(), n});
-        for (int j = 0; j < n; ++j) {
+    for (const SrvPiece &pc : batch) {
+        SrvRequest *r = pc.r;
+        auto it = model_of.find(r);
+        int32_t m;
+        if (it == model_of.end()) {
+            m = (int32_t)table.size();
+            model_of[r] = m;
+            table.push_back(r->bm);
+            Kmax = std::max(Kmax, r->K);
+        } else {
+            m = it->second;
+        }
+        L.parts.push_back({r, (int32_t)ids.size(), pc.a, pc.b});
+        for (int j = pc.a; j < pc.b; ++j) {
             nodes.push_back(r->nodes[2 * j]);
             nodes.push_back(r->nodes[2 * j + 1]);
             ids.push_back(r->ids[j]);
             begin.push_back(r->begin[j]);
             count.push_back(r->count[j]);
-            node_model.push_back((int32_t)m);
+            node_model.push_back(m);
         }
-        table.push_back(r->bm);
-        Kmax = std::max(Kmax, r->K);
     }
     const int32_t n_nodes = (int32_t)ids.size();
     L.n_nodes = n_nodes;
@@ -1348,7 +1494,7 @@ sdd_status srv_launch(sdd_server *srv, SrvLane &L, std::vector<SrvRequest *> &ba
     return SDD_OK;
 }
 
-// Mean and SE of a finished request (sums in fixed order: pilot, then top-up).
+// A request ends: its status and the counters.
 void srv_finish(sdd_server *srv, SrvRequest *r) {
     r->phase = 4;
     r->t_done = Clock::now();
@@ -1358,7 +1504,44 @@ void srv_finish(sdd_server *srv, SrvRequest *r) {
     if (r->cancelled) srv->st.cancelled += 1;
 }
 
-// A launch ended: fold its per-node sums into its requests.
+// All pieces of a request's phase are in: size the top-up from the pilot,
+// or finish.
+void srv_phase_done(sdd_server *srv, SrvRequest *r) {
+    const int E = srv->cfg.n_eval;
+    if (r->cancelled) {
+        srv_finish(srv, r);
+        return;
+    }
+    if (r->phase == 0 && r->fixed.empty()) {
+        const int32_t n = (int32_t)r->ids.size();
+        long long extra_total = 0;
+        for (int j = 0; j < n; ++j) {
+            double need = 0.0;
+            for (int e = 0; e < E; ++e) {
+                double m[2], sd[2];
+                finish(&r->sums[((size_t)j * E + e) * 4], r->nvalid[j], m, sd);
+                const double var = (sd[0] * sd[0] + sd[1] * sd[1]) * (double)r->nvalid[j];
+                if (std::isfinite(var)) need = std::max(need, var);
+            }
+            double N = std::ceil(need / (r->target_se * r->target_se));
+            if (!(N >= (double)r->n_pilot)) N = (double)r->n_pilot;
+            if (N > (double)r->n_max) N = (double)r->n_max;
+            r->n_used[j] = (int64_t)N;
+            r->begin[j] = r->n_pilot;
+            r->count[j] = (int64_t)N - r->n_pilot;
+            extra_total += r->count[j];
+        }
+        if (extra_total > 0) {
+            r->phase = 2;
+            srv_queue_phase(srv, r);
+            return;
+        }
+    }
+    srv_finish(srv, r);
+}
+
+// A launch ended: fold its per-node sums into its requests (the pieces of a
+// phase cover disjoint nodes, so the order of their launches does not matter).
 void srv_complete(sdd_server *srv, SrvLane &L) {
     const int E = srv->cfg.n_eval;
     float ms = 0.f;
@@ -1367,47 +1550,20 @@ void srv_complete(sdd_server *srv, SrvLane &L) {
     srv->st.launches += 1;
     srv->st.steps += L.h_cnt[0];
     srv->st.walks += L.h_cnt[1];
+    std::map<SrvRequest *, int> seen;
     for (const SrvPart &pt : L.parts) {
         SrvRequest *r = pt.r;
-        r->launches += 1;
-        for (int j = 0; j < pt.n; ++j) {
-            const long long nv = L.h_nvalid[pt.node0 + j];
+        if (seen[r]++ == 0) r->launches += 1;
+        for (int j = pt.a; j < pt.b; ++j) {
+            const int32_t k = pt.node0 + (j - pt.a);
+            const long long nv = L.h_nvalid[k];
             r->walks += (uint64_t)r->count[j];
             r->truncated += (uint64_t)(r->count[j] - nv);
             r->nvalid[j] += nv;
             for (int q = 0; q < E * 4; ++q)
-                r->sums[(size_t)j * E * 4 + q] += L.h_sums[((size_t)pt.node0 + j) * E * 4 + q];
+                r->sums[(size_t)j * E * 4 + q] += L.h_sums[(size_t)k * E * 4 + q];
         }
-        if (r->cancelled) {
-            srv_finish(srv, r);
-            continue;
-        }
-        if (r->phase == 1 && r->fixed.empty()) {
-            // adaptive: size each node from its pilot variance
-            long long extra_total = 0;
-            for (int j = 0; j < pt.n; ++j) {
-                double need = 0.0;
-                for (int e = 0; e < E; ++e) {
-                    double m[2], sd[2];
-                    finish(&r->sums[((size_t)j * E + e) * 4], r->nvalid[j], m, sd);
-                    const double var = (sd[0] * sd[0] + sd[1] * sd[1]) * (double)r->nvalid[j];
-                    if (std::isfinite(var)) need = std::max(need, var);
-                }
-                double N = std::ceil(need / (r->target_se * r->target_se));
-                if (!(N >= (double)r->n_pilot)) N = (double)r->n_pilot;
-                if (N > (double)r->n_max) N = (double)r->n_max;
-                r->n_used[j] = (int64_t)N;
-                r->begin[j] = r->n_pilot;
-                r->count[j] = (int64_t)N - r->n_pilot;
-                extra_total += r->count[j];
-            }
-            if (extra_total > 0) {
-                r->phase = 2;
-                srv->runnable.push_back(r);
-                continue;
-            }
-        }
-        srv_finish(srv, r);
+        if (--r->pieces_left == 0) srv_phase_done(srv, r);
     }
     L.parts.clear();
     L.busy = false;
@@ -1432,29 +1588,38 @@ void srv_worker(sdd_server *srv) {
         }
         for (SrvLane &L : srv->lanes) {
             if (L.busy || srv->runnable.empty() || srv->stop) continue;
-            std::vector<SrvRequest *> batch;
-            while (!srv->runnable.empty() && (int)batch.size() < srv->cfg.max_batch_models) {
-                SrvRequest *r = srv->runnable.front();
-                srv->runnable.pop_front();
-                if (r->cancelled) {
-                    srv_finish(srv, r);
+            std::vector<SrvPiece> batch;
+            std::map<SrvRequest *, int> models;
+            int64_t walks = 0;
+            while (!srv->runnable.empty()) {
+                const SrvPiece pc = srv->runnable.front();
+                if (pc.r->cancelled) {
+                    srv->runnable.pop_front();
+                    if (--pc.r->pieces_left == 0) srv_finish(srv, pc.r);
                     progress = true;
                     continue;
                 }
-                r->phase = r->phase == 0 ? 1 : 3;
-                if (!r->started) {
-                    r->started = true;
-                    r->t_first = Clock::now();
+                const bool new_model = models.find(pc.r) == models.end();
+                if (!batch.empty() && (walks + pc.walks > srv->batch_walks ||
+                                       (new_model && (int)models.size() >= srv->cfg.max_batch_models)))
+                    break;
+                srv->runnable.pop_front();
+                models[pc.r] = 1;
+                walks += pc.walks;
+                if (!pc.r->started) {
+                    pc.r->started = true;
+                    pc.r->t_first = Clock::now();
                 }
-                batch.push_back(r);
+                batch.push_back(pc);
             }
             if (batch.empty()) continue;
             sdd_status st = srv_launch(srv, L, batch);
             if (st != SDD_OK) {
                 srv->worker_error = g_last_error;
-                for (SrvRequest *r : batch) {
-                    r->status = st;
-                    srv_finish(srv, r);
+                for (const SrvPiece &pc : batch) {
+                    pc.r->status = st;
+                    pc.r->cancelled = true;
+                    if (--pc.r->pieces_left == 0) srv_finish(srv, pc.r);
                 }
                 L.busy = false;
             }
@@ -1482,6 +1647,7 @@ extern "C" sdd_status sdd_server_create(const sdd_server_config *cfg, sdd_server
     if (cfg->max_batch_models < 1 || cfg->max_batch_models > kMaxBatchModels)
         return fail(SDD_E_ARG, "max_batch_models must be in 1..256");
     if (cfg->max_bytes < 0) return fail(SDD_E_ARG, "max_bytes < 0");
+    if (cfg->max_batch_walks < 0) return fail(SDD_E_ARG, "max_batch_walks < 0");
     if (cfg->launch.precision != SDD_FP32) return fail(SDD_E_UNSUPPORTED, "the server runs the FP32 walk");
     sdd_status st;
     // a template model of the server's shape (one material, blank raster)
@@ -1500,6 +1666,7 @@ extern "C" sdd_status sdd_server_create(const sdd_server_config *cfg, sdd_server
     sdd_server *srv = new (std::nothrow) sdd_server();
     if (!srv) return fail(SDD_E_OOM, "host allocation failed");
     srv->cfg = *cfg;
+    srv->batch_walks = cfg->max_batch_walks > 0 ? cfg->max_batch_walks : (int64_t)1 << 24;
     st = sdd_create(&md, &srv->tmpl);
     if (st != SDD_OK) {
         delete srv;
@@ -1652,7 +1819,8 @@ extern "C" sdd_status sdd_server_submit(sdd_server *srv, const sdd_request_desc 
     r->id = srv->next_id++;
     r->t_submit = Clock::now();
     srv->reqs[r->id] = r;
-    srv->runnable.push_back(r);
+    r->phase = 0;
+    srv_queue_phase(srv, r);
     *id = r->id;
     lk.unlock();
     srv->cv.notify_all();
@@ -1730,9 +1898,13 @@ extern "C" sdd_status sdd_server_cancel(sdd_server *srv, uint64_t id) {
     SrvRequest *r = it->second;
     if (r->phase == 4) return SDD_OK;
     r->cancelled = true;
-    if (r->phase == 0 || r->phase == 2) {
-        // not on the GPU: end it now
-        srv->runnable.erase(std::remove(srv->runnable.begin(), srv->runnable.end(), r), srv->runnable.end());
+    // drop its queued pieces; pieces already on the GPU end it when they finish
+    const size_t before = srv->runnable.size();
+    srv->runnable.erase(std::remove_if(srv->runnable.begin(), srv->runnable.end(),
+                                       [r](const SrvPiece &p) { return p.r == r; }),
+                        srv->runnable.end());
+    r->pieces_left -= (int)(before - srv->runnable.size());
+    if (r->pieces_left == 0) {
         srv_finish(srv, r);
         srv->done_cv.notify_all();
     }
@@ -1745,5 +1917,78 @@ extern "C" sdd_status sdd_server_get_stats(sdd_server *srv, sdd_server_stats *ou
     *out = srv->st;
     out->in_flight = (int32_t)srv->reqs.size();
     out->bytes_in_use = srv->bytes_in_use;
+    return SDD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuning of the launch shape (sdd_autotune).
+
+extern "C" sdd_status sdd_autotune(sdd_ctx *ctx, const double *nodes_xz, int32_t n_nodes,
+                                   const int64_t *n_paths, double dt, uint64_t seed,
+                                   const sdd_config *base, sdd_config *best,
+                                   double *best_steps_per_s) {
+    sdd_status st = check_call(ctx, n_nodes, n_paths, dt, base);
+    if (st != SDD_OK) return st;
+    if (n_nodes < 1 || !nodes_xz) return fail(SDD_E_ARG, "autotuning needs nodes");
+    if (base && (base->block_threads || base->chunk_paths))
+        return fail(SDD_E_ARG, "base must leave block_threads and chunk_paths automatic");
+    sdd_config c;
+    std::memset(&c, 0, sizeof(c));
+    if (base) c = *base;
+    const int blocks[] = {128, 192, 256};
+    const int ks[] = {2, 4, 6, 10, 16};
+    std::vector<double> mean((size_t)n_nodes * ctx->E * 2), se(mean.size());
+    double best_rate = -1.0;
+    int best_b = 256, best_k = 6;
+    const int saved_b = ctx->tune_block, saved_k = ctx->tune_k;
+    const bool saved_read = ctx->tune_file_read;
+    ctx->tune_file_read = true;  // time the candidates, not the cached choice
+    for (int b : blocks)
+        for (int k : ks) {
+            ctx->tune_block = b;
+            ctx->tune_k = k;
+            double t = 1e30;
+            uint64_t steps = 0;
+            for (int rep = 0; rep < 2; ++rep) {
+                sdd_stats sst;
+                st = sdd_interface_values(ctx, nodes_xz, nullptr, n_nodes, n_paths, dt, seed, &c,
+                                          mean.data(), se.data(), &sst);
+                if (st != SDD_OK && st != SDD_E_TRUNCATED) {
+                    ctx->tune_block = saved_b;
+                    ctx->tune_k = saved_k;
+                    ctx->tune_file_read = saved_read;
+                    return st;
+                }
+                t = std::min(t, sst.kernel_ms);
+                steps = sst.steps;
+            }
+            const double rate = (double)steps / (t * 1e-3);
+            if (rate > best_rate) {
+                best_rate = rate;
+                best_b = b;
+                best_k = k;
+            }
+        }
+    ctx->tune_block = best_b;
+    ctx->tune_k = best_k;
+    if (const char *path = std::getenv("SDD_TUNE_CACHE")) {
+        if (*path) {
+            const bool f64 = c.precision == SDD_FP64;
+            const std::string key = tune_key(ctx, kmax_for(ctx->K), ctx->M.gcode, f64, dt);
+            if (FILE *f = std::fopen(path, "a")) {
+                std::fprintf(f, "%s|%d %d\n", key.c_str(), best_b, best_k);
+                std::fclose(f);
+            }
+        }
+    }
+    if (best) {
+        *best = c;
+        long long total = 0;
+        for (int j = 0; j < n_nodes; ++j) total += n_paths[j];
+        const Launch L = choose_launch(ctx, &c, dt, total);
+        best->block_threads = L.block;
+        best->chunk_paths = L.chunk;
+    }
+    if (best_steps_per_s) *best_steps_per_s = best_rate;
     return SDD_OK;
 }

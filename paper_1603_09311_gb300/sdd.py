@@ -61,7 +61,7 @@ class sdd_model_desc(ctypes.Structure):
 class sdd_config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_steps", ctypes.c_int64),
                 ("block_threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("chunk_paths", ctypes.c_int32)]
+                ("chunk_paths", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
 
 
 class sdd_batch_entry(ctypes.Structure):
@@ -84,6 +84,7 @@ class sdd_server_config(ctypes.Structure):
                 ("n_eval", ctypes.c_int32), ("g_kind", ctypes.c_int32),
                 ("max_requests", ctypes.c_int32), ("max_bytes", ctypes.c_int64),
                 ("n_streams", ctypes.c_int32), ("max_batch_models", ctypes.c_int32),
+                ("max_batch_walks", ctypes.c_int64),
                 ("dt", ctypes.c_double), ("seed", ctypes.c_uint64), ("launch", sdd_config)]
 
 
@@ -148,6 +149,9 @@ SIGNATURES = [
       P(sdd_request_stats)]),
     ("sdd_server_cancel", ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64]),
     ("sdd_server_get_stats", ctypes.c_int, [ctypes.c_void_p, P(sdd_server_stats)]),
+    ("sdd_autotune", ctypes.c_int,
+     [ctypes.c_void_p, P(ctypes.c_double), ctypes.c_int32, P(ctypes.c_int64), ctypes.c_double,
+      ctypes.c_uint64, P(sdd_config), P(sdd_config), P(ctypes.c_double)]),
     ("sdd_n_eval", ctypes.c_int32, [ctypes.c_void_p]),
     ("sdd_n_materials", ctypes.c_int32, [ctypes.c_void_p]),
     ("sdd_status_str", ctypes.c_char_p, [ctypes.c_int]),
@@ -218,11 +222,13 @@ def make_desc(model: dict):
     return d, keep
 
 
-def make_config(precision="fp32", max_steps=0, block_threads=0, ctas_per_sm=0, chunk_paths=0):
+def make_config(precision="fp32", max_steps=0, block_threads=0, ctas_per_sm=0, chunk_paths=0,
+                use_graph=0):
     c = sdd_config()
     c.precision = SDD_FP64 if precision in ("fp64", SDD_FP64) else SDD_FP32
     c.max_steps, c.block_threads = int(max_steps), int(block_threads)
     c.ctas_per_sm, c.chunk_paths = int(ctas_per_sm), int(chunk_paths)
+    c.use_graph = int(use_graph)
     return c
 
 
@@ -406,6 +412,22 @@ def sdd_walk_records(ctx: Context, x0: float, z0: float, node_id: int, p0: int, 
             "truncated": (wall < 0).astype(np.int32)}
 
 
+def sdd_autotune(ctx: Context, nodes, n_paths, dt: float, seed: int, **base):
+    """Time candidate launch shapes on this workload; the context keeps the
+    fastest.  Returns ({block_threads, chunk_paths}, walk-steps/s)."""
+    nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64).reshape(-1, 2))
+    npth = _paths(n_paths, nodes.shape[0])
+    b = make_config(**base)
+    out = sdd_config()
+    rate = ctypes.c_double()
+    st = lib().sdd_autotune(ctx.handle, _dp(nodes), nodes.shape[0], npth.ctypes.data_as(P(ctypes.c_int64)),
+                            float(dt), int(seed) & (2 ** 64 - 1), ctypes.byref(b), ctypes.byref(out),
+                            ctypes.byref(rate))
+    if st != SDD_OK:
+        raise SddError(st, "sdd_autotune")
+    return {"block_threads": out.block_threads, "chunk_paths": out.chunk_paths}, rate.value
+
+
 def sdd_status_str(status: int) -> str:
     return lib().sdd_status_str(status).decode()
 
@@ -420,12 +442,13 @@ class Server:
     the server's domain, raster size, n_eval and g_kind."""
 
     def __init__(self, domain, nx, nz, dt, seed, n_eval=1, g_kind=0, max_requests=64, max_bytes=0,
-                 n_streams=2, max_batch_models=64, **launch):
+                 n_streams=4, max_batch_models=64, max_batch_walks=0, **launch):
         c = sdd_server_config()
         c.domain = sdd_domain(*[float(v) for v in domain])
         c.nx, c.nz, c.n_eval, c.g_kind = int(nx), int(nz), int(n_eval), int(g_kind)
         c.max_requests, c.max_bytes = int(max_requests), int(max_bytes)
         c.n_streams, c.max_batch_models = int(n_streams), int(max_batch_models)
+        c.max_batch_walks = int(max_batch_walks)
         c.dt, c.seed = float(dt), int(seed) & (2 ** 64 - 1)
         c.launch = make_config(**launch)
         self.n_eval = int(n_eval)

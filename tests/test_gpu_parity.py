@@ -285,3 +285,50 @@ def test_fp32_raster_walks_count_materials_like_the_oracle():
         assert same.mean() >= 0.9
         eq = np.all(g["counts"][same] == o["counts"][same], axis=1)
         assert eq.mean() >= 0.95, eq.mean()
+
+
+def test_graph_mode_equals_direct_launches():
+    torch = pytest.importorskip("torch")
+    w = I.scaled(I.workload("quarterspace"), n_nodes=8, paths_per_node=4000, dt=1e-3)
+    ctx = sdd.sdd_create(w["model"])
+    dev = torch.device("cuda:0")
+    d_nodes = torch.tensor(w["nodes"], dtype=torch.float64, device=dev)
+    outs = {}
+    for mode, seed in (("direct", 1), ("graph", 1), ("graph", 2), ("direct", 2)):
+        m = torch.empty((8, 1, 2), dtype=torch.float64, device=dev)
+        s_ = torch.empty((8, 1, 2), dtype=torch.float64, device=dev)
+        c = torch.zeros(3, dtype=torch.int64, device=dev)
+        sdd.sdd_interface_values_device(ctx, d_nodes.data_ptr(), 8, w["n_paths"], w["dt"], seed,
+                                        m.data_ptr(), s_.data_ptr(), d_counters_ptr=c.data_ptr(),
+                                        stream=torch.cuda.current_stream().cuda_stream,
+                                        use_graph=int(mode == "graph"))
+        torch.cuda.synchronize()
+        outs[(mode, seed)] = (m.cpu().numpy(), s_.cpu().numpy(), c.cpu().numpy())
+    for seed in (1, 2):  # the second graph call updates the first graph in place
+        a, b = outs[("direct", seed)], outs[("graph", seed)]
+        assert np.allclose(a[0], b[0], rtol=0, atol=1e-12)
+        assert np.allclose(a[1], b[1], rtol=1e-9, atol=0)
+        assert np.array_equal(a[2], b[2])
+    assert not np.allclose(outs[("graph", 1)][0], outs[("graph", 2)][0])
+
+
+def test_autotune_keeps_results_and_caches_the_shape(tmp_path, monkeypatch):
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("SDD_TUNE_CACHE", str(cache))
+    w = I.scaled(I.workload("quarterspace"), n_nodes=16, paths_per_node=20000, dt=1e-3)
+    ctx = sdd.sdd_create(w["model"])
+    cfg, rate = sdd.sdd_autotune(ctx, w["nodes"], w["n_paths"], w["dt"], 3)
+    assert cfg["block_threads"] in (128, 192, 256) and cfg["chunk_paths"] % 32 == 0 and rate > 0
+    tuned, _, st = sdd.sdd_interface_values(ctx, w["nodes"], w["n_paths"], w["dt"], 5)
+    assert st["block"] == cfg["block_threads"]
+    plain = sdd.sdd_create(w["model"])
+    monkeypatch.delenv("SDD_TUNE_CACHE")
+    ref, _, st0 = sdd.sdd_interface_values(plain, w["nodes"], w["n_paths"], w["dt"], 5, block_threads=256,
+                                           chunk_paths=32)
+    assert np.allclose(tuned, ref, rtol=0, atol=1e-12)  # the same walks, another launch shape
+    lines = cache.read_text().splitlines()
+    assert len(lines) == 1 and "|" in lines[0]
+    monkeypatch.setenv("SDD_TUNE_CACHE", str(cache))
+    fresh = sdd.sdd_create(w["model"])  # reads the cached shape
+    _, _, st2 = sdd.sdd_interface_values(fresh, w["nodes"], w["n_paths"], w["dt"], 5)
+    assert st2["block"] == cfg["block_threads"]

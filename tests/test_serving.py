@@ -134,7 +134,8 @@ def test_cancel_wait_timeout_and_unknown_ids():
     assert srv.wait(big, 1) is False  # a long request is not done after 1 ms
     assert srv.wait(big, -1) is True
     st, mean, se, used, stats = srv.result(big)
-    assert st == sdd.SDD_OK and np.all(np.isfinite(mean)) and stats["launches"] == 1
+    # 64 nodes x 2e6 walks exceed the per-launch walk budget: the request ran in several pieces
+    assert st == sdd.SDD_OK and np.all(np.isfinite(mean)) and stats["launches"] > 1
     with pytest.raises(sdd.SddError):
         srv.cancel(987654)
     with pytest.raises(sdd.SddError):
