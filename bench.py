@@ -36,11 +36,12 @@ from paper_1603_09311_gb300 import inputs as I  # noqa: E402
 WORKLOAD = "quarterspace"
 METRIC = "walk-steps/s"
 # Algorithmic thread-instructions per Euler step of the single-precision walk
-# (derivation in the design doc): half a Philox4x32-10 call (20), two uniforms (4),
-# Box-Muller (7), Euler update (2), wall tests and bridge filter (6),
-# quarter-space material lookup (7), two occupation counters (4), step
-# bookkeeping (3).
-INST_PER_STEP = 53
+# on the quarter-space model (derivation in the design doc): half a Philox4x32-10
+# call with the first round's fixed product precomputed (19.5), two uniforms
+# from bit masks (3), Box-Muller (7), Euler update (2), wall distances and the
+# bridge filter (5), the vertical-contact material test (4), two occupation
+# power sums (2), step bookkeeping (2.5).
+INST_PER_STEP = 45
 
 
 def traffic_per_launch():

@@ -118,8 +118,8 @@ typedef struct {
     int32_t precision;     /* SDD_FP32: single-precision walk, FP64 sums.
                               SDD_FP64: double-precision walk (parity mode). */
     int64_t max_steps;     /* per-walk step cap, 0..2^26; 0 = ceil(20 / dt).  Rounded
-                              up to an even number (walks advance two Euler steps
-                              per Philox call) */
+                              up to a multiple of 8 (a single-precision walk
+                              advances 8 Euler steps per iteration) */
     int32_t block_threads; /* threads per CTA (multiple of 32, <= 256); 0 = auto */
     int32_t ctas_per_sm;   /* persistent CTAs per SM; 0 = occupancy limit */
     int32_t chunk_paths;   /* paths per work item; 0 = auto */

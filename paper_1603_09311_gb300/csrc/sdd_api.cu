@@ -118,7 +118,9 @@ struct sdd_ctx {
 namespace {
 
 // Cap on the steps of one walk: keeps the occupation power sums (up to
-// 27 x steps for four materials) inside 32 bits.
+// 27 x steps for four materials) inside 32 bits.  Caps are rounded up to a
+// multiple of 8 (the steps of one iteration of the single-precision walk),
+// in both precisions so that they truncate alike.
 constexpr int64_t kMaxSteps = 1ll << 26;
 
 int kmax_for(int K) { return K <= 2 ? 2 : (K <= 3 ? 3 : (K <= 4 ? 4 : 8)); }
@@ -415,7 +417,7 @@ Launch choose_launch(const sdd_ctx *ctx, const sdd_config *cfg, double dt, long 
     L.chunk = (int)chunk;
     L.max_steps = (cfg && cfg->max_steps) ? cfg->max_steps : (int64_t)std::ceil(20.0 / dt);
     if (L.max_steps > kMaxSteps) L.max_steps = kMaxSteps;
-    L.max_steps += L.max_steps & 1;  // walks advance two steps per random-number call
+    L.max_steps = (L.max_steps + 7) / 8 * 8;  // single-precision walks advance 8 steps per iteration
     return L;
 }
 

@@ -16,7 +16,8 @@
 //
 // The walk runs in centred coordinates X = x - xc, Z = z - zc, so the
 // distance to the nearer wall of each pair is h - |X|.  Two steps share one
-// Philox call (words 0,1 for the even step, 2,3 for the odd one).
+// Philox call (words 0,1 for the even step, 2,3 for the odd one), and one
+// call of iterate() runs 8 steps (4 with 8 materials).
 #include "walk_sched.cuh"
 
 namespace sdd {
@@ -255,14 +256,21 @@ struct WalkerF32 {
         return false;
     }
 
-    // Two Euler steps from one Philox call.  0 running, 1 exited, 2 truncated
-    // (max_steps is even, so a walk is only truncated after a pair).
+    // PAIRS Philox calls, two Euler steps each, per call of iterate: the
+    // per-iteration work of the scheduler loop (constants, vote, branch) is
+    // shared by 2 PAIRS steps.  0 running, 1 exited, 2 truncated (max_steps is
+    // a multiple of 8, so a walk is only truncated at the end of an iteration).
+    static constexpr int PAIRS = KMAX == 8 ? 2 : 4;
+
     __device__ __forceinline__ int iterate(const ModelDev &M, const WalkArgs &A, uint32_t path,
                                            ExitInfo<float> &ei) {
-        const uint4 w = philox_rk_pre(n >> 1, 0u, pre_x, pre_y, A.rk0, A.rk1);
-        if (substep(M, A, path, w.x, w.y, 0u, ei)) return 1;
-        if (substep(M, A, path, w.z, w.w, 1u, ei)) return 1;
-        n += 2;
+#pragma unroll
+        for (int q = 0; q < PAIRS; ++q) {
+            const uint4 w = philox_rk_pre((n >> 1) + q, 0u, pre_x, pre_y, A.rk0, A.rk1);
+            if (substep(M, A, path, w.x, w.y, 2u * q, ei)) return 1;
+            if (substep(M, A, path, w.z, w.w, 2u * q + 1u, ei)) return 1;
+        }
+        n += 2 * PAIRS;
         if (n >= A.max_steps) {
             ei.x = X; ei.z = Z; ei.th = 0.f; ei.wall = 0;
             ei.mlast = material(M, X, Z);
