@@ -122,10 +122,16 @@ typedef struct {
                               advances 8 Euler steps per iteration) */
     int32_t block_threads; /* threads per CTA (multiple of 32, <= 256); 0 = auto */
     int32_t ctas_per_sm;   /* persistent CTAs per SM; 0 = occupancy limit */
-    int32_t chunk_paths;   /* paths per work item; 0 = auto */
+    int32_t chunk_paths;   /* > 0: work items of this many paths (the last one of a
+                              node shorter); 0 = guided sizes (guided_factor) */
     int32_t use_graph;     /* sdd_interface_values_device: 1 = run the device work as a
                               CUDA graph cached in the context (updated in place on
                               later calls, re-instantiated only when its shape changes) */
+    int32_t guided_factor; /* guided work items (chunk_paths == 0): cut in rounds, each
+                              node's item taking ceil(R / (guided_factor x warps)) paths,
+                              R the paths not yet cut, rounded up to a multiple of 32,
+                              at least 32; the queue hands them out in cut order, so
+                              they shrink toward its end.  0 = auto (tuned, else 2) */
 } sdd_config;
 
 typedef struct {

@@ -85,6 +85,29 @@ struct DevBuf {
     }
 };
 
+// Work items of a call.  items are node by node, each node's in path order
+// (the order in which the per-node sums add them); order[q] is the item the
+// queue hands out q-th (empty: items in table order).
+struct Plan {
+    std::vector<Item> items;
+    std::vector<int32_t> node_item0;  // [n_nodes + 1]
+    std::vector<int32_t> order;
+    long long total_paths = 0;
+    bool cached = false;     // identical to the table already on the device
+};
+
+// What a plan was made from (the device copy is reused for an equal key).
+struct PlanKey {
+    std::vector<int64_t> paths;
+    int chunk = -1, factor = 0;
+    long long warps = 0;
+    uint32_t offset = 0;
+    bool operator==(const PlanKey &o) const {
+        return chunk == o.chunk && factor == o.factor && warps == o.warps && offset == o.offset &&
+               paths == o.paths;
+    }
+};
+
 }  // namespace
 
 struct sdd_ctx {
@@ -103,15 +126,15 @@ struct sdd_ctx {
     cudaEvent_t items_done = nullptr;  // last copy out of h_items finished
     cudaStream_t stream = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    // the item table last uploaded (reused when a call plans the same items)
-    std::vector<int64_t> plan_paths;
-    int plan_chunk = -1;
-    uint32_t plan_offset = 0;
+    // the plan whose item table was last uploaded (reused by a call with the
+    // same key)
+    Plan plan;
+    PlanKey plan_key;
     bool plan_valid = false;
     uint64_t last_h2d = 0;
     cudaGraphExec_t graph_exec = nullptr;  // device work of the last graph-mode call
     uint64_t graph_updates = 0, graph_instantiations = 0;
-    int tune_block = 0, tune_k = 0;        // autotuned threads per CTA, items per warp (0: none)
+    int tune_block = 0, tune_k = 0;        // autotuned threads per CTA, guided factor (0: none)
     bool tune_file_read = false;
 };
 
@@ -312,14 +335,6 @@ __global__ void sums_kernel(const double *__restrict__ slots, const int32_t *__r
     if (e == 0) nvalid[j] = nv;
 }
 
-struct Plan {
-    std::vector<Item> items;
-    std::vector<int32_t> node_item0;  // [n_nodes + 1]
-    long long total_paths = 0;
-    bool cached = false;     // identical to the table already on the device
-    bool cacheable = false;  // may be reused by a later call with the same key
-};
-
 sdd_status check_call(sdd_ctx *ctx, int32_t n_nodes, const int64_t *n_paths, double dt,
                       const sdd_config *cfg) {
     if (!ctx) return fail(SDD_E_ARG, "ctx is NULL");
@@ -339,6 +354,8 @@ sdd_status check_call(sdd_ctx *ctx, int32_t n_nodes, const int64_t *n_paths, dou
             return fail(SDD_E_ARG, "block_threads must be a multiple of 32 in 32..256");
         if (cfg->ctas_per_sm < 0 || cfg->chunk_paths < 0)
             return fail(SDD_E_ARG, "ctas_per_sm and chunk_paths must be >= 0");
+        if (cfg->guided_factor < 0 || cfg->guided_factor > 64)
+            return fail(SDD_E_ARG, "guided_factor must be in 0..64");
     }
     return SDD_OK;
 }
@@ -354,7 +371,9 @@ sdd_status check_nodes(const sdd_ctx *ctx, const double *xz, int32_t n) {
 
 struct Launch {
     bool f64;
-    int kmax, block, grid, chunk;
+    int kmax, block, grid;
+    int chunk;   // > 0: fixed items of chunk paths; 0: guided
+    int factor;  // guided: an item takes about 1 / (factor x warps) of the queued paths
     int64_t max_steps;
 };
 
@@ -390,7 +409,7 @@ void tune_from_file(sdd_ctx *ctx, int kmax, int gcode, bool f64, double dt) {
     std::fclose(f);
 }
 
-Launch choose_launch(const sdd_ctx *ctx, const sdd_config *cfg, double dt, long long total_paths,
+Launch choose_launch(const sdd_ctx *ctx, const sdd_config *cfg, double dt,
                      int kmax_override = 0, int gcode_override = -1) {
     Launch L;
     L.f64 = cfg && cfg->precision == SDD_FP64;
@@ -399,87 +418,114 @@ Launch choose_launch(const sdd_ctx *ctx, const sdd_config *cfg, double dt, long 
         tune_from_file(const_cast<sdd_ctx *>(ctx), L.kmax, ctx->M.gcode, L.f64, dt);
     const bool tuned = gcode_override < 0 && ctx->tune_block > 0;
     L.block = (cfg && cfg->block_threads) ? cfg->block_threads : (tuned ? ctx->tune_block : 256);
-    const int items_per_warp = tuned ? ctx->tune_k : 6;
+    L.factor = (cfg && cfg->guided_factor) ? cfg->guided_factor : (tuned ? ctx->tune_k : 2);
     const int gcode = gcode_override >= 0 ? gcode_override : ctx->M.gcode;
     int occ = L.f64 ? occupancy_f64(L.kmax, ctx->geo, L.block, ctx->E, ctx->K)
                     : occupancy_f32(L.kmax, gcode, L.block, ctx->E, std::max(ctx->K, L.kmax));
     if (occ < 1) occ = 1;
     if (cfg && cfg->ctas_per_sm > 0 && cfg->ctas_per_sm < occ) occ = cfg->ctas_per_sm;
     L.grid = ctx->n_sm * occ;
-    const long long warps = (long long)L.grid * (L.block / 32);
-    long long chunk = (cfg && cfg->chunk_paths) ? cfg->chunk_paths : 0;
-    if (chunk == 0) {
-        chunk = (total_paths + warps * items_per_warp - 1) / (warps * items_per_warp);
-        chunk = (chunk + 31) / 32 * 32;
-        if (chunk < 32) chunk = 32;
-        if (chunk > 16384) chunk = 16384;
-    }
-    L.chunk = (int)chunk;
+    L.chunk = (cfg && cfg->chunk_paths) ? cfg->chunk_paths : 0;
     L.max_steps = (cfg && cfg->max_steps) ? cfg->max_steps : (int64_t)std::ceil(20.0 / dt);
     if (L.max_steps > kMaxSteps) L.max_steps = kMaxSteps;
     L.max_steps = (L.max_steps + 7) / 8 * 8;  // single-precision walks advance 8 steps per iteration
     return L;
 }
 
-Plan plan_items(int32_t n_nodes, const int64_t *n_paths, int chunk, uint32_t p_offset) {
+// Items for paths [offset + begin[j], offset + begin[j] + count[j]) of every
+// node j (begin == nullptr: from 0), for the launch L.
+//   Fixed (L.chunk > 0): items of L.chunk paths, node by node.
+//   Guided (L.chunk == 0): cut in rounds; in each round every node with paths
+//   left gets one item of c = ceil(R / (F W)) paths, rounded up to a multiple
+//   of 32 and at least 32 (or at least total / 2^20, which bounds the table),
+//   R being the paths not yet cut, W the warps of the grid and F = L.factor.
+//   The queue hands items out in the order they were cut, so sizes shrink
+//   from about R / (F W) to one walk per lane toward the end of the queue,
+//   and no warp takes a large item just before the queue runs dry.
+Plan plan_work(int32_t n_nodes, const int64_t *begin, const int64_t *count, uint32_t p_offset,
+               const Launch &L) {
     Plan P;
-    P.node_item0.resize(n_nodes + 1);
-    for (int j = 0; j < n_nodes; ++j) {
-        P.node_item0[j] = (int32_t)P.items.size();
-        for (int64_t p = 0; p < n_paths[j]; p += chunk) {
-            Item I;
-            I.node = j;
-            I.path0 = p_offset + (uint32_t)p;
-            I.count = (int32_t)std::min<int64_t>(chunk, n_paths[j] - p);
-            I.model = 0;
-            P.items.push_back(I);
+    P.node_item0.assign((size_t)n_nodes + 1, 0);
+    for (int j = 0; j < n_nodes; ++j) P.total_paths += count[j];
+    auto first = [&](int j) -> int64_t { return begin ? begin[j] : 0; };
+    if (L.chunk > 0) {
+        for (int j = 0; j < n_nodes; ++j) {
+            P.node_item0[j] = (int32_t)P.items.size();
+            for (int64_t p = 0; p < count[j]; p += L.chunk) {
+                Item I;
+                I.node = j;
+                I.path0 = p_offset + (uint32_t)(first(j) + p);
+                I.count = (int32_t)std::min<int64_t>(L.chunk, count[j] - p);
+                I.model = 0;
+                P.items.push_back(I);
+            }
         }
-        P.total_paths += n_paths[j];
+        P.node_item0[n_nodes] = (int32_t)P.items.size();
+        return P;
     }
-    P.node_item0[n_nodes] = (int32_t)P.items.size();
+    const long long W = std::max<long long>(1, (long long)L.grid * (L.block / 32) * std::max(L.factor, 1));
+    const long long cmin = std::max<long long>(32, (P.total_paths / (1 << 20) + 31) / 32 * 32);
+    struct Cut {
+        int32_t node, k, count;
+    };
+    std::vector<Cut> seq;
+    std::vector<int32_t> live, per_node((size_t)n_nodes, 0);
+    std::vector<int64_t> done((size_t)n_nodes, 0);
+    for (int j = 0; j < n_nodes; ++j)
+        if (count[j] > 0) live.push_back(j);
+    long long R = P.total_paths;
+    while (!live.empty()) {
+        long long c = (R + W - 1) / W;
+        c = std::max(cmin, (c + 31) / 32 * 32);
+        c = std::min<long long>(c, 1 << 24);
+        size_t keep = 0;
+        for (int32_t j : live) {
+            const int64_t take = std::min<int64_t>(c, count[j] - done[j]);
+            seq.push_back({j, per_node[j]++, (int32_t)take});
+            done[j] += take;
+            R -= take;
+            if (done[j] < count[j]) live[keep++] = j;
+        }
+        live.resize(keep);
+    }
+    for (int j = 0; j < n_nodes; ++j) P.node_item0[j + 1] = P.node_item0[j] + per_node[j];
+    P.items.resize(seq.size());
+    P.order.resize(seq.size());
+    std::fill(done.begin(), done.end(), 0);
+    for (size_t q = 0; q < seq.size(); ++q) {
+        const Cut &x = seq[q];
+        const int32_t idx = P.node_item0[x.node] + x.k;
+        Item &I = P.items[idx];
+        I.node = x.node;
+        I.path0 = p_offset + (uint32_t)(first(x.node) + done[x.node]);
+        I.count = x.count;
+        I.model = 0;
+        done[x.node] += x.count;
+        P.order[q] = idx;
+    }
     return P;
 }
 
-// Plan the items of a call; reuse the device copy of the previous table when
-// the call has the same path counts, chunk and path offset.
-Plan plan_cached(sdd_ctx *ctx, int32_t n_nodes, const int64_t *n_paths, int chunk,
-                 uint32_t p_offset, bool cacheable) {
-    Plan P = plan_items(n_nodes, n_paths, chunk, p_offset);
-    const bool same = cacheable && ctx->plan_valid && ctx->plan_chunk == chunk &&
-                      ctx->plan_offset == p_offset && (int32_t)ctx->plan_paths.size() == n_nodes &&
-                      std::equal(ctx->plan_paths.begin(), ctx->plan_paths.end(), n_paths);
-    P.cached = same;
-    P.cacheable = cacheable;
-    if (!same) {
-        // the device table becomes valid for this key only once its upload is queued
-        ctx->plan_valid = false;
-        if (cacheable) {
-            ctx->plan_paths.assign(n_paths, n_paths + n_nodes);
-            ctx->plan_chunk = chunk;
-            ctx->plan_offset = p_offset;
-        }
+// The plan of a call with per-node path counts n_paths (paths from p_offset),
+// reusing the context's last plan, and its device table, for an equal key.
+const Plan &plan_cached(sdd_ctx *ctx, int32_t n_nodes, const int64_t *n_paths, uint32_t p_offset,
+                        const Launch &L) {
+    PlanKey key;
+    key.paths.assign(n_paths, n_paths + n_nodes);
+    key.chunk = L.chunk;
+    key.factor = L.chunk > 0 ? 0 : L.factor;
+    key.warps = L.chunk > 0 ? 0 : (long long)L.grid * (L.block / 32);
+    key.offset = p_offset;
+    if (ctx->plan_valid && key == ctx->plan_key) {
+        ctx->plan.cached = true;
+        return ctx->plan;
     }
-    return P;
-}
-
-// Items for paths [begin[j], begin[j] + count[j]) of every node.
-Plan plan_ranges(int32_t n_nodes, const int64_t *begin, const int64_t *count, int chunk) {
-    Plan P;
-    P.node_item0.resize(n_nodes + 1);
-    for (int j = 0; j < n_nodes; ++j) {
-        P.node_item0[j] = (int32_t)P.items.size();
-        for (int64_t p = 0; p < count[j]; p += chunk) {
-            Item I;
-            I.node = j;
-            I.path0 = (uint32_t)(begin[j] + p);
-            I.count = (int32_t)std::min<int64_t>(chunk, count[j] - p);
-            I.model = 0;
-            P.items.push_back(I);
-        }
-        P.total_paths += count[j];
-    }
-    P.node_item0[n_nodes] = (int32_t)P.items.size();
-    return P;
+    // the device table becomes valid for this key only once its upload is queued
+    ctx->plan_valid = false;
+    ctx->plan = plan_work(n_nodes, nullptr, n_paths, p_offset, L);
+    ctx->plan.cached = false;
+    ctx->plan_key = std::move(key);
+    return ctx->plan;
 }
 
 WalkArgs base_args(sdd_ctx *ctx, const Launch &L, double dt, uint64_t seed) {
@@ -502,20 +548,27 @@ WalkArgs base_args(sdd_ctx *ctx, const Launch &L, double dt, uint64_t seed) {
     return A;
 }
 
-// Upload the item table (through pinned staging) and launch walk + reduce.
-// Scratch buffers and the item table of a plan (uploaded unless cached).
+// Scratch buffers and the item table of a plan: items, node_item0 and the
+// queue order, uploaded through pinned staging unless the device already
+// holds this plan.
+size_t table_bytes(const Plan &P, int n_nodes) {
+    return P.items.size() * sizeof(Item) + ((size_t)n_nodes + 1) * sizeof(int32_t) +
+           P.order.size() * sizeof(int32_t);
+}
+
 sdd_status prepare(sdd_ctx *ctx, const Plan &P, int n_nodes, cudaStream_t s) {
     const size_t ni = P.items.size();
     if (ni == 0) return SDD_OK;
-    SDD_CUDA(ctx->items.ensure(ni * sizeof(Item) + (n_nodes + 1) * sizeof(int32_t)));
+    const size_t hbytes = table_bytes(P, n_nodes);
+    SDD_CUDA(ctx->items.ensure(hbytes));
     SDD_CUDA(ctx->slots.ensure(ni * (size_t)ctx->E * 4 * sizeof(double)));
     SDD_CUDA(ctx->trunc.ensure(ni * sizeof(int32_t)));
     SDD_CUDA(ctx->counters.ensure(3 * sizeof(unsigned long long)));
     SDD_CUDA(ctx->queue.ensure(sizeof(int32_t)));
     SDD_CUDA(ctx->err.ensure(sizeof(int32_t)));
-    const size_t hbytes = ni * sizeof(Item) + (n_nodes + 1) * sizeof(int32_t);
     ctx->last_h2d = 0;
-    if (!P.cached) {
+    const bool own = &P == &ctx->plan;
+    if (!(own && P.cached)) {
         if (ctx->items_done) SDD_CUDA(cudaEventSynchronize(ctx->items_done));
         if (hbytes > ctx->h_items_cap) {
             if (ctx->h_items) cudaFreeHost(ctx->h_items);
@@ -524,13 +577,16 @@ sdd_status prepare(sdd_ctx *ctx, const Plan &P, int n_nodes, cudaStream_t s) {
             SDD_CUDA(cudaMallocHost((void **)&ctx->h_items, hbytes + hbytes / 4 + 256));
             ctx->h_items_cap = hbytes + hbytes / 4 + 256;
         }
-        std::memcpy(ctx->h_items, P.items.data(), ni * sizeof(Item));
-        std::memcpy(reinterpret_cast<unsigned char *>(ctx->h_items) + ni * sizeof(Item),
-                    P.node_item0.data(), (n_nodes + 1) * sizeof(int32_t));
+        unsigned char *h = reinterpret_cast<unsigned char *>(ctx->h_items);
+        std::memcpy(h, P.items.data(), ni * sizeof(Item));
+        h += ni * sizeof(Item);
+        std::memcpy(h, P.node_item0.data(), ((size_t)n_nodes + 1) * sizeof(int32_t));
+        h += ((size_t)n_nodes + 1) * sizeof(int32_t);
+        if (!P.order.empty()) std::memcpy(h, P.order.data(), P.order.size() * sizeof(int32_t));
         SDD_CUDA(cudaMemcpyAsync(ctx->items.p, ctx->h_items, hbytes, cudaMemcpyHostToDevice, s));
         SDD_CUDA(cudaEventRecord(ctx->items_done, s));
         ctx->last_h2d = hbytes;
-        ctx->plan_valid = P.cacheable;
+        ctx->plan_valid = own;
     }
     return SDD_OK;
 }
@@ -546,6 +602,9 @@ sdd_status enqueue(sdd_ctx *ctx, const Plan &P, const Launch &L, WalkArgs A, cud
     SDD_CUDA(cudaMemsetAsync(ctx->counters.p, 0, 3 * sizeof(unsigned long long), s));
     A.items = (const Item *)ctx->items.p;
     A.n_items = (int32_t)ni;
+    A.order = P.order.empty() ? nullptr
+                              : reinterpret_cast<const int32_t *>(reinterpret_cast<unsigned char *>(ctx->items.p) +
+                                                                  ni * sizeof(Item) + ((size_t)n_nodes + 1) * sizeof(int32_t));
     A.slots = (double *)ctx->slots.p;
     A.item_trunc = (int32_t *)ctx->trunc.p;
     A.counters = (unsigned long long *)ctx->counters.p;
@@ -686,10 +745,8 @@ sdd_status sdd_interface_values(sdd_ctx *ctx, const double *nodes_xz, const uint
     if (!nodes_xz || !mean || !se) return fail(SDD_E_ARG, "nodes_xz, mean and se must not be NULL");
     st = check_nodes(ctx, nodes_xz, n_nodes);
     if (st != SDD_OK) return st;
-    long long total = 0;
-    for (int j = 0; j < n_nodes; ++j) total += n_paths[j];
-    const Launch L = choose_launch(ctx, cfg, dt, total);
-    const Plan P = plan_cached(ctx, n_nodes, n_paths, L.chunk, 0, true);
+    const Launch L = choose_launch(ctx, cfg, dt);
+    const Plan &P = plan_cached(ctx, n_nodes, n_paths, 0, L);
     cudaStream_t s = ctx->stream;
     const size_t ob = (size_t)n_nodes * ctx->E * 2 * sizeof(double);
     SDD_CUDA(ctx->nodes.ensure((size_t)n_nodes * 2 * sizeof(double)));
@@ -739,10 +796,8 @@ sdd_status sdd_interface_values_device(sdd_ctx *ctx, const double *d_nodes_xz,
     if (st != SDD_OK) return st;
     if (n_nodes == 0) return SDD_OK;
     if (!d_nodes_xz || !d_mean || !d_se) return fail(SDD_E_ARG, "d_nodes_xz, d_mean and d_se must not be NULL");
-    long long total = 0;
-    for (int j = 0; j < n_nodes; ++j) total += n_paths[j];
-    const Launch L = choose_launch(ctx, cfg, dt, total);
-    const Plan P = plan_cached(ctx, n_nodes, n_paths, L.chunk, 0, true);
+    const Launch L = choose_launch(ctx, cfg, dt);
+    const Plan &P = plan_cached(ctx, n_nodes, n_paths, 0, L);
     cudaStream_t s = (cudaStream_t)stream;
     WalkArgs A = base_args(ctx, L, dt, seed);
     A.nodes = d_nodes_xz;
@@ -814,8 +869,8 @@ sdd_status sdd_walk_records(sdd_ctx *ctx, double x0, double z0, uint32_t node_id
     const double xz[2] = {x0, z0};
     st = check_nodes(ctx, xz, 1);
     if (st != SDD_OK) return st;
-    const Launch L = choose_launch(ctx, cfg, dt, count);
-    const Plan P = plan_cached(ctx, 1, &np, L.chunk, p0, false);
+    const Launch L = choose_launch(ctx, cfg, dt);
+    const Plan P = plan_work(1, nullptr, &np, p0, L);
     cudaStream_t s = ctx->stream;
     SDD_CUDA(ctx->nodes.ensure(2 * sizeof(double)));
     SDD_CUDA(ctx->node_ids.ensure(sizeof(uint32_t)));
@@ -948,9 +1003,14 @@ extern "C" sdd_status sdd_interface_values_noalloc(sdd_ctx *ctx, const double *d
 
     long long total = 0;
     for (int j = 0; j < n_nodes; ++j) total += n_paths[j];
-    Launch L = choose_launch(ctx, cfg, dt, total);
-    // widen the chunks until the work items fit the scratch array
+    Launch L = choose_launch(ctx, cfg, dt);
+    // fixed-size items (the table is built on the device): about 6 per warp,
+    // widened until they fit the scratch array
     long long chunk = L.chunk;
+    if (chunk == 0) {
+        const long long per = (long long)L.grid * (L.block / 32) * 6;
+        chunk = std::max<long long>(32, ((total + per - 1) / per + 31) / 32 * 32);
+    }
     const long long room = (long long)kNaItems - n_nodes;
     if (chunk * room < total) chunk = (total + room - 1) / room;
     long long n_items = 0;
@@ -1069,7 +1129,7 @@ extern "C" sdd_status sdd_interface_values_target(sdd_ctx *ctx, const double *no
     std::vector<int64_t> begin((size_t)n_nodes, 0), extra((size_t)n_nodes, 0);
 
     // phase 1: the pilot walks of every node
-    Launch L = choose_launch(ctx, cfg, dt, (long long)n_pilot * n_nodes);
+    Launch L = choose_launch(ctx, cfg, dt);
     WalkArgs A = base_args(ctx, L, dt, seed);
     A.nodes = (const double *)ctx->nodes.p;
     if (node_ids) {
@@ -1079,7 +1139,7 @@ extern "C" sdd_status sdd_interface_values_target(sdd_ctx *ctx, const double *no
         A.node_ids = (const uint32_t *)ctx->node_ids.p;
     }
     ctx->plan_valid = false;
-    Plan P1 = plan_ranges(n_nodes, begin.data(), pilot.data(), L.chunk);
+    Plan P1 = plan_work(n_nodes, begin.data(), pilot.data(), 0, L);
     std::vector<double> s1, s2;
     std::vector<long long> v1, v2;
     unsigned long long c1[3], c2[3];
@@ -1108,11 +1168,11 @@ extern "C" sdd_status sdd_interface_values_target(sdd_ctx *ctx, const double *no
 
     // phase 2: the remaining walks, paths n_pilot .. N-1 of each node
     if (total2 > 0) {
-        L = choose_launch(ctx, cfg, dt, total2);
+        L = choose_launch(ctx, cfg, dt);
         WalkArgs A2 = base_args(ctx, L, dt, seed);
         A2.nodes = A.nodes;
         A2.node_ids = A.node_ids;
-        Plan P2 = plan_ranges(n_nodes, begin.data(), extra.data(), L.chunk);
+        Plan P2 = plan_work(n_nodes, begin.data(), extra.data(), 0, L);
         st = run_phase(ctx, P2, L, A2, n_nodes, s2, v2, c2, &ms2);
         if (st != SDD_OK) return st;
     } else {
@@ -1198,10 +1258,8 @@ extern "C" sdd_status sdd_batch_values(const sdd_batch_entry *entries, int32_t n
     const int32_t n_nodes = (int32_t)paths.size();
     first[n_entries] = n_nodes;
     if (n_nodes == 0) return SDD_OK;
-    long long total = 0;
-    for (int64_t p : paths) total += p;
-    const Launch L = choose_launch(own, cfg, dt, total, kmax_for(Kmax), GC_RASTER_MULTI);
-    Plan P = plan_items(n_nodes, paths.data(), L.chunk, 0);
+    const Launch L = choose_launch(own, cfg, dt, kmax_for(Kmax), GC_RASTER_MULTI);
+    Plan P = plan_work(n_nodes, nullptr, paths.data(), 0, L);
     for (Item &I : P.items) I.model = node_model[I.node];
     own->plan_valid = false;
 
@@ -1424,13 +1482,14 @@ sdd_status srv_launch(sdd_server *srv, SrvLane &L, std::vector<SrvPiece> &batch)
     long long total = 0;
     for (int64_t c : count) total += c;
     L.walks = (uint64_t)total;
-    const Launch La = choose_launch(srv->tmpl, &srv->cfg.launch, srv->cfg.dt, total, kmax_for(Kmax),
+    const Launch La = choose_launch(srv->tmpl, &srv->cfg.launch, srv->cfg.dt, kmax_for(Kmax),
                                     GC_RASTER_MULTI);
-    Plan P = plan_ranges(n_nodes, begin.data(), count.data(), La.chunk);
+    Plan P = plan_work(n_nodes, begin.data(), count.data(), 0, La);
     for (Item &I : P.items) I.model = node_model[I.node];
     const size_t ni = P.items.size();
     cudaStream_t s = L.s;
-    SDD_CUDA(L.items.ensure(ni * sizeof(Item) + (n_nodes + 1) * sizeof(int32_t)));
+    const size_t tb = table_bytes(P, n_nodes);
+    SDD_CUDA(L.items.ensure(tb));
     SDD_CUDA(L.slots.ensure(std::max<size_t>(ni, 1) * (size_t)E * 4 * sizeof(double)));
     SDD_CUDA(L.trunc.ensure(std::max<size_t>(ni, 1) * sizeof(int32_t)));
     SDD_CUDA(L.counters.ensure(3 * sizeof(unsigned long long)));
@@ -1451,9 +1510,12 @@ sdd_status srv_launch(sdd_server *srv, SrvLane &L, std::vector<SrvPiece> &batch)
         SDD_CUDA(cudaMallocHost((void **)&L.h_nvalid, (size_t)n_nodes * sizeof(long long)));
         L.h_cap_nodes = n_nodes;
     }
-    std::vector<unsigned char> hi(ni * sizeof(Item) + (n_nodes + 1) * sizeof(int32_t));
+    std::vector<unsigned char> hi(tb);
     std::memcpy(hi.data(), P.items.data(), ni * sizeof(Item));
     std::memcpy(hi.data() + ni * sizeof(Item), P.node_item0.data(), (n_nodes + 1) * sizeof(int32_t));
+    if (!P.order.empty())
+        std::memcpy(hi.data() + ni * sizeof(Item) + (n_nodes + 1) * sizeof(int32_t), P.order.data(),
+                    P.order.size() * sizeof(int32_t));
     SDD_CUDA(cudaMemcpyAsync(L.items.p, hi.data(), hi.size(), cudaMemcpyHostToDevice, s));
     SDD_CUDA(cudaMemcpyAsync(L.nodes.p, nodes.data(), nodes.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     SDD_CUDA(cudaMemcpyAsync(L.ids.p, ids.data(), ids.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
@@ -1463,6 +1525,9 @@ sdd_status srv_launch(sdd_server *srv, SrvLane &L, std::vector<SrvPiece> &batch)
     WalkArgs A = base_args(srv->tmpl, La, srv->cfg.dt, srv->cfg.seed);
     A.items = (const Item *)L.items.p;
     A.n_items = (int32_t)ni;
+    if (!P.order.empty())
+        A.order = reinterpret_cast<const int32_t *>(reinterpret_cast<unsigned char *>(L.items.p) +
+                                                    ni * sizeof(Item) + (n_nodes + 1) * sizeof(int32_t));
     A.nodes = (const double *)L.nodes.p;
     A.node_ids = (const uint32_t *)L.ids.p;
     A.slots = (double *)L.slots.p;
@@ -1932,16 +1997,16 @@ extern "C" sdd_status sdd_autotune(sdd_ctx *ctx, const double *nodes_xz, int32_t
     sdd_status st = check_call(ctx, n_nodes, n_paths, dt, base);
     if (st != SDD_OK) return st;
     if (n_nodes < 1 || !nodes_xz) return fail(SDD_E_ARG, "autotuning needs nodes");
-    if (base && (base->block_threads || base->chunk_paths))
-        return fail(SDD_E_ARG, "base must leave block_threads and chunk_paths automatic");
+    if (base && (base->block_threads || base->chunk_paths || base->guided_factor))
+        return fail(SDD_E_ARG, "base must leave block_threads, chunk_paths and guided_factor automatic");
     sdd_config c;
     std::memset(&c, 0, sizeof(c));
     if (base) c = *base;
     const int blocks[] = {128, 192, 256};
-    const int ks[] = {2, 4, 6, 10, 16};
+    const int ks[] = {1, 2, 4, 8};  // guided factors
     std::vector<double> mean((size_t)n_nodes * ctx->E * 2), se(mean.size());
     double best_rate = -1.0;
-    int best_b = 256, best_k = 6;
+    int best_b = 256, best_k = 2;
     const int saved_b = ctx->tune_block, saved_k = ctx->tune_k;
     const bool saved_read = ctx->tune_file_read;
     ctx->tune_file_read = true;  // time the candidates, not the cached choice
@@ -1985,11 +2050,9 @@ extern "C" sdd_status sdd_autotune(sdd_ctx *ctx, const double *nodes_xz, int32_t
     }
     if (best) {
         *best = c;
-        long long total = 0;
-        for (int j = 0; j < n_nodes; ++j) total += n_paths[j];
-        const Launch L = choose_launch(ctx, &c, dt, total);
-        best->block_threads = L.block;
-        best->chunk_paths = L.chunk;
+        best->block_threads = best_b;
+        best->chunk_paths = 0;
+        best->guided_factor = best_k;
     }
     if (best_steps_per_s) *best_steps_per_s = best_rate;
     return SDD_OK;

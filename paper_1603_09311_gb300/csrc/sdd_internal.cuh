@@ -112,6 +112,7 @@ struct ModelDev {
 struct WalkArgs {
     const Item *items;
     int32_t n_items;
+    const int32_t *order;      // [n_items] item of each queue position (nullptr: identity)
     const double *nodes;       // [n][2] absolute
     const uint32_t *node_ids;  // nullable
     double dt;
@@ -123,7 +124,8 @@ struct WalkArgs {
     uint32_t rk0[10], rk1[10]; // the key of each Philox round (key bumped by the Weyl constants)
     uint32_t max_steps;
     double *slots;             // [n_items][E][4]: sum re, sum im, sum re^2, sum im^2
-    int32_t *item_trunc;       // [n_items] truncated walks
+                               // (cleared by the warp that opens the item)
+    int32_t *item_trunc;       // [n_items] truncated walks (cleared likewise)
     unsigned long long *counters;  // steps, walks, truncated
     int32_t *queue;            // next item (zero before launch)
     int32_t *error;            // nonzero if a device-side check failed

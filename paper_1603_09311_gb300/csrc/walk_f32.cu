@@ -258,17 +258,22 @@ struct WalkerF32 {
 
     // PAIRS Philox calls, two Euler steps each, per call of iterate: the
     // per-iteration work of the scheduler loop (constants, vote, branch) is
-    // shared by 2 PAIRS steps.  0 running, 1 exited, 2 truncated (max_steps is
-    // a multiple of 8, so a walk is only truncated at the end of an iteration).
+    // shared by 2 PAIRS steps.  The calls depend only on the step counter, so
+    // all of them are issued first, as independent chains the SM can overlap
+    // (a walk that exits early discards the rest).  0 running, 1 exited,
+    // 2 truncated (max_steps is a multiple of 8, so a walk is only truncated
+    // at the end of an iteration).
     static constexpr int PAIRS = KMAX == 8 ? 2 : 4;
 
     __device__ __forceinline__ int iterate(const ModelDev &M, const WalkArgs &A, uint32_t path,
                                            ExitInfo<float> &ei) {
+        uint4 w[PAIRS];
+#pragma unroll
+        for (int q = 0; q < PAIRS; ++q) w[q] = philox_rk_pre((n >> 1) + q, 0u, pre_x, pre_y, A.rk0, A.rk1);
 #pragma unroll
         for (int q = 0; q < PAIRS; ++q) {
-            const uint4 w = philox_rk_pre((n >> 1) + q, 0u, pre_x, pre_y, A.rk0, A.rk1);
-            if (substep(M, A, path, w.x, w.y, 2u * q, ei)) return 1;
-            if (substep(M, A, path, w.z, w.w, 2u * q + 1u, ei)) return 1;
+            if (substep(M, A, path, w[q].x, w[q].y, 2u * q, ei)) return 1;
+            if (substep(M, A, path, w[q].z, w[q].w, 2u * q + 1u, ei)) return 1;
         }
         n += 2 * PAIRS;
         if (n >= A.max_steps) {

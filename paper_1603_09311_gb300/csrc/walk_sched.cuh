@@ -2,23 +2,27 @@
 //
 // Work model.  The estimator of Sec. 3.1 averages independent walks per
 // interface node; the node values are independent of one another (Sec. 5).
-// The host cuts every node's paths into work items (node, path chunk).
-// Each warp of a persistent grid takes items from a global atomic counter and
-// keeps its 32 lanes busy: a lane whose walk has reached the boundary takes
-// the next path of the warp's current item at once, and when that item is
-// fully handed out the warp opens the next item while the last walks of the
-// previous one finish (two items may be open per warp).  Uneven exit times
-// therefore idle no lane until the queue is empty.
+// The host cuts every node's paths into work items (node, path range) and
+// orders them so that item sizes shrink toward the end of the queue (guided
+// self-scheduling, down to one walk per lane): when the queue runs dry, every
+// warp holds little unfinished work.  Each warp of a persistent grid takes
+// items from a global atomic counter and keeps its 32 lanes busy: a lane
+// whose walk has reached the boundary takes the next path of the warp's
+// current item at once, and the warp opens the next item as soon as the
+// current one is fully handed out, however many earlier items still have
+// walks in flight.  Uneven exit times therefore idle no lane until the queue
+// is empty.
 //
-// Exit records.  A finished walk writes a small record (exit point, hit
-// fraction theta, wall, last material, per-material step counts) into a
+// Exit records.  A finished walk writes a small record (item, exit point,
+// hit fraction theta, wall, last material, per-material step counts) into a
 // per-warp ring in shared memory.  Once 32 records are waiting, the whole
 // warp turns them into samples g(exit) exp(-i (1/2) sum_m kappa_{e,m} T_m)
-// for every evaluation e, lane l handling evaluation l mod Epad, and adds
-// them to per-lane FP64 sums (sum re, sum im, sum re^2, sum im^2) kept per
-// open item.  When an item's last walk is done its sums are reduced across
-// the lanes with warp shuffles (fixed order) and written to the item's slot;
-// a second kernel adds the slots of each node in item order.
+// for every evaluation e, lane l handling evaluation l mod Epad.  The samples
+// of each item are summed across the lanes with warp shuffles (fixed order)
+// and lane e adds them to the item's slot in global memory (sum re, sum im,
+// sum re^2, sum im^2; a few MB, L2-resident).  An item belongs to the one
+// warp that opened it, so its slot needs no atomics.  A second kernel adds
+// the slots of each node in item order.
 #pragma once
 
 #include "sdd_internal.cuh"
@@ -103,28 +107,25 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const uint32_t (&rk0)[10],
 }
 
 // Shared-memory layout of one CTA: model tables, then for each warp its
-// exit-record ring, its scheduler state and its lanes' FP64 sums.
+// exit-record ring and its scheduler state.
 template <class Real, int KMAX>
 struct Ring {
     Real x[kRing], z[kRing], th[kRing];
-    uint32_t meta[kRing];  // wall | m_last << 2 | tag << 5 | truncated << 6 | model << 8
+    uint32_t meta[kRing];  // wall | m_last << 2 | truncated << 6 | model << 8
+    int32_t item[kRing];
     uint32_t n[kRing];     // occupation steps (all steps but the exiting one)
     uint32_t path[kRing];
     uint32_t cnt[KMAX > 1 ? KMAX - 1 : 1][kRing];  // steps in materials 1..K-1
 };
 
 // Scheduler state of one warp (every field is the same for all its lanes,
-// each lane reads back what it wrote) and the lanes' sums, kept out of
-// registers because only the exit handler touches them.
+// each lane reads back what it wrote), kept out of registers because only
+// the exit handler touches it.
 struct WarpState {
-    double acc[2][4][32];  // [set][sum re, sum im, sum re^2, sum im^2][lane]
     unsigned long long steps[32];
     unsigned long long walks, trunc;
     double nx0, nz0;
-    int32_t item[2];   // item of accumulator set (-1: free)
-    int32_t out[2];    // walks handed out and not yet ended
-    int32_t ntr[2];    // truncated walks
-    int32_t disp_set, disp_rem, disp_model;
+    int32_t disp_item, disp_rem, disp_model;
     uint32_t disp_next, nid;
     uint32_t head, tail;
     int32_t queue_empty;
@@ -167,13 +168,17 @@ struct ExitInfo {
 //   using Real; static constexpr int KMAX;
 //   start(M, A, x0, z0, path, node_id, model)  -- begin a walk
 //   iterate(M, A, path, ExitInfo&) -> 0 running, 1 exited, 2 truncated
-//     (two Euler steps per call)
+//     (a few Euler steps per call; max_steps is a multiple of them)
 //   counts(c): steps spent in materials 1..KMAX-1 (at the exit)
 //   bind(a): shared-memory address of the lane's occupancy histogram
 //   static sample(M, T, A, model, e, x, z, th, wall, mlast, counts) -> double2
 //   static to_abs(M, x, z, ax, az)
+// Launch bounds: at most 256 threads, and at least 3 such CTAs per SM, which
+// leaves up to 85 registers a thread.  24 resident warps whose iterations
+// carry four independent Philox chains keep the issue slots fuller than 32
+// warps squeezed into 64 registers.
 template <class W>
-__global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ ModelDev M,
+__global__ void __launch_bounds__(256, 3) walk_kernel(const __grid_constant__ ModelDev M,
                                                    const WalkArgs A) {
     using Real = typename W::Real;
     constexpr int KMAX = W::KMAX;
@@ -192,17 +197,10 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     const bool dump = A.rec_steps != nullptr;
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) S.acc[s][q][lane] = 0.0;
     S.steps[lane] = 0ull;
     if (lane == 0) {
         S.walks = 0ull; S.trunc = 0ull;
-        S.item[0] = S.item[1] = -1;
-        S.out[0] = S.out[1] = 0;
-        S.ntr[0] = S.ntr[1] = 0;
-        S.disp_set = -1; S.disp_rem = 0; S.disp_model = 0; S.disp_next = 0; S.nid = 0;
+        S.disp_item = -1; S.disp_rem = 0; S.disp_model = 0; S.disp_next = 0; S.nid = 0;
         S.head = S.tail = 0;
         S.queue_empty = 0;
         S.nx0 = S.nz0 = 0.0;
@@ -213,12 +211,14 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
     W w;
     w.bind((uint32_t)__cvta_generic_to_shared(&WS.hist[0][lane]));
     bool active = false;
-    int tag = 0;
+    int item = 0;
     int model = 0;
     uint32_t path = 0;
 
     // Turn records [head, head + cnt) of the ring into samples; lane l
-    // handles evaluation l mod Epad of records l / Epad, l / Epad + 32 / Epad, ...
+    // handles evaluation l mod Epad of records l / Epad, l / Epad + 32 / Epad,
+    // ...; the samples of each item are summed across the lanes in a fixed
+    // shuffle order and lane e adds them to the item's slot for evaluation e.
     auto process = [&](int cnt) {
         const int Epad = M.Epad;
         const int my_e = lane & (Epad - 1);
@@ -228,11 +228,12 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
         const int rounds = (cnt * Epad + 31) >> 5;
         for (int k = 0; k < rounds; ++k) {
             const int ri = k * per_round + my_ro;
+            double2 v = make_double2(0.0, 0.0);
+            int my_it = -1;
             if (ri < cnt && my_e < M.E) {
                 const int s = (head + ri) & (kRing - 1);
                 const uint32_t meta = R.meta[s];
                 const bool tr = (meta >> 6) & 1u;
-                const int rt = (meta >> 5) & 1u;
                 uint32_t c[KMAX];
                 uint32_t rest = R.n[s];
 #pragma unroll
@@ -257,14 +258,31 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
                         A.rec_mlast[o] = (int)((meta >> 2) & 7u);
                     }
                 } else if (!tr) {
-                    const double2 v = W::sample(M, T, A, (int)(meta >> 8), my_e, R.x[s], R.z[s],
-                                                R.th[s], (int)(meta & 3u), (int)((meta >> 2) & 7u), c);
-                    double *a0 = &S.acc[rt][0][lane];
-                    a0[0] += v.x;
-                    a0[32] += v.y;
-                    a0[64] = fma(v.x, v.x, a0[64]);
-                    a0[96] = fma(v.y, v.y, a0[96]);
+                    v = W::sample(M, T, A, (int)(meta >> 8), my_e, R.x[s], R.z[s], R.th[s],
+                                  (int)(meta & 3u), (int)((meta >> 2) & 7u), c);
+                    my_it = R.item[s];
                 }
+            }
+            unsigned pend = __ballot_sync(kFull, my_it >= 0);
+            while (pend) {
+                const int it = __shfl_sync(kFull, my_it, __ffs(pend) - 1);
+                const bool mine = my_it == it;
+                double a0 = mine ? v.x : 0.0, a1 = mine ? v.y : 0.0;
+                double a2 = a0 * a0, a3 = a1 * a1;
+                for (int off = 16; off >= Epad; off >>= 1) {
+                    a0 += __shfl_xor_sync(kFull, a0, off);
+                    a1 += __shfl_xor_sync(kFull, a1, off);
+                    a2 += __shfl_xor_sync(kFull, a2, off);
+                    a3 += __shfl_xor_sync(kFull, a3, off);
+                }
+                if (lane < M.E) {
+                    double *o = A.slots + ((size_t)it * M.E + lane) * 4;
+                    o[0] += a0;
+                    o[1] += a1;
+                    o[2] += a2;
+                    o[3] += a3;
+                }
+                pend &= ~__ballot_sync(kFull, mine);
             }
         }
         __syncwarp();
@@ -272,54 +290,32 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
         __syncwarp();
     };
 
-    // Reduce the sums of set s across lanes (fixed order) and store them.
-    auto flush_set = [&](int s) {
-        const int Epad = M.Epad;
-        double v0 = S.acc[s][0][lane], v1 = S.acc[s][1][lane];
-        double v2 = S.acc[s][2][lane], v3 = S.acc[s][3][lane];
-        for (int off = 16; off >= Epad; off >>= 1) {
-            v0 += __shfl_xor_sync(kFull, v0, off);
-            v1 += __shfl_xor_sync(kFull, v1, off);
-            v2 += __shfl_xor_sync(kFull, v2, off);
-            v3 += __shfl_xor_sync(kFull, v3, off);
-        }
-        const int it = S.item[s];
-        if (!dump) {
-            if (lane < M.E) {
-                double *o = A.slots + ((size_t)it * M.E + lane) * 4;
-                o[0] = v0; o[1] = v1; o[2] = v2; o[3] = v3;
-            }
-            if (lane == 0) A.item_trunc[it] = S.ntr[s];
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) S.acc[s][q][lane] = 0.0;
-        __syncwarp();
-        if (lane == 0) { S.item[s] = -1; S.ntr[s] = 0; }
-        __syncwarp();
-    };
-
-    // Hand paths to idle lanes; open new items while a set is free.
+    // Hand paths to idle lanes, opening the next queued item whenever the
+    // current one is fully handed out.
     auto refill = [&]() {
         unsigned need = __ballot_sync(kFull, !active);
         while (need) {
             if (S.disp_rem == 0) {
                 if (S.queue_empty) break;
-                const int fs = S.item[0] < 0 ? 0 : (S.item[1] < 0 ? 1 : -1);
-                if (fs < 0) break;  // both sets open: wait for one to finish
-                int it = 0;
-                if (lane == 0) it = atomicAdd(A.queue, 1);
-                it = __shfl_sync(kFull, it, 0);
-                if (it >= A.n_items) {
+                int q = 0;
+                if (lane == 0) q = atomicAdd(A.queue, 1);
+                q = __shfl_sync(kFull, q, 0);
+                if (q >= A.n_items) {
                     if (lane == 0) S.queue_empty = 1;
                     __syncwarp();
                     break;
                 }
+                const int it = A.order ? A.order[q] : q;
                 const Item I = A.items[it];
+                if (!dump) {
+                    if (lane < M.E) {
+                        double *o = A.slots + ((size_t)it * M.E + lane) * 4;
+                        o[0] = 0.0; o[1] = 0.0; o[2] = 0.0; o[3] = 0.0;
+                    }
+                    if (lane == 0) A.item_trunc[it] = 0;
+                }
                 if (lane == 0) {
-                    S.item[fs] = it;
-                    S.out[fs] = 0;
-                    S.ntr[fs] = 0;
-                    S.disp_set = fs;
+                    S.disp_item = it;
                     S.disp_model = I.model;
                     S.disp_next = I.path0;
                     S.disp_rem = I.count;
@@ -337,7 +333,7 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
             const bool mine = ((need >> lane) & 1u) && rank < k;
             if (mine) {
                 path = S.disp_next + (uint32_t)rank;
-                tag = S.disp_set;
+                item = S.disp_item;
                 model = S.disp_model;
                 active = true;
                 w.start(M, A, S.nx0, S.nz0, path, S.nid, model);
@@ -347,7 +343,6 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
             if (lane == 0) {
                 S.disp_next += (uint32_t)k;
                 S.disp_rem = rem - k;
-                S.out[S.disp_set] += k;
             }
             __syncwarp();
         }
@@ -372,8 +367,9 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
             R.x[slot] = ei.x;
             R.z[slot] = ei.z;
             R.th[slot] = ei.th;
-            R.meta[slot] = (uint32_t)ei.wall | ((uint32_t)ei.mlast << 2) | ((uint32_t)tag << 5) |
-                           ((uint32_t)tr << 6) | ((uint32_t)model << 8);
+            R.meta[slot] = (uint32_t)ei.wall | ((uint32_t)ei.mlast << 2) | ((uint32_t)tr << 6) |
+                           ((uint32_t)model << 8);
+            R.item[slot] = item;
             R.n[slot] = ei.nocc;
             R.path[slot] = path;
             uint32_t c[KMAX > 1 ? KMAX - 1 : 1];
@@ -381,37 +377,24 @@ __global__ void __launch_bounds__(256) walk_kernel(const __grid_constant__ Model
 #pragma unroll
             for (int j = 1; j < KMAX; ++j) R.cnt[j - 1][slot] = c[j - 1];
             S.steps[lane] += (unsigned long long)ei.nocc + (tr ? 0ull : 1ull);
+            if (tr && !dump) atomicAdd(&A.item_trunc[item], 1);
         }
-        const unsigned t1 = __ballot_sync(kFull, st != 0 && tag == 1);
-        const unsigned tr0 = __ballot_sync(kFull, st == 2 && tag == 0);
-        const unsigned tr1 = __ballot_sync(kFull, st == 2 && tag == 1);
+        const unsigned trm = __ballot_sync(kFull, st == 2);
         if (lane == 0) {
             S.tail = tail + (uint32_t)nex;
-            S.out[1] -= __popc(t1);
-            S.out[0] -= nex - __popc(t1);
-            S.ntr[0] += __popc(tr0);
-            S.ntr[1] += __popc(tr1);
             S.walks += (unsigned long long)nex;
-            S.trunc += (unsigned long long)(__popc(tr0) + __popc(tr1));
+            S.trunc += (unsigned long long)__popc(trm);
         }
         __syncwarp();
 
         // 2. a full batch of records
         while (S.tail - S.head >= 32) process(32);
 
-        // 3. items whose walks have all ended
-#pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            if (S.item[s] >= 0 && S.out[s] == 0 && !(S.disp_set == s && S.disp_rem > 0)) {
-                if (S.tail != S.head) process((int)(S.tail - S.head));
-                flush_set(s);
-            }
-        }
-
-        // 4. new walks for idle lanes
+        // 3. new walks for idle lanes
         refill();
         n_active = __popc(__ballot_sync(kFull, active));
     }
+    if (S.tail != S.head) process((int)(S.tail - S.head));
     // every item handed to this warp has been flushed (its walks all ended)
 
     unsigned long long my_steps = S.steps[lane];

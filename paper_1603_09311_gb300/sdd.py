@@ -61,7 +61,8 @@ class sdd_model_desc(ctypes.Structure):
 class sdd_config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("max_steps", ctypes.c_int64),
                 ("block_threads", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("chunk_paths", ctypes.c_int32), ("use_graph", ctypes.c_int32)]
+                ("chunk_paths", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("guided_factor", ctypes.c_int32)]
 
 
 class sdd_batch_entry(ctypes.Structure):
@@ -223,12 +224,12 @@ def make_desc(model: dict):
 
 
 def make_config(precision="fp32", max_steps=0, block_threads=0, ctas_per_sm=0, chunk_paths=0,
-                use_graph=0):
+                use_graph=0, guided_factor=0):
     c = sdd_config()
     c.precision = SDD_FP64 if precision in ("fp64", SDD_FP64) else SDD_FP32
     c.max_steps, c.block_threads = int(max_steps), int(block_threads)
     c.ctas_per_sm, c.chunk_paths = int(ctas_per_sm), int(chunk_paths)
-    c.use_graph = int(use_graph)
+    c.use_graph, c.guided_factor = int(use_graph), int(guided_factor)
     return c
 
 
@@ -414,7 +415,7 @@ def sdd_walk_records(ctx: Context, x0: float, z0: float, node_id: int, p0: int, 
 
 def sdd_autotune(ctx: Context, nodes, n_paths, dt: float, seed: int, **base):
     """Time candidate launch shapes on this workload; the context keeps the
-    fastest.  Returns ({block_threads, chunk_paths}, walk-steps/s)."""
+    fastest.  Returns ({block_threads, guided_factor}, walk-steps/s)."""
     nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64).reshape(-1, 2))
     npth = _paths(n_paths, nodes.shape[0])
     b = make_config(**base)
@@ -425,7 +426,7 @@ def sdd_autotune(ctx: Context, nodes, n_paths, dt: float, seed: int, **base):
                             ctypes.byref(rate))
     if st != SDD_OK:
         raise SddError(st, "sdd_autotune")
-    return {"block_threads": out.block_threads, "chunk_paths": out.chunk_paths}, rate.value
+    return {"block_threads": out.block_threads, "guided_factor": out.guided_factor}, rate.value
 
 
 def sdd_status_str(status: int) -> str:
