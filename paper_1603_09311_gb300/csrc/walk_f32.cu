@@ -229,23 +229,33 @@ struct WalkerF32 {
         return true;
     }
 
-    // One Euler step driven by the Philox words (wa, wb); sub = 0 or 1 within
-    // the pair.  Returns true when the walk reached the boundary.
-    __device__ __forceinline__ bool substep(const ModelDev &M, const WalkArgs &A, uint32_t path,
-                                            uint32_t wa, uint32_t wb, uint32_t sub,
-                                            ExitInfo<float> &ei) {
-        const float u0 = uni23(wa);
-        // sqrt(-2 ln(u0) dt); |.| only guards the last-ulp sign of lg2 near u0 = 1
-        const float r = sqrtf(fabsf(A.f_cdt * __log2f(u0)));
-        float sn, cs;
-        // angle 2 pi (u1 - 1/2): cos(2 pi u1) = -cs, sin(2 pi u1) = -sn
-        __sincosf(fmaf(one_plus(wb), 6.28318530718f, -9.42477796077f), &sn, &cs);
-        const float Xn = fmaf(-r, cs, X);
-        const float Zn = fmaf(-r, sn, Z);
+    // The part of an Euler step that does not depend on the position: the
+    // step length r = sqrt(-2 ln(u0) dt) and direction of the normal pair
+    // (angle 2 pi (u1 - 1/2), so cos(2 pi u1) = -cs and sin(2 pi u1) = -sn)
+    // from the step's Philox words (wa, wb).
+    struct Incr {
+        float r, sn, cs;
+    };
+    __device__ __forceinline__ static Incr increment(const WalkArgs &A, uint32_t wa, uint32_t wb) {
+        Incr d;
+        // |.| only guards the last-ulp sign of lg2 near u0 = 1
+        d.r = sqrtf(fabsf(A.f_cdt * __log2f(uni23(wa))));
+        __sincosf(fmaf(one_plus(wb), 6.28318530718f, -9.42477796077f), &d.sn, &d.cs);
+        return d;
+    }
+
+    // The rest of the step: move, test the walls, count the occupation.
+    // Only the high 9 bits of wa and wb are read (the bridge uniform, on the
+    // rare steps near a wall).  k = steps of this walk since n.  Returns true
+    // when the walk reached the boundary.
+    __device__ __forceinline__ bool advance(const ModelDev &M, const WalkArgs &A, const Incr &d,
+                                            uint32_t wa, uint32_t wb, uint32_t k, ExitInfo<float> &ei) {
+        const float Xn = fmaf(-d.r, d.cs, X);
+        const float Zn = fmaf(-d.r, d.sn, Z);
         const float dn = fminf(M.fhw - fabsf(Xn), M.fhh - fabsf(Zn));
         if (dmin * dn <= A.f_bthr) {
             if (near_wall(M, A, Xn, Zn, dn, wa, wb, ei)) {
-                ei.nocc = n + sub;
+                ei.nocc = n + k;
                 return true;
             }
         }
@@ -254,6 +264,11 @@ struct WalkerF32 {
         Z = Zn;
         dmin = dn;
         return false;
+    }
+
+    __device__ __forceinline__ bool substep(const ModelDev &M, const WalkArgs &A, uint32_t wa,
+                                            uint32_t wb, uint32_t k, ExitInfo<float> &ei) {
+        return advance(M, A, increment(A, wa, wb), wa, wb, k, ei);
     }
 
     // PAIRS Philox calls, two Euler steps each, per call of iterate: the
@@ -272,8 +287,8 @@ struct WalkerF32 {
         for (int q = 0; q < PAIRS; ++q) w[q] = philox_rk_pre((n >> 1) + q, 0u, pre_x, pre_y, A.rk0, A.rk1);
 #pragma unroll
         for (int q = 0; q < PAIRS; ++q) {
-            if (substep(M, A, path, w[q].x, w[q].y, 2u * q, ei)) return 1;
-            if (substep(M, A, path, w[q].z, w[q].w, 2u * q + 1u, ei)) return 1;
+            if (substep(M, A, w[q].x, w[q].y, 2u * q, ei)) return 1;
+            if (substep(M, A, w[q].z, w[q].w, 2u * q + 1u, ei)) return 1;
         }
         n += 2 * PAIRS;
         if (n >= A.max_steps) {
@@ -282,6 +297,49 @@ struct WalkerF32 {
             ei.nocc = n;
             return 2;
         }
+        return 0;
+    }
+
+    // Cooperative tail (scheduler): once few walks are left, every lane of
+    // the warp computes increments for them, and each walk then runs only
+    // the position-dependent chain of its steps.  The increments are the
+    // ones increment() gives in iterate(), so the walks are the same.
+    static constexpr bool kCoop = true;
+    __device__ __forceinline__ uint32_t steps() const { return n; }
+    __device__ __forceinline__ uint2 key() const { return make_uint2(pre_x, pre_y); }
+
+    // The two increments of Philox pair q of a walk with step counter n0
+    // (even) and key (pre_x, pre_y); the fourth word keeps the high 9 bits of
+    // wa (bits 31..23) and of wb (bits 22..14).
+    __device__ __forceinline__ static void pair_increments(const WalkArgs &A, uint32_t n0, uint2 key,
+                                                           uint32_t q, float4 &s0, float4 &s1) {
+        const uint4 w = philox_rk_pre((n0 >> 1) + q, 0u, key.x, key.y, A.rk0, A.rk1);
+        const Incr a = increment(A, w.x, w.y), b = increment(A, w.z, w.w);
+        s0 = make_float4(a.r, a.sn, a.cs, __uint_as_float((w.x & 0xff800000u) | (w.y >> 9)));
+        s1 = make_float4(b.r, b.sn, b.cs, __uint_as_float((w.z & 0xff800000u) | (w.w >> 9)));
+    }
+
+    // Steps with the cnt (even) increments d[0 .. cnt-1].  0 running,
+    // 1 exited, 2 truncated (at max_steps exactly, as in iterate()).
+    __device__ __forceinline__ int consume(const ModelDev &M, const WalkArgs &A, const float4 *d,
+                                           int cnt, ExitInfo<float> &ei) {
+        for (int k = 0; k < cnt; ++k) {
+            const float4 v = d[k];
+            Incr c;
+            c.r = v.x;
+            c.sn = v.y;
+            c.cs = v.z;
+            const uint32_t hb = __float_as_uint(v.w);
+            if (advance(M, A, c, hb & 0xff800000u, hb << 9, (uint32_t)k, ei)) return 1;
+            if (n + (uint32_t)k + 1u >= A.max_steps) {
+                n += (uint32_t)k + 1u;
+                ei.x = X; ei.z = Z; ei.th = 0.f; ei.wall = 0;
+                ei.mlast = material(M, X, Z);
+                ei.nocc = n;
+                return 2;
+            }
+        }
+        n += (uint32_t)cnt;
         return 0;
     }
 

@@ -24,6 +24,7 @@ template <int KMAX_, int GEO>
 struct WalkerF64 {
     using Real = double;
     static constexpr int KMAX = KMAX_;
+    static constexpr bool kCoop = false;  // no cooperative tail: the parity walk stays plain
 
     double x, z;
     uint32_t n;

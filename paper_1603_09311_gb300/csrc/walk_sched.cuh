@@ -147,7 +147,12 @@ struct WarpSmem {
     Ring<Real, KMAX> ring;
     WarpState st;
     uint32_t hist[KMAX == 8 ? 8 : 1][32];  // per-lane step counts of up to 8 materials
+    float4 tail[sizeof(Real) == 4 ? 64 : 1];  // step increments of the cooperative tail
 };
+
+// A warp whose queue is drained switches to the cooperative tail once it
+// has at most this many walks left.
+constexpr int kTailWalks = 8;
 
 
 template <class Real, int KMAX>
@@ -348,18 +353,13 @@ __global__ void __launch_bounds__(256, 3) walk_kernel(const __grid_constant__ Mo
         }
     };
 
-    refill();
-    int n_active = __popc(__ballot_sync(kFull, active));
+    // Records of the walks that ended this iteration (st: 1 exited,
+    // 2 truncated), then a batch of samples once 32 records are waiting.
     ExitInfo<Real> ei;
-    while (n_active > 0) {
-        int st = 0;
-        if (active) st = w.iterate(M, A, path, ei);
+    auto on_exits = [&](int st) {
         const unsigned em = __ballot_sync(kFull, st != 0);
-        if (em == 0) continue;
         const int nex = __popc(em);
         if (st != 0) active = false;
-
-        // 1. records of the walks that ended
         const uint32_t tail = S.tail;
         if (st != 0) {
             const int slot = (tail + __popc(em & lt_mask)) & (kRing - 1);
@@ -386,13 +386,49 @@ __global__ void __launch_bounds__(256, 3) walk_kernel(const __grid_constant__ Mo
             S.trunc += (unsigned long long)__popc(trm);
         }
         __syncwarp();
-
-        // 2. a full batch of records
         while (S.tail - S.head >= 32) process(32);
+    };
 
-        // 3. new walks for idle lanes
+    refill();
+    int n_active = __popc(__ballot_sync(kFull, active));
+    while (n_active > 0) {
+        if (W::kCoop && n_active <= kTailWalks && S.queue_empty && S.disp_rem == 0) break;
+        int st = 0;
+        if (active) st = w.iterate(M, A, path, ei);
+        if (__ballot_sync(kFull, st != 0) == 0) continue;
+        on_exits(st);
         refill();
         n_active = __popc(__ballot_sync(kFull, active));
+    }
+
+    // Cooperative tail: nothing is left to hand out and at most kTailWalks
+    // walks remain.  Each round, lane l computes Philox pair l / a of the
+    // (l mod a)-th live walk (a walks live), so every walk gets 32 / a pairs
+    // of step increments at once; then each live lane runs its 2 (32 / a)
+    // steps from shared memory, whose serial part is only the move, the wall
+    // tests and the material lookup.
+    if constexpr (W::kCoop) {
+        float4 *buf = WS.tail;
+        while (n_active > 0) {
+            const unsigned act = __ballot_sync(kFull, active);
+            const int a = __popc(act);
+            const int per = 32 / a;
+            const int j = lane % a, q = lane / a;
+            unsigned m = act;
+            for (int t = 0; t < j; ++t) m &= m - 1u;
+            const int src = __ffs(m) - 1;
+            const uint32_t n0 = __shfl_sync(kFull, w.steps(), src);
+            const uint2 k0 = w.key();
+            const uint2 key = make_uint2(__shfl_sync(kFull, k0.x, src), __shfl_sync(kFull, k0.y, src));
+            if (q < per) W::pair_increments(A, n0, key, (uint32_t)q, buf[j * 2 * per + 2 * q],
+                                            buf[j * 2 * per + 2 * q + 1]);
+            __syncwarp();
+            int st = 0;
+            if (active) st = w.consume(M, A, buf + __popc(act & lt_mask) * 2 * per, 2 * per, ei);
+            __syncwarp();
+            if (__ballot_sync(kFull, st != 0) != 0) on_exits(st);
+            n_active = __popc(__ballot_sync(kFull, active));
+        }
     }
     if (S.tail != S.head) process((int)(S.tail - S.head));
     // every item handed to this warp has been flushed (its walks all ended)
