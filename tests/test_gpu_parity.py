@@ -127,6 +127,26 @@ def test_fp32_walks_follow_the_oracle_streams():
     assert np.array_equal(g["counts"].sum(1), g["steps"] - 1)
 
 
+@pytest.mark.parametrize("name", ["quarterspace", "triangle_raster", "eight_materials"])
+def test_fp32_cooperative_tail_gives_the_same_walks(name):
+    # A launch of a few walks runs them in the cooperative tail (the warp's
+    # lanes compute the step increments, each walk only moves); the same paths
+    # inside one launch of 2048 walks run in full warps for most of their
+    # steps.  Every record must be identical, truncation included.
+    model, (x0, z0) = MODELS[name]
+    ctx = sdd.sdd_create(model)
+    full = sdd.sdd_walk_records(ctx, x0, z0, 5, 0, 2048, 1e-3, 91, chunk_paths=2048)
+    for p0, cnt in ((0, 1), (7, 3), (100, 8), (2040, 8), (513, 5)):
+        part = sdd.sdd_walk_records(ctx, x0, z0, 5, p0, cnt, 1e-3, 91)
+        for k in ("steps", "counts", "exit", "wall", "m_last"):
+            assert np.array_equal(part[k], full[k][p0:p0 + cnt]), (name, p0, cnt, k)
+    full = sdd.sdd_walk_records(ctx, x0, z0, 5, 0, 512, 1e-3, 92, max_steps=40, chunk_paths=512)
+    part = sdd.sdd_walk_records(ctx, x0, z0, 5, 200, 3, 1e-3, 92, max_steps=40)
+    assert (full["wall"] < 0).sum() > 100 and (full["wall"] >= 0).any()
+    for k in ("steps", "counts", "exit", "wall", "m_last"):
+        assert np.array_equal(part[k], full[k][200:203]), (name, k)
+
+
 def test_empty_and_single_inputs():
     ctx = sdd.sdd_create(I.halfspace(2.0))
     mean, se, st = sdd.sdd_interface_values(ctx, np.zeros((0, 2)), np.zeros(0, dtype=np.int64), 1e-3, 0)
