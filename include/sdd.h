@@ -105,7 +105,7 @@ typedef struct {
     const sdd_shape *shapes; /* host, copied; may be NULL if n_shapes == 0 */
     int32_t n_shapes;        /* 0..SDD_MAX_SHAPES */
     const int8_t *raster;    /* host, [nz][nx] material ids, copied; or NULL */
-    int32_t nx, nz;
+    int32_t nx, nz;          /* raster size: each side 1..2^20 cells, nx * nz <= 2^31 */
     int32_t g_kind;
     int32_t g_left, g_right;
     double g_coef[6];
@@ -322,7 +322,7 @@ typedef struct sdd_server sdd_server;
 
 typedef struct {
     sdd_domain domain;        /* every request's domain */
-    int32_t nx, nz;           /* every request's raster size */
+    int32_t nx, nz;           /* every request's raster size (limits as in sdd_model_desc) */
     int32_t n_eval;           /* every request's number of evaluations */
     int32_t g_kind;           /* every request's boundary-data kind */
     int32_t max_requests;     /* admission slots: admitted and not yet collected, 1..4096 */

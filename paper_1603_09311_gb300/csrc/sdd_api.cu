@@ -22,7 +22,7 @@ using namespace sdd;
 
 void sdd::build_tiles(const int8_t *raster, int nx, int nz, std::vector<uint32_t> &coarse,
                       std::vector<uint8_t> &pool) {
-    const int ntx = (nx + kTile - 1) / kTile, ntz = (nz + kTile - 1) / kTile;
+    const int ntx = tile_cols(nx), ntz = tile_cols(nz);
     coarse.assign((size_t)ntx * ntz, 0u);
     pool.clear();
     uint8_t cells[kTile * kTile];
@@ -31,7 +31,8 @@ void sdd::build_tiles(const int8_t *raster, int nx, int nz, std::vector<uint32_t
             bool uniform = true;
             for (int a = 0; a < kTile; ++a)
                 for (int b = 0; b < kTile; ++b) {
-                    const int iz = std::min(tz * kTile + a, nz - 1), ix = std::min(tx * kTile + b, nx - 1);
+                    const int iz = std::min(std::max(tz * kTile + a - kTile, 0), nz - 1);
+                    const int ix = std::min(std::max(tx * kTile + b - kTile, 0), nx - 1);
                     cells[a * kTile + b] = (uint8_t)raster[(size_t)iz * nx + ix];
                     uniform = uniform && cells[a * kTile + b] == cells[0];
                 }
@@ -169,7 +170,8 @@ sdd_status check_model(const sdd_model_desc *m) {
             return fail(SDD_E_ARG, "kappa must be finite and >= 0");
     const int K = m->n_materials;
     if (m->raster) {
-        if (m->nx < 1 || m->nz < 1 || (long long)m->nx * m->nz > (1ll << 31))
+        if (m->nx < 1 || m->nz < 1 || m->nx > kMaxRasterSide || m->nz > kMaxRasterSide ||
+            (long long)m->nx * m->nz > (1ll << 31))
             return fail(SDD_E_ARG, "raster size out of range");
         const long long n = (long long)m->nx * m->nz;
         for (long long i = 0; i < n; ++i)
@@ -264,8 +266,8 @@ void build_model(const sdd_model_desc *m, ModelDev &M) {
         M.sz = (double)m->nz / (d.z_max - d.z_min);
         M.fsx = (float)M.sx;
         M.fsz = (float)M.sz;
-        M.fox = (float)(M.hw * M.sx - 0.5);
-        M.foz = (float)(M.hh * M.sz - 0.5);
+        M.fox = (float)(M.hw * M.sx - 0.5 + kTile);
+        M.foz = (float)(M.hh * M.sz - 0.5 + kTile);
     }
     M.g_kind = m->g_kind;
     for (int j = 0; j < 6; ++j) M.g_coef[j] = m->g_coef[j];
@@ -707,7 +709,7 @@ sdd_status sdd_create(const sdd_model_desc *model, sdd_ctx **out) {
         }
         c->M.tcoarse = (const uint32_t *)c->tiles.p;
         c->M.tpool = (const uint8_t *)c->tiles.p + cb;
-        c->M.ntx = (model->nx + kTile - 1) / kTile;
+        c->M.ntx = tile_cols(model->nx);
         c->M.tpool_off = (uint32_t)cb;
     }
     *out = c;
@@ -1706,7 +1708,8 @@ extern "C" sdd_status sdd_server_create(const sdd_server_config *cfg, sdd_server
     if (!out) return fail(SDD_E_ARG, "out is NULL");
     *out = nullptr;
     if (!cfg) return fail(SDD_E_ARG, "cfg is NULL");
-    if (cfg->nx < 1 || cfg->nz < 1 || (long long)cfg->nx * cfg->nz > (1ll << 31))
+    if (cfg->nx < 1 || cfg->nz < 1 || cfg->nx > kMaxRasterSide || cfg->nz > kMaxRasterSide ||
+        (long long)cfg->nx * cfg->nz > (1ll << 31))
         return fail(SDD_E_ARG, "raster size out of range");
     if (cfg->n_eval < 1 || cfg->n_eval > SDD_MAX_EVAL) return fail(SDD_E_ARG, "n_eval must be in 1..32");
     if (cfg->max_requests < 1 || cfg->max_requests > 4096) return fail(SDD_E_ARG, "max_requests must be in 1..4096");
@@ -1746,7 +1749,7 @@ extern "C" sdd_status sdd_server_create(const sdd_server_config *cfg, sdd_server
         return st;
     }
     srv->device = srv->tmpl->device;
-    const size_t ntx = (cfg->nx + kTile - 1) / kTile, ntz = (cfg->nz + kTile - 1) / kTile;
+    const size_t ntx = tile_cols(cfg->nx), ntz = tile_cols(cfg->nz);
     srv->coarse_bytes = (ntx * ntz * sizeof(uint32_t) + 255) / 256 * 256;
     srv->slot_bytes = srv->coarse_bytes + ntx * ntz * kTile * kTile;  // pool of every tile mixed at most
     cudaError_t e = srv->arena.ensure((size_t)cfg->max_requests * srv->slot_bytes);

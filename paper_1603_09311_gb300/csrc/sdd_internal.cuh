@@ -66,10 +66,17 @@ constexpr int kMaxBatchModels = 256;
 
 // Two-level form of an int8 raster, identical cell by cell: tiles of
 // kTile x kTile cells; coarse[tz][tx] = kTileUniform | material for a tile of
-// one material, else the index of the tile's kTile^2 cells in the pool.
+// one material, else the index of the tile's kTile^2 cells in the pool.  The
+// tiles start one tile before the raster and end at least one tile after it,
+// their cells outside the raster repeating its nearest edge cell, so a cell
+// index that rounding puts one past an edge needs no clamp.
 constexpr int kTileShift = 4;
 constexpr int kTile = 1 << kTileShift;
 constexpr uint32_t kTileUniform = 0x80000000u;
+__host__ __device__ constexpr int tile_cols(int n) { return n / kTile + 2; }
+// Raster side limit: cell indices are formed by FP32 magic-number rounding,
+// exact below 2^22.
+constexpr int kMaxRasterSide = 1 << 20;
 
 // Per-model data of a batched launch (device memory).
 struct BatchModel {
@@ -106,7 +113,8 @@ struct ModelDev {
     float fxc, fzc;  // centre
     float fzs;       // earth surface z = 0 in centred coordinates
     float fsx, fsz;  // raster cells per unit length
-    float fox, foz;  // hw * sx - 1/2, hh * sz - 1/2 (cell index = round(X sx + ox))
+    float fox, foz;  // hw * sx - 1/2 + kTile, hh * sz - 1/2 + kTile: round(X sx + ox) is the
+                     // cell index plus kTile (the tile map's margin)
 };
 
 struct WalkArgs {

@@ -128,13 +128,15 @@ struct WalkerF32 {
 
     __device__ __forceinline__ int material(const ModelDev &M, float X, float Z) const {
         if (GC == GC_RASTER || GC == GC_RASTER_MULTI) {
-            // round(v - 1/2) = floor(v) for v = (X + hw) sx >= 0 (magic-number rounding)
-            int ix = __float_as_int(fmaf(X, M.fsx, M.fox) + 12582912.0f) - 0x4B400000;
-            int iz = __float_as_int(fmaf(Z, M.fsz, M.foz) + 12582912.0f) - 0x4B400000;
-            ix = min(ix, M.nx - 1);
-            iz = min(iz, M.nz - 1);
-            // two-level lookup: the coarse entry (L1-resident) is the material of
-            // a uniform tile, else the tile's cells in the pool
+            // round(v - 1/2) = floor(v) for v = (X + hw) sx >= 0 (magic-number
+            // rounding), plus kTile: the index into the tile map, which starts
+            // one tile before the raster.  A point inside the domain gives a cell
+            // index in -1 .. n (rounding can reach one past an edge), and the
+            // map's margin tiles repeat the edge cells, so no clamp is needed.
+            // Two-level lookup: the coarse entry (L1-resident) is the material
+            // of a uniform tile, else the tile's cells in the pool.
+            const int ix = __float_as_int(fmaf(X, M.fsx, M.fox) + 12582912.0f) - 0x4B400000;
+            const int iz = __float_as_int(fmaf(Z, M.fsz, M.foz) + 12582912.0f) - 0x4B400000;
             const uint32_t *co = GC == GC_RASTER_MULTI ? tco : M.tcoarse;
             const uint32_t c = __ldg(co + (iz >> kTileShift) * M.ntx + (ix >> kTileShift));
             if (c & kTileUniform) return (int)(c & 0xffu);
@@ -197,12 +199,18 @@ struct WalkerF32 {
     // wall iff 2 d_w d'_w / dt <= -ln U for the smallest product, tested as
     // U <= exp(-2 d_w d'_w / dt).  U is made of the 18 bits of the step's two
     // Philox words that the normals leave unused:
-    // U = (high 9 bits of wa : high 9 bits of wb + 1/2) 2^-18.
+    // U = (high 9 bits of wa : high 9 bits of wb + 1/2) 2^-18.  Every
+    // product d_w d'_w is at least pn = dmin dn (the nearest distances before
+    // and after the step), so U > exp(-2 pn / dt) rules out a hit without
+    // forming the four products; most near-wall steps end there.
     __device__ __forceinline__ bool near_wall(const ModelDev &M, const WalkArgs &A, float Xn,
-                                              float Zn, float dn, uint32_t wa, uint32_t wb,
+                                              float Zn, float dn, float pn, uint32_t wa, uint32_t wb,
                                               ExitInfo<float> &ei) const {
         const float d[4] = {X + M.fhw, M.fhw - X, Z + M.fhh, M.fhh - Z};
         const float e[4] = {Xn + M.fhw, M.fhw - Xn, Zn + M.fhh, M.fhh - Zn};
+        const uint32_t u18 = ((wa >> 23) << 9) | (wb >> 23);
+        const float U = fmaf((float)u18, 3.814697265625e-06f, 1.9073486328125e-06f);
+        if (dn > 0.f && U > __expf(-pn * A.f_c2dt)) return false;
         if (dn <= 0.f) {
             float best = 2.0f;
             int bw = 0;
@@ -219,8 +227,6 @@ struct WalkerF32 {
         const float p0 = d[0] * e[0], p1 = d[1] * e[1], p2 = d[2] * e[2], p3 = d[3] * e[3];
         const float pmin = fminf(fminf(p0, p1), fminf(p2, p3));
         const float es = pmin * A.f_c2dt;
-        const uint32_t u18 = ((wa >> 23) << 9) | (wb >> 23);
-        const float U = fmaf((float)u18, 3.814697265625e-06f, 1.9073486328125e-06f);
         if (U > __expf(-es)) return false;
         // a hit: the wall of the smallest product (first in wall order) and
         // the fraction theta = (2 d d' / dt) / (-ln U)
@@ -253,8 +259,9 @@ struct WalkerF32 {
         const float Xn = fmaf(-d.r, d.cs, X);
         const float Zn = fmaf(-d.r, d.sn, Z);
         const float dn = fminf(M.fhw - fabsf(Xn), M.fhh - fabsf(Zn));
-        if (dmin * dn <= A.f_bthr) {
-            if (near_wall(M, A, Xn, Zn, dn, wa, wb, ei)) {
+        const float pn = dmin * dn;
+        if (pn <= A.f_bthr) {
+            if (near_wall(M, A, Xn, Zn, dn, pn, wa, wb, ei)) {
                 ei.nocc = n + k;
                 return true;
             }

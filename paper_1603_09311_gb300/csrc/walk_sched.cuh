@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(256, 3) walk_kernel(const __grid_constant__ Mo
 
     // Records of the walks that ended this iteration (st: 1 exited,
     // 2 truncated), then a batch of samples once 32 records are waiting.
-    ExitInfo<Real> ei;
+    ExitInfo<Real> ei{};
     auto on_exits = [&](int st) {
         const unsigned em = __ballot_sync(kFull, st != 0);
         const int nex = __popc(em);

@@ -88,6 +88,7 @@ def test_status_strings(L):
     (lambda m: m.update(kappa=np.zeros((33, 2))), "n_eval"),
     (lambda m: m.update(kappa=np.zeros((1, 9))), "n_materials"),
     (lambda m: m.update(raster=np.full((4, 4), 3, dtype=np.int8)), "raster"),
+    (lambda m: m.update(raster=np.zeros((1, (1 << 20) + 1), dtype=np.int8)), "raster size"),
 ])
 def test_bad_models_are_rejected_before_any_cuda_call(L, mutate, msg):
     m = I.halfspace(2.0)
