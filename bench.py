@@ -168,9 +168,9 @@ def serving(sdd, n_requests: int, seed: int = 5):
 
     def make_server():
         return sdd.Server(domain=I.DOMAIN, nx=I.RASTER_NX, nz=I.RASTER_NZ, dt=1e-3, seed=seed,
-                          max_requests=64, n_streams=4, max_batch_models=64)
+                          max_requests=64, n_streams=2, max_batch_models=64, max_batch_walks=1 << 25)
 
-    def open_loop(srv, arrivals):
+    def open_loop(srv, arrivals, reqs=reqs, kw=kw):
         t0 = time.perf_counter()
         pending, done_at, k = {}, {}, 0
         while len(done_at) < len(reqs):
@@ -188,6 +188,13 @@ def serving(sdd, n_requests: int, seed: int = 5):
         lat = np.array([done_at[i] - arrivals[i] for i in range(len(reqs))])
         return lat, max(done_at.values())
 
+    def fifo(arrivals, service):
+        free_at, out = 0.0, []
+        for a, s_ in zip(arrivals, service):
+            free_at = max(a, free_at) + s_
+            out.append(free_at - a)
+        return np.array(out)
+
     srv = make_server()
     # closed loop: every request at t = 0
     lat_c, span_c = open_loop(srv, np.zeros(len(reqs)))
@@ -201,20 +208,17 @@ def serving(sdd, n_requests: int, seed: int = 5):
     srv.close()
     steps = st1["steps"] - st0["steps"]
     # baseline: one request per launch, served in arrival order on the same arrivals
+    # (a request brings its model: its upload is part of the service, as it is
+    # part of a served request's latency)
     service = []
     for r in reqs:
-        ctx = sdd.sdd_create(r["model"])
         t = time.perf_counter()
+        ctx = sdd.sdd_create(r["model"])
         sdd.sdd_interface_values_target(ctx, r["nodes"], kw["n_pilot"], kw["n_max"], kw["target_se"],
                                         1e-3, seed, node_ids=r["node_ids"])
-        service.append(time.perf_counter() - t)
         ctx.close()
-    free_at, base_lat = 0.0, []
-    for a, s_ in zip(arr, service):
-        start = max(a, free_at)
-        free_at = start + s_
-        base_lat.append(free_at - a)
-    base_lat = np.array(base_lat)
+        service.append(time.perf_counter() - t)
+    base_lat = fifo(arr, service)
     # the plain form: one node per launch (pilot + top-up per node), on the
     # first requests only (it is far slower)
     n_plain = min(3, len(reqs))
@@ -230,6 +234,43 @@ def serving(sdd, n_requests: int, seed: int = 5):
         ctx.close()
     t_served = sum(service[:n_plain])
     total_nodes = sum(len(r["nodes"]) for r in reqs)
+
+    # small requests (16-64 nodes, fixed 2e4 walks per node), where one
+    # request alone cannot fill the GPU: closed-loop capacity of the server and
+    # of one request per launch, then both on the same Poisson arrivals at
+    # 0.7 x the capacity of one request per launch
+    rng_s = np.random.default_rng(seed + 7)
+    small = []
+    for i in range(48):
+        r = I.random_request(rng_s, 1000 + i)
+        r["nodes"] = r["nodes"][: int(rng_s.integers(16, 65))]
+        r["node_ids"] = np.arange(len(r["nodes"]), dtype=np.uint32) + np.uint32(4096 * r["id"])
+        small.append(r)
+    kw_s = dict(n_paths=20_000)
+    srv = make_server()
+    _, span_s = open_loop(srv, np.zeros(len(small)), small, kw_s)
+    service_s = []
+    for r in small:
+        t = time.perf_counter()
+        ctx = sdd.sdd_create(r["model"])
+        sdd.sdd_interface_values(ctx, r["nodes"], kw_s["n_paths"], 1e-3, seed, node_ids=r["node_ids"])
+        ctx.close()
+        service_s.append(time.perf_counter() - t)
+    cap_base_s = len(small) / sum(service_s)
+    arr_s = np.cumsum(np.random.default_rng(seed + 8).exponential(1.0 / (0.7 * cap_base_s), len(small)))
+    arr_s -= arr_s[0]
+    lat_s, _ = open_loop(srv, arr_s, small, kw_s)
+    srv.close()
+    base_s = fifo(arr_s, service_s)
+    small_out = {
+        "requests": len(small), "workload": "random raster requests, 16-64 nodes, 2e4 walks per node, dt 1e-3",
+        "arrivals": "Poisson at 0.7 x the capacity of one request per launch",
+        "capacity_req_per_s": len(small) / span_s,
+        "p50_ms": 1e3 * float(np.percentile(lat_s, 50)), "p99_ms": 1e3 * float(np.percentile(lat_s, 99)),
+        "baseline_one_request_per_launch": {
+            "capacity_req_per_s": cap_base_s,
+            "p50_ms": 1e3 * float(np.percentile(base_s, 50)),
+            "p99_ms": 1e3 * float(np.percentile(base_s, 99))}}
     return {"requests": len(reqs), "arrivals": "Poisson at 0.7 x closed-loop capacity",
             "capacity_req_per_s": cap, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
             "p99_ms": 1e3 * float(np.percentile(lat, 99)),
@@ -244,7 +285,9 @@ def serving(sdd, n_requests: int, seed: int = 5):
                 "node_solves_per_s": nodes_plain / t_plain,
                 "slowdown_vs_one_request_per_launch": t_plain / t_served},
             "workload": "random raster requests (1024x768 int8, 1-4 shapes), 16-1024 nodes, "
-                        "target SE 1e-3, pilot 4096, cap 1e6, dt 1e-3"}
+                        "target SE 1e-3, pilot 4096, cap 1e6, dt 1e-3",
+            "server": "2 streams, up to 2^25 walks and 64 models per launch",
+            "small_requests": small_out}
 
 
 def run_reference(args):

@@ -28,14 +28,23 @@ void sdd::build_tiles(const int8_t *raster, int nx, int nz, std::vector<uint32_t
     uint8_t cells[kTile * kTile];
     for (int tz = 0; tz < ntz; ++tz)
         for (int tx = 0; tx < ntx; ++tx) {
+            const int z0 = tz * kTile - kTile, x0 = tx * kTile - kTile;
+            if (z0 >= 0 && z0 + kTile <= nz && x0 >= 0 && x0 + kTile <= nx) {
+                for (int a = 0; a < kTile; ++a)
+                    std::memcpy(cells + a * kTile, raster + (size_t)(z0 + a) * nx + x0, kTile);
+            } else {  // a tile over the raster's edge: cells outside repeat the nearest edge cell
+                for (int a = 0; a < kTile; ++a)
+                    for (int b = 0; b < kTile; ++b) {
+                        const int iz = std::min(std::max(z0 + a, 0), nz - 1);
+                        const int ix = std::min(std::max(x0 + b, 0), nx - 1);
+                        cells[a * kTile + b] = (uint8_t)raster[(size_t)iz * nx + ix];
+                    }
+            }
+            uint64_t w[kTile * kTile / 8];
+            std::memcpy(w, cells, sizeof(w));
+            const uint64_t rep = 0x0101010101010101ull * cells[0];
             bool uniform = true;
-            for (int a = 0; a < kTile; ++a)
-                for (int b = 0; b < kTile; ++b) {
-                    const int iz = std::min(std::max(tz * kTile + a - kTile, 0), nz - 1);
-                    const int ix = std::min(std::max(tx * kTile + b - kTile, 0), nx - 1);
-                    cells[a * kTile + b] = (uint8_t)raster[(size_t)iz * nx + ix];
-                    uniform = uniform && cells[a * kTile + b] == cells[0];
-                }
+            for (int k = 0; k < kTile * kTile / 8; ++k) uniform = uniform && w[k] == rep;
             if (uniform) {
                 coarse[(size_t)tz * ntx + tx] = kTileUniform | cells[0];
             } else {
@@ -1423,10 +1432,16 @@ int64_t request_bytes(const sdd_server *srv, int32_t n_nodes) {
 }
 
 // Cut a request's current phase into pieces of at most batch_walks walks
-// (whole nodes; nodes with no walks left out) and queue them.
+// (whole nodes; nodes with no walks left out) and queue them in submission
+// order of their requests: a top-up phase goes ahead of the pilot phases of
+// requests submitted after it, so launches serve the oldest request first and
+// fill up with younger ones.
 void srv_queue_phase(sdd_server *srv, SrvRequest *r) {
     const int32_t n = (int32_t)r->ids.size();
     int pieces = 0;
+    auto at = std::upper_bound(srv->runnable.begin(), srv->runnable.end(), r->id,
+                               [](uint64_t id, const SrvPiece &pc) { return id < pc.r->id; });
+    std::vector<SrvPiece> add;
     int32_t a = 0;
     while (a < n) {
         while (a < n && r->count[a] == 0) ++a;
@@ -1438,10 +1453,11 @@ void srv_queue_phase(sdd_server *srv, SrvRequest *r) {
             ++b;
             while (b < n && r->count[b] == 0) ++b;
         }
-        srv->runnable.push_back({r, a, b, w});
+        add.push_back({r, a, b, w});
         ++pieces;
         a = b;
     }
+    srv->runnable.insert(at, add.begin(), add.end());
     r->pieces_left = pieces;
 }
 
