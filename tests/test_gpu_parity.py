@@ -234,6 +234,76 @@ def test_full_size_quarterspace_sampled_nodes():
     assert np.all(np.isfinite(mean)) and np.all(se > 0)
 
 
+def _fp32_close(mean, se, ref_mean, ref_se):
+    tol = FP32_NSE * np.sqrt(se ** 2 + ref_se ** 2) + FP32_ABS
+    d = mean - ref_mean
+    return bool(np.all(np.abs(d.real) <= tol[..., 0]) and np.all(np.abs(d.imag) <= tol[..., 1]))
+
+
+def test_full_size_halfspace_every_node():
+    # the half-space workload in full (16 nodes x 1e4 paths, dt 1e-3), every
+    # node recomputed by the oracle, in both precisions
+    w = I.workload("halfspace")
+    ctx = sdd.sdd_create(w["model"])
+    m32, s32, st = sdd.sdd_interface_values(ctx, w["nodes"], w["n_paths"], w["dt"], w["seed"])
+    r32 = O.interface_values(w["model"], w["nodes"], w["n_paths"], w["dt"], w["seed"], urule=23)
+    assert st["walks"] == 160_000 and _fp32_close(m32, s32, r32["mean"], r32["se"])
+    m64, _, _ = sdd.sdd_interface_values(ctx, w["nodes"], w["n_paths"], w["dt"], w["seed"], precision="fp64")
+    r64 = O.interface_values(w["model"], w["nodes"], w["n_paths"], w["dt"], w["seed"], urule=32)
+    tol = FP64_REL * _gmax(w["model"])
+    assert np.allclose(m64.real, r64["mean"].real, rtol=0, atol=tol)
+    assert np.allclose(m64.imag, r64["mean"].imag, rtol=0, atol=tol)
+
+
+def test_full_size_block_sampled_nodes():
+    # the batched block workload in full (256 nodes, 1e4..1e6 paths, 16
+    # evaluations per walk, dt 1e-4); the three nodes with the fewest paths are
+    # recomputed by the oracle under their own node ids
+    w = I.workload("block")
+    ctx = sdd.sdd_create(w["model"])
+    mean, se, st = sdd.sdd_interface_values(ctx, w["nodes"], w["n_paths"], w["dt"], w["seed"])
+    assert st["walks"] == w["n_paths"].sum() and st["truncated"] == 0 and mean.shape == (256, 16)
+    for j in np.argsort(w["n_paths"])[:3]:
+        r = O.interface_values(w["model"], w["nodes"][j:j + 1], w["n_paths"][j:j + 1], w["dt"],
+                               w["seed"], urule=23, node_id0=int(j))
+        assert _fp32_close(mean[j], se[j], r["mean"][0], r["se"][0]), j
+    assert np.all(np.isfinite(mean)) and np.all(se > 0)
+
+
+@pytest.mark.parametrize("dt", [1e-3, 3e-4, 1e-4, 3e-5])
+def test_triangle_dt_sweep_both_precisions(dt):
+    # the triangle workload's time-step sweep on four of its nodes: the FP64
+    # walk equals the oracle's to 1e-10, the FP32 walk is within 4 combined SE
+    w = I.workload("triangle")
+    nodes = w["nodes"][[0, 40, 85, 127]]
+    n_paths = np.full(4, 3000, dtype=np.int64)
+    ctx = sdd.sdd_create(w["model"])
+    m64, _, st64 = sdd.sdd_interface_values(ctx, nodes, n_paths, dt, w["seed"], precision="fp64")
+    r64 = O.interface_values(w["model"], nodes, n_paths, dt, w["seed"], urule=32)
+    tol = FP64_REL * _gmax(w["model"])
+    assert np.allclose(m64.real, r64["mean"].real, rtol=0, atol=tol)
+    assert np.allclose(m64.imag, r64["mean"].imag, rtol=0, atol=tol)
+    assert st64["steps"] == r64["steps"]
+    m32, s32, _ = sdd.sdd_interface_values(ctx, nodes, n_paths, dt, w["seed"])
+    r32 = O.interface_values(w["model"], nodes, n_paths, dt, w["seed"], urule=23)
+    assert _fp32_close(m32, s32, r32["mean"], r32["se"])
+
+
+def test_full_size_triangle_sampled_node():
+    # the triangle workload at its full path count (128 nodes x 1e6 paths) at
+    # the sweep's largest step, dt 1e-3; one node recomputed by the oracle
+    w = I.workload("triangle")
+    dt = 1e-3
+    ctx = sdd.sdd_create(w["model"])
+    mean, se, st = sdd.sdd_interface_values(ctx, w["nodes"], w["n_paths"], dt, w["seed"])
+    assert st["walks"] == 128_000_000 and st["truncated"] == 0
+    j = 70
+    r = O.interface_values(w["model"], w["nodes"][j:j + 1], w["n_paths"][j:j + 1], dt, w["seed"],
+                           urule=23, node_id0=j)
+    assert _fp32_close(mean[j], se[j], r["mean"][0], r["se"][0])
+    assert np.all(np.isfinite(mean)) and np.all(se > 0)
+
+
 def test_target_se_equals_fixed_counts_and_meets_target():
     # adaptive path counts: pilot, then top-up to N = var / se^2; the result
     # must be the fixed-count evaluation with n_paths = N (same walks), and
