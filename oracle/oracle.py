@@ -14,7 +14,11 @@ A model is described by a plain dict (see ``sdd_inputs.py``):
              kind 1 closed triangle (v0,v1),(v2,v3),(v4,v5)
     raster   optional int8 [nz][nx] material map (replaces bg and shapes)
     g        ("columns", left_material, right_material) | ("affine", a, b, c)
-             | ("x2mz2",)
+             | ("x2mz2",) | ("tm_cosh",) | ("tm_flux",)
+TM mode (a diffusion coefficient that jumps across vertical interfaces):
+    diffusion  [K] diffusion coefficient of strip m (material m)
+    interfaces [K-1] increasing strip boundaries x; strip m = [x_{m-1}, x_m)
+    (bg, shapes and raster are then unused: the material is the strip)
 """
 from __future__ import annotations
 
@@ -61,6 +65,9 @@ class _Model(ctypes.Structure):
         ("g_coef", ctypes.POINTER(ctypes.c_double)),
         ("urule", ctypes.c_int),
         ("max_steps", ctypes.c_int64),
+        ("tm", ctypes.c_int),
+        ("diff", ctypes.POINTER(ctypes.c_double)),
+        ("xif", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -100,7 +107,10 @@ def lib():
             P(_Model), ctypes.c_double, ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32,
             ctypes.c_int, ctypes.c_double, ctypes.c_uint64, ctypes.c_int, P(ctypes.c_int64),
             P(ctypes.c_int64), P(ctypes.c_double), P(ctypes.c_int), P(ctypes.c_int),
-            P(ctypes.c_int)]
+            P(ctypes.c_int), P(ctypes.c_double), P(ctypes.c_int64)]
+        L.orc_tm_uniforms.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                      ctypes.c_int64, ctypes.c_int, P(ctypes.c_double)]
+        L.orc_tm_uniforms.restype = None
         L.orc_walk_records.restype = None
         L.orc_max_threads.argtypes = []
         L.orc_max_threads.restype = ctypes.c_int
@@ -140,6 +150,10 @@ class OracleModel:
             coef[:] = [a.real, a.imag, b.real, b.imag, c.real, c.imag]
         elif g[0] == "x2mz2":
             g_kind, gl, gr = 2, 0, 0
+        elif g[0] == "tm_cosh":
+            g_kind, gl, gr = 3, 0, 0
+        elif g[0] == "tm_flux":
+            g_kind, gl, gr = 4, 0, 0
         else:
             raise ValueError(f"unknown g kind {g[0]}")
         self.g_coef = coef
@@ -158,6 +172,16 @@ class OracleModel:
             0 if self.raster is None else self.raster.shape[1],
             0 if self.raster is None else self.raster.shape[0],
             g_kind, gl, gr, _ptr(self.g_coef, ctypes.c_double), int(urule), int(max_steps))
+        self.diff = np.ascontiguousarray(np.asarray(model.get("diffusion", [1.0] * K), dtype=np.float64))
+        self.xif = np.ascontiguousarray(np.asarray(list(model.get("interfaces", [])) + [0.0], dtype=np.float64))
+        if "diffusion" in model:
+            if self.diff.shape != (K,) or len(model.get("interfaces", [])) != K - 1:
+                raise ValueError("TM mode needs K diffusion coefficients and K-1 interfaces")
+            self.s.tm = 1
+        elif g_kind in (3, 4):
+            raise ValueError("tm_cosh and tm_flux boundary data need TM mode")
+        self.s.diff = _ptr(self.diff, ctypes.c_double)
+        self.s.xif = _ptr(self.xif, ctypes.c_double)
         self.E, self.K = E, K
 
 
@@ -182,6 +206,12 @@ def normals(seed: int, node: int, path: int, n: int, urule: int = 32):
 
 def bridge_uniform(seed: int, node: int, path: int, n: int, urule: int = 32) -> float:
     return lib().orc_bridge_uniform(seed, node, path, n, urule)
+
+
+def tm_uniforms(seed: int, node: int, path: int, n: int, urule: int = 32):
+    out = np.zeros(4)
+    lib().orc_tm_uniforms(seed, node, path, n, urule, _ptr(out, ctypes.c_double))
+    return out
 
 
 def material(model: dict, x: float, z: float) -> int:
@@ -232,7 +262,9 @@ def interface_values(model: dict, nodes, n_paths, dt: float, seed: int, urule: i
 
 def walk_records(model: dict, node_xz, node_id: int, p0: int, count: int, dt: float, seed: int,
                  urule: int = 32, max_steps: int | None = None, threads: int = 0):
-    """Per-path records: steps, counts [count][K], exit (x, z, theta), wall, m_last, truncated."""
+    """Per-path records: steps, counts [count][K], exit (x, z, theta), wall, m_last, truncated,
+    occ [count][K] (occupation time per material in units of dt; TE: the counts), hits
+    (TM interface randomisations)."""
     om = OracleModel(model, urule=urule, max_steps=max_steps, dt=dt)
     steps = np.zeros(count, dtype=np.int64)
     counts = np.zeros((count, om.K), dtype=np.int64)
@@ -240,13 +272,16 @@ def walk_records(model: dict, node_xz, node_id: int, p0: int, count: int, dt: fl
     wall = np.zeros(count, dtype=np.int32)
     mlast = np.zeros(count, dtype=np.int32)
     trunc = np.zeros(count, dtype=np.int32)
+    occ = np.zeros((count, om.K))
+    hits = np.zeros(count, dtype=np.int64)
     lib().orc_walk_records(ctypes.byref(om.s), float(node_xz[0]), float(node_xz[1]), node_id, p0,
                            count, dt, seed, threads, _ptr(steps, ctypes.c_int64),
                            _ptr(counts, ctypes.c_int64), _ptr(ext, ctypes.c_double),
                            _ptr(wall, ctypes.c_int), _ptr(mlast, ctypes.c_int),
-                           _ptr(trunc, ctypes.c_int))
+                           _ptr(trunc, ctypes.c_int), _ptr(occ, ctypes.c_double),
+                           _ptr(hits, ctypes.c_int64))
     return {"steps": steps, "counts": counts, "exit": ext, "wall": wall, "m_last": mlast,
-            "truncated": trunc}
+            "truncated": trunc, "occ": occ, "hits": hits}
 
 
 def max_threads() -> int:

@@ -45,6 +45,41 @@
  * bridge uniform from the remaining 18 bits, ((a>>23) 2^9 + (b>>23) + 1/2) 2^-18.
  * The paper fixes no random-number mapping; these are the library's.
  *
+ * TM mode (diffusion coefficient that jumps; Sec. 2.2, Eq. for the Helmholtz
+ * equation per sub-domain (1/2) kappa_i Lap u - lambda_i u = 0 with flux
+ * continuity, and the interface rules of Sec. 3.1).  The sub-domains are
+ * vertical strips (the paper treats one vertical interface "without loss of
+ * generality"): strip m = [xif[m-1], xif[m]) has diffusion D_m and rates
+ * kappa_{e,m}, i.e. D_m Lap u = i kappa_{e,m} u, and the walk weight keeps
+ * the form exp(-i (1/2) sum_m kappa_{e,m} T_m).  Per step, in strip i:
+ *   1. beta' = beta + sqrt(D_i dt) W (the discretised-process equation).
+ *   2. dOmega first: overshoot as in TE; bridge with kappa_i = D_i,
+ *      2 d d' / (D_i dt) <= -ln U.
+ *   3. Interfaces to a strip of other D only (equal D: no regime change).
+ *      Crossed: hitting fraction |d / (beta'_x - beta_x)| (second case of the
+ *      first-hitting-time equation).  Not crossed: the nearer interface of
+ *      strip i (smallest 2 d d' / (D_i dt)) against -ln U_g, U_g a separate
+ *      uniform (first case).  A hit at fraction th resumes on side i with
+ *      probability p_i = D_i / (D_i + D_j) (crossing-probability equation),
+ *      uniformly in the disc of radius h = sqrt(dt max(D_i, D_j)) centred at
+ *      (x_g -/+ h, z_g), z_g the hit height, tangent to the interface.
+ *      Occupation: side i gets T_i += dt - (1/2)(dt - t_g) p_i,
+ *      T_j += (1/2)(dt - t_g) p_i; side j gets T_i += t_g + (1/2)(dt - t_g) p_j
+ *      and T_j the rest of dt (the printed T_j of that branch does not sum to
+ *      dt with T_i; the reading keeps T_i and conserves dt).  A resampled
+ *      point outside Omega ends the walk on the nearest wall (theta = 0).
+ *   4. Otherwise dt goes to the strip of beta'.
+ * A walk that starts on an interface between strips of different D has hit
+ * it at time 0: its first step is the randomisation of 3 with t_g = 0, from
+ * the strip on the left.
+ * Pins (tests/test_oracle_pins.py): the flux-continuous solution int dx/D
+ * (kappa = 0), the analytic test model, finite volumes with phase and flux,
+ * equal D = the TE walk.  Parity unpinned: the occupation split of step 3
+ * moves O(dt) per hit, below the resolution of every pin; it is checked only
+ * by conservation of time and by path-by-path GPU equality.
+ * The TM uniforms (U_g, U_alpha, disc radius, disc angle) are the four
+ * words of the Philox call with counter (n, r, node, 2), by the urule.
+ *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -shared -fPIC.
  */
 #include <complex.h>
@@ -76,6 +111,9 @@ typedef struct {
     const double *g_coef;            /* g_kind 1: a_re a_im b_re b_im c_re c_im */
     int urule;                       /* 32 or 23 */
     int64_t max_steps;
+    int tm;                          /* 0 = TE; 1 = TM strips */
+    const double *diff;              /* TM: [K] diffusion coefficient of strip m */
+    const double *xif;               /* TM: [K-1] increasing strip boundaries */
 } orc_model;
 
 typedef struct {
@@ -86,6 +124,8 @@ typedef struct {
     int m_last;          /* material of beta^n (gets theta*dt) */
     int truncated;
     int64_t count[ORC_MAX_K];
+    double occ[ORC_MAX_K];   /* TM: occupation time per strip in units of dt */
+    int64_t hits;            /* TM: interface randomisations */
 } orc_walk_rec;
 
 /* ---------------------------------------------------------------- Philox */
@@ -173,7 +213,27 @@ double orc_bridge_uniform(uint64_t seed, uint32_t node, uint32_t path, int64_t n
     return orc_uniform(x[0], urule);
 }
 
+/* The four TM uniforms of step n: U_g (interface bridge), U_alpha (side),
+ * disc radius, disc angle, from the Philox call with counter (n, path, node, 2). */
+void orc_tm_uniforms(uint64_t seed, uint32_t node, uint32_t path, int64_t n, int urule,
+                     double U[4])
+{
+    uint32_t key[2], ctr[4], x[4];
+    seed_key(seed, key);
+    ctr[0] = (uint32_t)n; ctr[1] = path; ctr[2] = node; ctr[3] = 2;
+    orc_philox4x32_10(ctr, key, x);
+    for (int k = 0; k < 4; ++k) U[k] = orc_uniform(x[k], urule);
+}
+
 /* ------------------------------------------------------------- materials */
+
+/* TM: the strip of abscissa x. */
+int orc_strip(const orc_model *m, double x)
+{
+    int k = 0;
+    while (k < m->K - 1 && x >= m->xif[k]) ++k;
+    return k;
+}
 
 static int in_shape(int kind, const double *v, double x, double z)
 {
@@ -191,6 +251,7 @@ static int in_shape(int kind, const double *v, double x, double z)
 
 int orc_material(const orc_model *m, double x, double z)
 {
+    if (m->tm) return orc_strip(m, x);
     if (m->raster) {
         double fx = floor((x - m->xmin) * ((double)m->nx / (m->xmax - m->xmin)));
         double fz = floor((z - m->zmin) * ((double)m->nz / (m->zmax - m->zmin)));
@@ -230,6 +291,26 @@ double complex orc_g_value(const orc_model *m, int e, int wall, double x, double
     }
     if (m->g_kind == 2)
         return x * x - z * z;
+    if (m->g_kind == 3) {
+        /* TM analytic test (Sec. 4.1, closed form read as (z + 1) cosh(a x)
+         * with D a^2 = i kappa per strip): solves D Lap u = i kappa u in each
+         * strip, continuous with zero flux at an interface at x = 0 */
+        int st = orc_strip(m, x);
+        double complex a = csqrt(I * m->kappa[e * m->K + st] / m->diff[st]);
+        return (z + 1.0) * ccosh(a * x);
+    }
+    if (m->g_kind == 4) {
+        /* TM, kappa = 0: u(x) = int_{xmin}^x ds / D(s), continuous with the
+         * same flux D u' = 1 in every strip */
+        double u = 0.0, a = m->xmin;
+        for (int k = 0; k < m->K; ++k) {
+            double b = (k < m->K - 1) ? m->xif[k] : m->xmax;
+            if (x <= b) return u + (x - a) / m->diff[k];
+            u += (b - a) / m->diff[k];
+            a = b;
+        }
+        return u;
+    }
     double kl = m->kappa[e * m->K + m->g_left];
     double kr = m->kappa[e * m->K + m->g_right];
     if (wall == 0)
@@ -356,13 +437,156 @@ void orc_walk(const orc_model *m, double x0, double z0, uint32_t node, uint32_t 
     }
 }
 
+/* One TM walk (the steps listed in the header). */
+void orc_walk_tm(const orc_model *m, double x0, double z0, uint32_t node, uint32_t path,
+                 double dt, uint64_t seed, orc_walk_rec *rec)
+{
+    double x = x0, z = z0;
+    int i = orc_strip(m, x);
+    int64_t n = 0;
+    memset(rec, 0, sizeof(*rec));
+    for (;;) {
+        if (n >= m->max_steps) {
+            rec->steps = n;
+            rec->truncated = 1;
+            rec->wall = -1;
+            rec->ex = x;
+            rec->ez = z;
+            rec->m_last = i;
+            return;
+        }
+        double w0, w1;
+        orc_normals(seed, node, path, n, m->urule, &w0, &w1);
+        double Di = m->diff[i];
+        double s = sqrt(Di * dt);
+        double xn = x + s * w0;
+        double zn = z + s * w1;
+        double U = orc_bridge_uniform(seed, node, path, n, m->urule);
+        double theta, ex, ez;
+        int wall;
+        double th = 2.0, xg = 0.0;
+        int side = -1;
+        double V[4];
+        orc_tm_uniforms(seed, node, path, n, m->urule, V);
+        int j = i;
+        if (n == 0 && i > 0 && x == m->xif[i - 1] && m->diff[i - 1] != Di) {
+            /* started on an interface: a hit at t_g = 0 from the left strip */
+            i = i - 1;
+            Di = m->diff[i];
+            xn = x;
+            zn = z;
+            th = 0.0;
+            side = i + 1;
+            xg = x;
+        } else {
+            /* 2. the outer boundary first, with the strip's diffusion */
+            if (orc_exit_rule(m, x, z, xn, zn, Di * dt, U, &theta, &wall, &ex, &ez)) {
+                rec->steps = n + 1;
+                rec->ex = ex;
+                rec->ez = ez;
+                rec->theta = theta;
+                rec->wall = wall;
+                rec->m_last = i;
+                return;
+            }
+            /* 3. the interfaces of strip i */
+            j = orc_strip(m, xn);
+            if (j != i) {
+                int jn = (j > i) ? i + 1 : i - 1;
+                double xi = (j > i) ? m->xif[i] : m->xif[i - 1];
+                if (m->diff[jn] != Di) {
+                    th = fabs((x - xi) / (xn - x));
+                    side = jn;
+                    xg = xi;
+                }
+            } else {
+                double best = INFINITY, bx = 0.0;
+                int bs = -1;
+                if (i > 0 && m->diff[i - 1] != Di) {
+                    double e = 2.0 * (x - m->xif[i - 1]) * (xn - m->xif[i - 1]) / (Di * dt);
+                    if (e < best) { best = e; bs = i - 1; bx = m->xif[i - 1]; }
+                }
+                if (i < m->K - 1 && m->diff[i + 1] != Di) {
+                    double e = 2.0 * (m->xif[i] - x) * (m->xif[i] - xn) / (Di * dt);
+                    if (e < best) { best = e; bs = i + 1; bx = m->xif[i]; }
+                }
+                double L = -log(V[0]);
+                if (bs >= 0 && best <= L) {
+                    th = best / L;
+                    side = bs;
+                    xg = bx;
+                }
+            }
+        }
+        if (side >= 0) {
+            /* randomise the side (crossing probability), resample in the disc,
+             * split the step's time */
+            double Dj = m->diff[side];
+            double pi_ = Di / (Di + Dj), pj = Dj / (Di + Dj);
+            double zg = z + th * (zn - z);
+            double h = sqrt(dt * (Di > Dj ? Di : Dj));
+            double c = (x <= xg) ? h : -h;
+            double rest = 1.0 - th, cx;
+            if (V[1] < pi_) {
+                rec->occ[i] += 1.0 - 0.5 * rest * pi_;
+                rec->occ[side] += 0.5 * rest * pi_;
+                cx = xg - c;
+            } else {
+                double ti = th + 0.5 * rest * pj;
+                rec->occ[i] += ti;
+                rec->occ[side] += 1.0 - ti;
+                cx = xg + c;
+            }
+            double rho = h * sqrt(V[2]);
+            double ang = 6.283185307179586 * V[3];
+            xn = cx + rho * cos(ang);
+            zn = zg + rho * sin(ang);
+            rec->hits += 1;
+            double dn[4];
+            wall_dist(m, xn, zn, dn);
+            int bw = -1;
+            double most = 0.0;
+            for (int w = 0; w < 4; ++w)
+                if (dn[w] <= most && (bw < 0 || dn[w] < most)) { most = dn[w]; bw = w; }
+            if (bw >= 0) {
+                /* the resampled point left Omega: end on the nearest wall */
+                ex = xn < m->xmin ? m->xmin : (xn > m->xmax ? m->xmax : xn);
+                ez = zn < m->zmin ? m->zmin : (zn > m->zmax ? m->zmax : zn);
+                if (bw == 0) ex = m->xmin;
+                if (bw == 1) ex = m->xmax;
+                if (bw == 2) ez = m->zmin;
+                if (bw == 3) ez = m->zmax;
+                rec->steps = n + 1;
+                rec->ex = ex;
+                rec->ez = ez;
+                rec->theta = 0.0;
+                rec->wall = bw;
+                rec->m_last = i;
+                return;
+            }
+            x = xn;
+            z = zn;
+            i = orc_strip(m, x);
+            n += 1;
+            continue;
+        }
+        /* 4. the step's time goes to the strip of beta' */
+        rec->count[j] += 1;
+        rec->occ[j] += 1.0;
+        x = xn;
+        z = zn;
+        i = j;
+        n += 1;
+    }
+}
+
 /* Sample of one finished walk for evaluation e (Monte Carlo estimator of
  * Sec. 3.1): g(exit) * exp(-i (1/2) sum_m kappa_{e,m} T_m). */
 double complex orc_sample(const orc_model *m, int e, const orc_walk_rec *rec, double dt)
 {
     double phase = 0.0;
     for (int k = 0; k < m->K; ++k)
-        phase += m->kappa[e * m->K + k] * ((double)rec->count[k] * dt);
+        phase += m->kappa[e * m->K + k] * ((m->tm ? rec->occ[k] : (double)rec->count[k]) * dt);
     phase += m->kappa[e * m->K + rec->m_last] * (rec->theta * dt);
     phase *= 0.5;
     double complex wgt = cexp(-I * phase);
@@ -413,8 +637,8 @@ int64_t orc_interface_values(const orc_model *m, const double *nodes_xz, int n_n
         orc_partial *P = &part[b];
         for (int64_t p = p0; p < p1; ++p) {
             orc_walk_rec rec;
-            orc_walk(m, nodes_xz[2 * j], nodes_xz[2 * j + 1], node_id0 + (uint32_t)j,
-                     (uint32_t)p, dt, seed, &rec);
+            (m->tm ? orc_walk_tm : orc_walk)(m, nodes_xz[2 * j], nodes_xz[2 * j + 1],
+                                             node_id0 + (uint32_t)j, (uint32_t)p, dt, seed, &rec);
             P->steps += rec.steps;
             P->walks += 1;
             if (rec.truncated) {
@@ -484,7 +708,8 @@ int64_t orc_interface_values(const orc_model *m, const double *nodes_xz, int n_n
 void orc_walk_records(const orc_model *m, double x0, double z0, uint32_t node, uint32_t p0,
                       int count, double dt, uint64_t seed, int n_threads, int64_t *steps,
                       int64_t *counts /* [count][K] */, double *exit_xzt /* [count][3] */,
-                      int *wall, int *m_last, int *truncated)
+                      int *wall, int *m_last, int *truncated, double *occ /* [count][K] */,
+                      int64_t *hits)
 {
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
@@ -492,8 +717,11 @@ void orc_walk_records(const orc_model *m, double x0, double z0, uint32_t node, u
 #pragma omp parallel for schedule(dynamic, 64)
     for (int i = 0; i < count; ++i) {
         orc_walk_rec rec;
-        orc_walk(m, x0, z0, node, p0 + (uint32_t)i, dt, seed, &rec);
+        (m->tm ? orc_walk_tm : orc_walk)(m, x0, z0, node, p0 + (uint32_t)i, dt, seed, &rec);
         steps[i] = rec.steps;
+        for (int k = 0; k < m->K; ++k)
+            occ[(int64_t)i * m->K + k] = m->tm ? rec.occ[k] : (double)rec.count[k];
+        hits[i] = rec.hits;
         for (int k = 0; k < m->K; ++k) counts[(int64_t)i * m->K + k] = rec.count[k];
         exit_xzt[3 * i + 0] = rec.ex;
         exit_xzt[3 * i + 1] = rec.ez;

@@ -125,3 +125,79 @@ def fd_richardson(kappa_fn, domain, kl, kr, pts, h=1 / 40):
     b = fd_value(kappa_fn, domain, h / 2, kl, kr, pts)
     ext = (4 * b - a) / 3
     return ext, np.abs(b - a) / 3
+
+
+def u_flux(x, diffusion, interfaces, xmin):
+    """int_{xmin}^x ds / D(s) for strips with diffusion D_m between the given
+    interfaces: continuous, with the same flux D u' = 1 in every strip."""
+    x = np.asarray(x, dtype=float)
+    bounds = [xmin] + list(interfaces) + [np.inf]
+    u = np.zeros_like(x)
+    for k, D in enumerate(diffusion):
+        lo, hi = bounds[k], bounds[k + 1]
+        u += (np.clip(x, lo, hi) - lo) / D
+    return u
+
+
+def fd_solve_tm(domain, h, diffusion, interfaces, kappa, g_fn):
+    """Finite volumes for div(D grad u) - i kappa u = 0 on a uniform grid of
+    spacing h, D and kappa constant on vertical strips whose interfaces lie on
+    grid columns.  x-faces take the D of the strip they lie in; a node on an
+    interface takes the mean of its two strips for D on its z-faces and for
+    kappa (its control volume is half in each).  Dirichlet data g_fn(X, Z).
+    Returns (xs, zs, U)."""
+    xmin, xmax, zmin, zmax = domain
+    nx = int(round((xmax - xmin) / h))
+    nz = int(round((zmax - zmin) / h))
+    xs = xmin + h * np.arange(nx + 1)
+    zs = zmin + h * np.arange(nz + 1)
+    bounds = np.asarray(interfaces, dtype=float)
+
+    def strip(x):
+        return np.searchsorted(bounds, x, side="right")
+
+    D = np.asarray(diffusion, dtype=float)
+    kap = np.asarray(kappa, dtype=float)
+    on_if = np.isclose(xs[:, None], bounds[None, :], atol=1e-9 * h).any(axis=1) if len(bounds) else np.zeros(nx + 1, bool)
+    s_node = strip(xs)
+    s_left = strip(xs - 0.5 * h)
+    d_node = np.where(on_if, 0.5 * (D[s_left] + D[s_node]), D[s_node])
+    k_node = np.where(on_if, 0.5 * (kap[s_left] + kap[s_node]), kap[s_node])
+    d_xface = D[strip(xs[:-1] + 0.5 * h)]  # face between nodes i and i+1
+    X, Z = np.meshgrid(xs, zs)
+    U = np.zeros((nz + 1, nx + 1), dtype=np.complex128)
+    U[:, 0], U[:, -1] = g_fn(X[:, 0], Z[:, 0]), g_fn(X[:, -1], Z[:, -1])
+    U[0, :], U[-1, :] = g_fn(X[0, :], Z[0, :]), g_fn(X[-1, :], Z[-1, :])
+    ni, nk = nx - 1, nz - 1
+    idx = np.arange(ni * nk).reshape(nk, ni)
+    KZ, KX = np.meshgrid(np.arange(nk), np.arange(ni), indexing="ij")
+    ix = KX + 1  # full-grid column of each unknown
+    inv = 1.0 / h ** 2
+    cw, ce = d_xface[ix - 1] * inv, d_xface[ix] * inv
+    cz = d_node[ix] * inv
+    diag = -(cw + ce + 2.0 * cz) - 1j * k_node[ix]
+    rows, cols, vals = [idx.ravel()], [idx.ravel()], [diag.ravel()]
+    rhs = np.zeros(ni * nk, dtype=np.complex128)
+    for dz, dx, c in ((-1, 0, cz), (1, 0, cz), (0, -1, cw), (0, 1, ce)):
+        JZ, JX = KZ + dz, KX + dx
+        inside = (JZ >= 0) & (JZ < nk) & (JX >= 0) & (JX < ni)
+        rows.append(idx[inside])
+        cols.append(idx[JZ[inside], JX[inside]])
+        vals.append(c[inside].astype(np.complex128))
+        out = ~inside
+        np.subtract.at(rhs, idx[out], c[out] * U[JZ[out] + 1, JX[out] + 1])
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(ni * nk, ni * nk))
+    U[1:-1, 1:-1] = spla.spsolve(A.tocsc(), rhs).reshape(nk, ni)
+    return xs, zs, U
+
+
+def fd_tm_richardson(domain, diffusion, interfaces, kappa, g_fn, pts, h=1 / 40):
+    """Richardson-extrapolated FD values at grid points pts (on both grids),
+    and the size of the extrapolation step as an error estimate."""
+    vals = []
+    for hh in (h, h / 2):
+        xs, zs, U = fd_solve_tm(domain, hh, diffusion, interfaces, kappa, g_fn)
+        vals.append(np.array([U[int(round((z - zs[0]) / hh)), int(round((x - xs[0]) / hh))] for x, z in pts]))
+    ext = (4.0 * vals[1] - vals[0]) / 3.0
+    return ext, np.abs(ext - vals[1])

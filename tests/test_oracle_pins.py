@@ -304,3 +304,110 @@ def test_each_evaluation_row_uses_its_own_rates():
         se = r["se"][0, e]
         assert abs(dev.real) <= 4 * se[0] + pins.bias_bound(dt)
         assert abs(dev.imag) <= 4 * se[1] + pins.bias_bound(dt)
+
+
+# ------------------------------------------------------------------ TM mode
+# Diffusion coefficient that jumps across vertical interfaces (Sec. 2.2 and
+# the interface rules of Sec. 3.1).  The interface treatment is first order:
+# its bias is O(sqrt(dt)); TM_BIAS_C sqrt(dt) bounds what a dt sweep of these
+# pins measured (<= 0.028 sqrt(dt) away from interfaces started on, at
+# dt = 1e-4 and 1e-3).
+TM_BIAS_C = 0.3
+TM_DOM = (-1.0, 1.0, -0.5, 1.0)
+
+
+def _tm(diffusion, interfaces, kappa, g=("tm_flux",), domain=TM_DOM):
+    return {"domain": domain, "kappa": [list(kappa)], "diffusion": list(diffusion),
+            "interfaces": list(interfaces), "g": g}
+
+
+def _tm_close(mean, se, exact, dt):
+    tol_re = 4.0 * se[..., 0] + TM_BIAS_C * np.sqrt(dt)
+    tol_im = 4.0 * se[..., 1] + TM_BIAS_C * np.sqrt(dt)
+    d = mean - exact
+    return bool(np.all(np.abs(d.real) <= tol_re) and np.all(np.abs(d.imag) <= tol_im))
+
+
+def test_tm_uniforms_are_the_words_of_their_own_philox_call():
+    for urule in (32, 23):
+        U = O.tm_uniforms(77, 3, 11, 5, urule)
+        w = O.philox4x32_10([5, 11, 3, 2], [77, 0])
+        assert np.array_equal(U, [O.uniform(int(x), urule) for x in w])
+
+
+@pytest.mark.parametrize("diffusion,interfaces", [((1.0, 10.0), (0.3,)), ((4.0, 0.5, 2.0), (-0.4, 0.2))])
+def test_tm_flux_continuous_solution_without_phase(diffusion, interfaces):
+    # kappa = 0: u(x) = int dx / D solves div(D grad u) = 0 with the same flux
+    # on both sides of every interface; its kink pins the crossing probability
+    # D_i / (D_i + D_j) and the side of the resampling disc (a probability of
+    # 1/2, or the disc on the wrong side, miss by tens of standard errors)
+    dt = 1e-3
+    m = _tm(diffusion, interfaces, [0.0] * len(diffusion))
+    xs = np.array([-0.8, -0.45, -0.4, 0.0, 0.25, 0.3, 0.6, 0.9])
+    nodes = np.stack([xs, np.full_like(xs, 0.25)], axis=1)
+    r = O.interface_values(m, nodes, 20000, dt, 11)
+    exact = pins.u_flux(xs, diffusion, interfaces, TM_DOM[0])
+    assert _tm_close(r["mean"][:, 0], r["se"][:, 0], exact, dt)
+
+
+def test_tm_analytic_test_model():
+    # the analytic test of Sec. 4.1 on [-1,1]^2: D = 1 | 10 across x = 0,
+    # lambda = 10i, i.e. D Lap u = i kappa u with kappa = -10; exact solution
+    # (z + 1) cosh(a x), D a^2 = i kappa, read with the square root over
+    # lambda / kappa_j only (the printed form is garbled)
+    dt = 1e-4
+    m = _tm((1.0, 10.0), (0.0,), (-10.0, -10.0), g=("tm_cosh",), domain=(-1.0, 1.0, -1.0, 1.0))
+    nodes = np.array([[0.6, 0.6], [-0.5, 0.2], [0.0, -0.3]])
+    r = O.interface_values(m, nodes, 20000, dt, 7)
+    exact = np.array([(z + 1.0) * np.cosh(np.sqrt(1j * -10.0 / (1.0 if x < 0 else 10.0)) * x) for x, z in nodes])
+    assert _tm_close(r["mean"][:, 0], r["se"][:, 0], exact, dt)
+
+
+def test_tm_matches_finite_volumes_with_phase_and_flux():
+    # kappa = 2 | 20 and D = 1 | 10 across x = 0 with boundary data int dx / D:
+    # no closed form; Richardson-extrapolated finite volumes on h = 1/40, 1/80
+    # (flux-conservative faces, the interface on a grid column); one node on
+    # the interface itself
+    dt = 1e-4
+    D, xif, kap = (1.0, 10.0), (0.0,), (2.0, 20.0)
+    pts = [(-0.5, 0.25), (-0.1, 0.25), (0.0, 0.5), (0.1, 0.25), (0.5, 0.75)]
+    ref, err = pins.fd_tm_richardson(TM_DOM, D, xif, kap,
+                                     lambda X, Z: pins.u_flux(X, D, xif, TM_DOM[0]) + 0.0j, pts)
+    r = O.interface_values(_tm(D, xif, kap), np.array(pts), 12000, dt, 5)
+    assert _tm_close(r["mean"][:, 0], r["se"][:, 0] + err[:, None], ref, dt)
+
+
+def test_tm_equal_diffusion_is_the_te_walk():
+    # D the same in every strip: no interface events, so every walk equals the
+    # TE walk through the same material map (strip = material), step by step
+    dt = 1e-3
+    tm = _tm((1.0, 1.0), (0.3,), (2.0, 20.0), g=("affine", 0.5, 1.0, 0.25))
+    te = {"domain": TM_DOM, "kappa": [[2.0, 20.0]], "bg": (0, 0),
+          "shapes": [(0, 1, (0.3, 2.0, -1.0, 2.0, 0.0, 0.0))], "g": ("affine", 0.5, 1.0, 0.25)}
+    a = O.walk_records(tm, (0.1, 0.2), 4, 0, 500, dt, 3)
+    b = O.walk_records(te, (0.1, 0.2), 4, 0, 500, dt, 3)
+    for k in ("steps", "counts", "exit", "wall", "m_last"):
+        assert np.array_equal(a[k], b[k]), k
+    assert np.array_equal(a["occ"], a["counts"]) and a["hits"].sum() == 0
+    # a uniform D = 4 is Brownian motion run 4 times faster: mean exit time / 4
+    fast = _tm((4.0, 4.0), (0.3,), (0.0, 0.0))
+    nodes = np.array([[0.0, 0.25], [0.5, 0.25]])
+    rf = O.interface_values(fast, nodes, 20000, dt, 9)
+    for (x, z), t in zip(nodes, rf["tau_mean"]):
+        assert abs(t - pins.exit_time_series(x, z, TM_DOM) / 4.0) <= 0.02 * pins.exit_time_series(x, z, TM_DOM) / 4.0 + 0.002
+
+
+def test_tm_walks_hit_interfaces_and_conserve_time():
+    dt = 1e-3
+    m = _tm((1.0, 10.0), (0.0,), (2.0, 20.0))
+    rec = O.walk_records(m, (0.0, 0.25), 0, 0, 2000, dt, 5)
+    assert rec["hits"].min() >= 1  # every walk starts on the interface
+    ok = rec["truncated"] == 0
+    # occupation per walk, in units of dt: every step but the exiting one
+    # (which contributes theta through the last material), or every step when
+    # the walk ended because a resampled point fell outside the domain
+    # (theta = 0; the step's dt was split at the interface)
+    disc_exit = rec["exit"][:, 2] == 0.0
+    want = rec["steps"] - 1 + disc_exit
+    assert np.allclose(rec["occ"][ok].sum(1), want[ok], rtol=0, atol=1e-9)
+    assert 0 < disc_exit.sum() < 50
