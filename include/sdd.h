@@ -88,14 +88,27 @@ typedef struct {
  *   between the two corner values.
  * SDD_G_AFFINE: g = a + b x + c z, complex a, b, c in g_coef
  *   (a_re, a_im, b_re, b_im, c_re, c_im); harmonic, for checks.
- * SDD_G_X2MZ2: g = x^2 - z^2; harmonic, for checks. */
-enum { SDD_G_COLUMNS = 0, SDD_G_AFFINE = 1, SDD_G_X2MZ2 = 2 };
+ * SDD_G_X2MZ2: g = x^2 - z^2; harmonic, for checks.
+ * SDD_G_TM_COSH (TM mode only): g = (z + 1) cosh(a x), a = sqrt(i kappa_{e,s} / D_s)
+ *   with Re a >= 0 for the strip s of x: the exact solution of the analytic
+ *   test model of Sec. 4.1 when its one interface is at x = 0.
+ * SDD_G_TM_FLUX (TM mode only): g = int_{x_min}^x ds / D(s), the solution with
+ *   kappa = 0 and the same flux D u' = 1 in every strip. */
+enum { SDD_G_COLUMNS = 0, SDD_G_AFFINE = 1, SDD_G_X2MZ2 = 2, SDD_G_TM_COSH = 3, SDD_G_TM_FLUX = 4 };
 
 /* Conductivity model.  Material of a point: if raster != NULL, the cell
  * (clamp(floor((x - x_min) nx / (x_max - x_min))), same for z) of the int8
  * raster [nz][nx]; otherwise bg_air (z < 0) or bg_earth (z >= 0) overridden
  * by the shapes in order.  kappa[e][m] >= 0 is the dimensionless phase rate
- * of material m in evaluation e. */
+ * of material m in evaluation e.
+ *
+ * TM mode (diffusion != NULL): the diffusion coefficient jumps across
+ * vertical interfaces (Sec. 2.2, the Helmholtz equation per sub-domain with
+ * flux continuity; the interface rules of Sec. 3.1).  Material m is the strip
+ * [interfaces[m-1], interfaces[m]) (the first from x_min, the last to x_max)
+ * with diffusion D_m, and D_m Lap u = i kappa_{e,m} u there; kappa may then
+ * be negative.  Shapes, raster and background are not used, and g_kind is
+ * AFFINE, X2MZ2, TM_COSH or TM_FLUX. */
 typedef struct {
     sdd_domain domain;
     int32_t n_materials;   /* K, 1..SDD_MAX_MATERIALS */
@@ -109,6 +122,9 @@ typedef struct {
     int32_t g_kind;
     int32_t g_left, g_right;
     double g_coef[6];
+    const double *diffusion;  /* host, [n_materials] D_m > 0, copied; NULL = TE mode */
+    const double *interfaces; /* host, [n_materials - 1] strictly increasing, inside
+                                 (x_min, x_max), copied; TM mode only */
 } sdd_model_desc;
 
 enum { SDD_FP32 = 0, SDD_FP64 = 1 };
@@ -266,6 +282,20 @@ sdd_status sdd_walk_records(sdd_ctx *ctx, double x0, double z0, uint32_t node_id
                             int32_t count, double dt, uint64_t seed, const sdd_config *cfg,
                             int64_t *steps, int64_t *counts, double *exit_xzt, int32_t *wall,
                             int32_t *m_last);
+
+/* Per-path occupation records, for TE and TM models (a TM model's interface
+ * hits split a step's time between two strips, Sec. 3.1; sdd_walk_records
+ * rejects TM models with SDD_E_UNSUPPORTED):
+ *   steps     [count] Euler steps taken (the exiting step included)
+ *   occ       [count][n_materials] time spent in material m in units of dt,
+ *             without the theta of the last step (TE: the step counts)
+ *   exit_xzt, wall, m_last  as in sdd_walk_records
+ *   hits      [count] interface randomisations (TM; 0 in TE)
+ * Every output pointer may be NULL except steps. */
+sdd_status sdd_walk_occupation(sdd_ctx *ctx, double x0, double z0, uint32_t node_id, uint32_t p0,
+                               int32_t count, double dt, uint64_t seed, const sdd_config *cfg,
+                               int64_t *steps, double *occ, double *exit_xzt, int32_t *wall,
+                               int32_t *m_last, int64_t *hits);
 
 /* Limits of sdd_interface_values_noalloc: nodes per call, work items per call
  * (the path chunks are widened until the items fit), and the size in bytes of

@@ -129,7 +129,7 @@ struct sdd_ctx {
     DevBuf raster, tiles;
     // per-call scratch
     DevBuf items, slots, trunc, counters, queue, err, nodes, node_ids, mean, se;
-    DevBuf rec_steps, rec_counts, rec_exit, rec_wall, rec_mlast;
+    DevBuf rec_steps, rec_counts, rec_occ, rec_hits, rec_exit, rec_wall, rec_mlast;
     DevBuf batch_models;  // model table of batched launches owned by this context
     Item *h_items = nullptr;  // pinned staging of the item table
     size_t h_items_cap = 0;
@@ -174,10 +174,27 @@ sdd_status check_model(const sdd_model_desc *m) {
         return fail(SDD_E_ARG, "n_materials must be in 1..8");
     if (m->n_eval < 1 || m->n_eval > SDD_MAX_EVAL) return fail(SDD_E_ARG, "n_eval must be in 1..32");
     if (!m->kappa) return fail(SDD_E_ARG, "kappa is NULL");
+    const bool tm = m->diffusion != nullptr;
     for (int i = 0; i < m->n_eval * m->n_materials; ++i)
-        if (!std::isfinite(m->kappa[i]) || m->kappa[i] < 0.0)
-            return fail(SDD_E_ARG, "kappa must be finite and >= 0");
+        if (!std::isfinite(m->kappa[i]) || (!tm && m->kappa[i] < 0.0))
+            return fail(SDD_E_ARG, tm ? "kappa must be finite" : "kappa must be finite and >= 0");
     const int K = m->n_materials;
+    if (tm) {
+        for (int k = 0; k < K; ++k)
+            if (!(m->diffusion[k] > 0.0) || !std::isfinite(m->diffusion[k]))
+                return fail(SDD_E_ARG, "TM diffusion must be finite and > 0");
+        if (K > 1 && !m->interfaces) return fail(SDD_E_ARG, "TM interfaces is NULL");
+        for (int k = 0; k + 1 < K; ++k) {
+            const double xk = m->interfaces[k];
+            if (!(xk > d.x_min && xk < d.x_max) || (k > 0 && !(xk > m->interfaces[k - 1])))
+                return fail(SDD_E_ARG, "TM interfaces must increase strictly inside (x_min, x_max)");
+        }
+        if (m->raster || m->n_shapes != 0) return fail(SDD_E_ARG, "TM mode takes no shapes or raster");
+        if (m->g_kind != SDD_G_AFFINE && m->g_kind != SDD_G_X2MZ2 && m->g_kind != SDD_G_TM_COSH &&
+            m->g_kind != SDD_G_TM_FLUX)
+            return fail(SDD_E_ARG, "TM mode g_kind must be AFFINE, X2MZ2, TM_COSH or TM_FLUX");
+        return SDD_OK;
+    }
     if (m->raster) {
         if (m->nx < 1 || m->nz < 1 || m->nx > kMaxRasterSide || m->nz > kMaxRasterSide ||
             (long long)m->nx * m->nz > (1ll << 31))
@@ -201,7 +218,8 @@ sdd_status check_model(const sdd_model_desc *m) {
                 if (std::isnan(S.v[j])) return fail(SDD_E_ARG, "shape coordinate is NaN");
         }
     }
-    if (m->g_kind < SDD_G_COLUMNS || m->g_kind > SDD_G_X2MZ2) return fail(SDD_E_ARG, "unknown g_kind");
+    if (m->g_kind < SDD_G_COLUMNS || m->g_kind > SDD_G_X2MZ2)
+        return fail(SDD_E_ARG, "unknown g_kind (TM_COSH and TM_FLUX need TM mode)");
     if (m->g_kind == SDD_G_COLUMNS &&
         (m->g_left < 0 || m->g_left >= K || m->g_right < 0 || m->g_right >= K))
         return fail(SDD_E_ARG, "g_left / g_right out of range");
@@ -226,7 +244,23 @@ void build_model(const sdd_model_desc *m, ModelDev &M) {
     M.fhw = (float)M.hw; M.fhh = (float)M.hh;
     M.fxc = (float)M.xc; M.fzc = (float)M.zc;
     M.fzs = (float)(0.0 - M.zc);
-    if (!m->raster) {
+    if (m->diffusion) {
+        M.tm = 1;
+        M.gcode = GC_TM;
+        for (int k = 0; k < M.K; ++k) {
+            M.diff[k] = m->diffusion[k];
+            M.fdiff[k] = (float)m->diffusion[k];
+            M.xif[k] = k + 1 < M.K ? m->interfaces[k] : d.x_max;
+            M.fxif[k] = (float)M.xif[k];
+        }
+        for (int e = 0; e < M.E; ++e)
+            for (int k = 0; k < M.K; ++k) {
+                const std::complex<double> a =
+                    std::sqrt(std::complex<double>(0.0, m->kappa[e * M.K + k] / m->diffusion[k]));
+                M.tm_a[e][k][0] = a.real();
+                M.tm_a[e][k][1] = a.imag();
+            }
+    } else if (!m->raster) {
         M.n_shapes = m->n_shapes;
         for (int s = 0; s < m->n_shapes; ++s) {
             const sdd_shape &S = m->shapes[s];
@@ -691,6 +725,7 @@ sdd_status sdd_create(const sdd_model_desc *model, sdd_ctx **out) {
     build_model(model, c->M);
     c->K = model->n_materials;
     c->E = model->n_eval;
+    if (model->diffusion) c->geo = GEO_TM;
     if (model->raster) {
         c->geo = GEO_RASTER;
         const size_t nb = (size_t)model->nx * model->nz;
@@ -730,7 +765,8 @@ void sdd_destroy(sdd_ctx *c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     DevBuf *bufs[] = {&c->raster, &c->tiles, &c->items, &c->slots, &c->trunc, &c->counters, &c->queue,
                       &c->err, &c->nodes, &c->node_ids, &c->mean, &c->se, &c->rec_steps,
-                      &c->rec_counts, &c->rec_exit, &c->rec_wall, &c->rec_mlast,
+                      &c->rec_counts, &c->rec_occ, &c->rec_hits, &c->rec_exit, &c->rec_wall,
+                      &c->rec_mlast,
                       &c->batch_models};
     for (DevBuf *b : bufs) b->release();
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
@@ -867,10 +903,16 @@ sdd_status sdd_interface_values_device(sdd_ctx *ctx, const double *d_nodes_xz,
     return SDD_OK;
 }
 
-sdd_status sdd_walk_records(sdd_ctx *ctx, double x0, double z0, uint32_t node_id, uint32_t p0,
-                            int32_t count, double dt, uint64_t seed, const sdd_config *cfg,
-                            int64_t *steps, int64_t *counts, double *exit_xzt, int32_t *wall,
-                            int32_t *m_last) {
+}  // extern "C"
+
+namespace {
+
+// Per-path records of paths p0 .. p0+count-1 of one node (the walk kernel
+// writes them instead of summing samples).
+sdd_status walk_records(sdd_ctx *ctx, double x0, double z0, uint32_t node_id, uint32_t p0,
+                        int32_t count, double dt, uint64_t seed, const sdd_config *cfg,
+                        int64_t *steps, int64_t *counts, double *occ, double *exit_xzt,
+                        int32_t *wall, int32_t *m_last, int64_t *hits) {
     const int64_t np = count;
     sdd_status st = check_call(ctx, count > 0 ? 1 : 0, &np, dt, cfg);
     if (st != SDD_OK) return st;
@@ -887,6 +929,8 @@ sdd_status sdd_walk_records(sdd_ctx *ctx, double x0, double z0, uint32_t node_id
     SDD_CUDA(ctx->node_ids.ensure(sizeof(uint32_t)));
     SDD_CUDA(ctx->rec_steps.ensure((size_t)count * 8));
     SDD_CUDA(ctx->rec_counts.ensure((size_t)count * ctx->K * 8));
+    SDD_CUDA(ctx->rec_occ.ensure((size_t)count * ctx->K * 8));
+    SDD_CUDA(ctx->rec_hits.ensure((size_t)count * 8));
     SDD_CUDA(ctx->rec_exit.ensure((size_t)count * 3 * 8));
     SDD_CUDA(ctx->rec_wall.ensure((size_t)count * 4));
     SDD_CUDA(ctx->rec_mlast.ensure((size_t)count * 4));
@@ -897,6 +941,8 @@ sdd_status sdd_walk_records(sdd_ctx *ctx, double x0, double z0, uint32_t node_id
     A.node_ids = (const uint32_t *)ctx->node_ids.p;
     A.rec_steps = (int64_t *)ctx->rec_steps.p;
     A.rec_counts = (int64_t *)ctx->rec_counts.p;
+    A.rec_occ = (double *)ctx->rec_occ.p;
+    A.rec_hits = (int64_t *)ctx->rec_hits.p;
     A.rec_exit = (double *)ctx->rec_exit.p;
     A.rec_wall = (int32_t *)ctx->rec_wall.p;
     A.rec_mlast = (int32_t *)ctx->rec_mlast.p;
@@ -905,6 +951,8 @@ sdd_status sdd_walk_records(sdd_ctx *ctx, double x0, double z0, uint32_t node_id
     SDD_CUDA(cudaMemcpyAsync(steps, ctx->rec_steps.p, (size_t)count * 8, cudaMemcpyDeviceToHost, s));
     if (counts)
         SDD_CUDA(cudaMemcpyAsync(counts, ctx->rec_counts.p, (size_t)count * ctx->K * 8, cudaMemcpyDeviceToHost, s));
+    if (occ) SDD_CUDA(cudaMemcpyAsync(occ, ctx->rec_occ.p, (size_t)count * ctx->K * 8, cudaMemcpyDeviceToHost, s));
+    if (hits) SDD_CUDA(cudaMemcpyAsync(hits, ctx->rec_hits.p, (size_t)count * 8, cudaMemcpyDeviceToHost, s));
     if (exit_xzt)
         SDD_CUDA(cudaMemcpyAsync(exit_xzt, ctx->rec_exit.p, (size_t)count * 24, cudaMemcpyDeviceToHost, s));
     if (wall) SDD_CUDA(cudaMemcpyAsync(wall, ctx->rec_wall.p, (size_t)count * 4, cudaMemcpyDeviceToHost, s));
@@ -913,7 +961,27 @@ sdd_status sdd_walk_records(sdd_ctx *ctx, double x0, double z0, uint32_t node_id
     return SDD_OK;
 }
 
-}  // extern "C"
+}  // namespace
+
+extern "C" sdd_status sdd_walk_records(sdd_ctx *ctx, double x0, double z0, uint32_t node_id, uint32_t p0,
+                                       int32_t count, double dt, uint64_t seed, const sdd_config *cfg,
+                                       int64_t *steps, int64_t *counts, double *exit_xzt, int32_t *wall,
+                                       int32_t *m_last) {
+    if (ctx && ctx->geo == GEO_TM)
+        return fail(SDD_E_UNSUPPORTED, "TM walks split steps between strips: use sdd_walk_occupation");
+    return walk_records(ctx, x0, z0, node_id, p0, count, dt, seed, cfg, steps, counts, nullptr,
+                        exit_xzt, wall, m_last, nullptr);
+}
+
+extern "C" sdd_status sdd_walk_occupation(sdd_ctx *ctx, double x0, double z0, uint32_t node_id,
+                                          uint32_t p0, int32_t count, double dt, uint64_t seed,
+                                          const sdd_config *cfg, int64_t *steps, double *occ,
+                                          double *exit_xzt, int32_t *wall, int32_t *m_last,
+                                          int64_t *hits) {
+    return walk_records(ctx, x0, z0, node_id, p0, count, dt, seed, cfg, steps, nullptr, occ, exit_xzt,
+                        wall, m_last, hits);
+}
+
 
 // ---------------------------------------------------------------------------
 // Entry point that allocates nothing (sdd_interface_values_noalloc).

@@ -17,7 +17,7 @@ constexpr int kMaxE = 32;
 constexpr int kMaxShapes = 16;
 constexpr int kRing = 64;  // exit records buffered per warp
 
-enum Geo : int { GEO_SHAPES = 0, GEO_RASTER = 1 };
+enum Geo : int { GEO_SHAPES = 0, GEO_RASTER = 1, GEO_TM = 2 };
 
 // Material-lookup programs of the single-precision walk, chosen per model so
 // that the common cases run without loops or branches: the layered
@@ -27,9 +27,10 @@ enum Geo : int { GEO_SHAPES = 0, GEO_RASTER = 1 };
 // by a vertical contact at x0 (the quarter-space model), tested with two
 // compares; it takes the same decisions as GC_RECT1 on every inside point.
 // GC_RASTER_MULTI serves a batch of raster models sharing the domain and the
-// raster size: each lane reads the raster of its walk's model.
+// raster size: each lane reads the raster of its walk's model.  GC_TM is the
+// TM walk over vertical strips (its own walker).
 enum GeoCode : int { GC_LAYER = 0, GC_RECT1 = 1, GC_TRI1 = 2, GC_SHAPES4 = 3, GC_SHAPES16 = 4,
-                     GC_RASTER = 5, GC_CONTACT = 6, GC_RASTER_MULTI = 7 };
+                     GC_RASTER = 5, GC_CONTACT = 6, GC_RASTER_MULTI = 7, GC_TM = 8 };
 
 
 
@@ -115,6 +116,12 @@ struct ModelDev {
     float fsx, fsz;  // raster cells per unit length
     float fox, foz;  // hw * sx - 1/2 + kTile, hh * sz - 1/2 + kTile: round(X sx + ox) is the
                      // cell index plus kTile (the tile map's margin)
+    // TM mode: material m is the vertical strip [xif[m-1], xif[m]) with
+    // diffusion diff[m]
+    int32_t tm;
+    double diff[kMaxK], xif[kMaxK];
+    float fdiff[kMaxK], fxif[kMaxK];
+    double tm_a[kMaxE][kMaxK][2];  // boundary data kind 3: sqrt(i kappa_{e,m} / D_m)
 };
 
 struct WalkArgs {
@@ -140,7 +147,9 @@ struct WalkArgs {
     // per-path dump (sdd_walk_records); when rec_steps != nullptr the walk
     // records are written here instead of being summed
     int64_t *rec_steps;
-    int64_t *rec_counts;       // [count][K]
+    int64_t *rec_counts;       // [count][K] (nullable)
+    double *rec_occ;           // [count][K] occupation in units of dt (nullable)
+    int64_t *rec_hits;         // [count] interface randomisations (nullable)
     double *rec_exit;          // [count][3]
     int32_t *rec_wall;
     int32_t *rec_mlast;

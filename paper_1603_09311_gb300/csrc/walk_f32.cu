@@ -19,6 +19,7 @@
 // Philox call (words 0,1 for the even step, 2,3 for the odd one), and one
 // call of iterate() runs 8 steps (4 with 8 materials).
 #include "walk_sched.cuh"
+#include "walk_tm.cuh"
 
 namespace sdd {
 
@@ -110,6 +111,11 @@ template <int KMAX_, int GC>
 struct WalkerF32 {
     using Real = float;
     static constexpr int KMAX = KMAX_;
+    // records: step counts of materials 1..K-1 (material 0 from the total)
+    using Occ = uint32_t;
+    using HistT = uint32_t;
+    static constexpr int kStored = KMAX - 1;
+    static constexpr int kHist = KMAX == 8 ? 8 : 1;
 
     float X, Z, dmin;  // centred position, distance to the nearest wall
     uint32_t n;        // Euler steps accepted (even at the start of iterate)
@@ -163,7 +169,7 @@ struct WalkerF32 {
     }
 
     __device__ __forceinline__ void counts(uint32_t *c) const { occ.counts(c); }
-    __device__ __forceinline__ void bind(uint32_t a) { occ.bind(a); }
+    __device__ __forceinline__ void bind(HistT *h) { occ.bind((uint32_t)__cvta_generic_to_shared(h)); }
 
     __device__ __forceinline__ void start(const ModelDev &M, const WalkArgs &A, double x0,
                                           double z0, uint32_t path, uint32_t node_id, int model) {
@@ -418,7 +424,7 @@ struct WalkerF32 {
 template <int KMAX, int GC>
 static cudaError_t launch_one(const ModelDev &M, const WalkArgs &A, int grid, int block,
                               cudaStream_t s) {
-    const size_t sm = shared_bytes<float, KMAX>(block / 32, M.E, M.K);
+    const size_t sm = shared_bytes<WalkerF32<KMAX, GC>>(block / 32, M.E, M.K);
     auto k = walk_kernel<WalkerF32<KMAX, GC>>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -428,7 +434,7 @@ static cudaError_t launch_one(const ModelDev &M, const WalkArgs &A, int grid, in
 
 template <int KMAX, int GC>
 static int occ_one(int block, int E, int K) {
-    const size_t sm = shared_bytes<float, KMAX>(block / 32, E, K);
+    const size_t sm = shared_bytes<WalkerF32<KMAX, GC>>(block / 32, E, K);
     auto k = walk_kernel<WalkerF32<KMAX, GC>>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
         return 0;
@@ -460,14 +466,55 @@ static int occ_one(int block, int E, int K) {
     default: break;                                                             \
     }
 
+// The TM walk (vertical strips, K <= KMAX in {2, 3, 4, 8}).
+template <int KMAX>
+static cudaError_t launch_tm(const ModelDev &M, const WalkArgs &A, int grid, int block, cudaStream_t s) {
+    using W = WalkerTM<float, KMAX>;
+    const size_t sm = shared_bytes<W>(block / 32, M.E, M.K);
+    auto k = walk_kernel<W>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k<<<grid, block, sm, s>>>(M, A);
+    return cudaGetLastError();
+}
+
+template <int KMAX>
+static int occ_tm(int block, int E, int K) {
+    using W = WalkerTM<float, KMAX>;
+    const size_t sm = shared_bytes<W>(block / 32, E, K);
+    auto k = walk_kernel<W>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, sm) != cudaSuccess) return 0;
+    return n;
+}
+
+#define SDD_TM_DISPATCH(FN, ...)                                                \
+    switch (kmax) {                                                             \
+    case 2: return FN<2>(__VA_ARGS__);                                          \
+    case 3: return FN<3>(__VA_ARGS__);                                          \
+    case 4: return FN<4>(__VA_ARGS__);                                          \
+    case 8: return FN<8>(__VA_ARGS__);                                          \
+    default: break;                                                             \
+    }
+
 cudaError_t launch_walk_f32(int kmax, int /*geo*/, const ModelDev &M, const WalkArgs &A, int grid,
                             int block, cudaStream_t s) {
     const int gcode = M.gcode;
+    if (gcode == GC_TM) {
+        SDD_TM_DISPATCH(launch_tm, M, A, grid, block, s)
+        return cudaErrorInvalidValue;
+    }
     SDD_DISPATCH(launch_one, M, A, grid, block, s)
     return cudaErrorInvalidValue;
 }
 
 int occupancy_f32(int kmax, int gcode, int block, int E, int K) {
+    if (gcode == GC_TM) {
+        SDD_TM_DISPATCH(occ_tm, block, E, K)
+        return 0;
+    }
     SDD_DISPATCH(occ_one, block, E, K)
     return 0;
 }

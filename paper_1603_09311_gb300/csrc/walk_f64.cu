@@ -13,6 +13,7 @@
 // -> hit iff min_w 2 d_w d'_w / dt <= -ln U (first case with kappa_i = 1);
 // else the step counts for the material of beta'.
 #include "walk_sched.cuh"
+#include "walk_tm.cuh"
 
 namespace sdd {
 
@@ -25,6 +26,10 @@ struct WalkerF64 {
     using Real = double;
     static constexpr int KMAX = KMAX_;
     static constexpr bool kCoop = false;  // no cooperative tail: the parity walk stays plain
+    using Occ = uint32_t;
+    using HistT = uint32_t;
+    static constexpr int kStored = KMAX - 1;
+    static constexpr int kHist = 1;
 
     double x, z;
     uint32_t n;
@@ -63,7 +68,7 @@ struct WalkerF64 {
         }
     }
 
-    __device__ __forceinline__ void bind(uint32_t) {}
+    __device__ __forceinline__ void bind(HistT *) {}
 
     __device__ __forceinline__ void counts(uint32_t *c) const {
 #pragma unroll
@@ -220,7 +225,7 @@ struct WalkerF64 {
 template <int KMAX, int GEO>
 static cudaError_t launch_one(const ModelDev &M, const WalkArgs &A, int grid, int block,
                               cudaStream_t s) {
-    const size_t sm = shared_bytes<double, KMAX>(block / 32, M.E, M.K);
+    const size_t sm = shared_bytes<WalkerF64<KMAX, GEO>>(block / 32, M.E, M.K);
     auto k = walk_kernel<WalkerF64<KMAX, GEO>>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -230,7 +235,7 @@ static cudaError_t launch_one(const ModelDev &M, const WalkArgs &A, int grid, in
 
 template <int KMAX, int GEO>
 static int occ_one(int block, int E, int K) {
-    const size_t sm = shared_bytes<double, KMAX>(block / 32, E, K);
+    const size_t sm = shared_bytes<WalkerF64<KMAX, GEO>>(block / 32, E, K);
     auto k = walk_kernel<WalkerF64<KMAX, GEO>>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
         return 0;
@@ -252,13 +257,54 @@ static int occ_one(int block, int E, int K) {
     default: break;                                                             \
     }
 
+// The TM parity walk (vertical strips).
+template <int KMAX>
+static cudaError_t launch_tm(const ModelDev &M, const WalkArgs &A, int grid, int block, cudaStream_t s) {
+    using W = WalkerTM<double, KMAX>;
+    const size_t sm = shared_bytes<W>(block / 32, M.E, M.K);
+    auto k = walk_kernel<W>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k<<<grid, block, sm, s>>>(M, A);
+    return cudaGetLastError();
+}
+
+template <int KMAX>
+static int occ_tm(int block, int E, int K) {
+    using W = WalkerTM<double, KMAX>;
+    const size_t sm = shared_bytes<W>(block / 32, E, K);
+    auto k = walk_kernel<W>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+        return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, block, sm) != cudaSuccess) return 0;
+    return n;
+}
+
+#define SDD_TM_DISPATCH(FN, ...)                                                \
+    switch (kmax) {                                                             \
+    case 2: return FN<2>(__VA_ARGS__);                                          \
+    case 3: return FN<3>(__VA_ARGS__);                                          \
+    case 4: return FN<4>(__VA_ARGS__);                                          \
+    case 8: return FN<8>(__VA_ARGS__);                                          \
+    default: break;                                                             \
+    }
+
 cudaError_t launch_walk_f64(int kmax, int geo, const ModelDev &M, const WalkArgs &A, int grid,
                             int block, cudaStream_t s) {
+    if (geo == GEO_TM) {
+        SDD_TM_DISPATCH(launch_tm, M, A, grid, block, s)
+        return cudaErrorInvalidValue;
+    }
     SDD_DISPATCH(launch_one, M, A, grid, block, s)
     return cudaErrorInvalidValue;
 }
 
 int occupancy_f64(int kmax, int geo, int block, int E, int K) {
+    if (geo == GEO_TM) {
+        SDD_TM_DISPATCH(occ_tm, block, E, K)
+        return 0;
+    }
     SDD_DISPATCH(occ_one, block, E, K)
     return 0;
 }

@@ -107,15 +107,21 @@ __device__ __forceinline__ uint4 philox_rk(uint4 c, const uint32_t (&rk0)[10],
 }
 
 // Shared-memory layout of one CTA: model tables, then for each warp its
-// exit-record ring and its scheduler state.
-template <class Real, int KMAX>
+// exit-record ring and its scheduler state.  A walker W states what it
+// records per material: W::Occ (step counts, or occupation times when they
+// can be fractional) for W::kStored materials (all but material 0 when that
+// one is derived from the step total, else all K), and W::kHist words per
+// lane of shared-memory occupation histogram (W::HistT).
+template <class W>
 struct Ring {
+    using Real = typename W::Real;
     Real x[kRing], z[kRing], th[kRing];
     uint32_t meta[kRing];  // wall | m_last << 2 | truncated << 6 | model << 8
     int32_t item[kRing];
     uint32_t n[kRing];     // occupation steps (all steps but the exiting one)
     uint32_t path[kRing];
-    uint32_t cnt[KMAX > 1 ? KMAX - 1 : 1][kRing];  // steps in materials 1..K-1
+    uint32_t aux[kRing];   // interface randomisations (TM walks)
+    typename W::Occ cnt[W::kStored][kRing];
 };
 
 // Scheduler state of one warp (every field is the same for all its lanes,
@@ -142,12 +148,12 @@ __host__ __device__ constexpr size_t tables_bytes(int E, int K) {
     return ((size_t)E * K * sizeof(double) + 15) / 16 * 16 + (size_t)E * sizeof(EvalDev);
 }
 
-template <class Real, int KMAX>
+template <class W>
 struct WarpSmem {
-    Ring<Real, KMAX> ring;
+    Ring<W> ring;
     WarpState st;
-    uint32_t hist[KMAX == 8 ? 8 : 1][32];  // per-lane step counts of up to 8 materials
-    float4 tail[sizeof(Real) == 4 ? 64 : 1];  // step increments of the cooperative tail
+    typename W::HistT hist[W::kHist][32];     // per-lane occupation histogram
+    float4 tail[W::kCoop ? 64 : 1];           // step increments of the cooperative tail
 };
 
 // A warp whose queue is drained switches to the cooperative tail once it
@@ -155,9 +161,9 @@ struct WarpSmem {
 constexpr int kTailWalks = 8;
 
 
-template <class Real, int KMAX>
+template <class W>
 __host__ __device__ constexpr size_t shared_bytes(int warps, int E, int K) {
-    return (tables_bytes(E, K) + 15) / 16 * 16 + (size_t)warps * sizeof(WarpSmem<Real, KMAX>);
+    return (tables_bytes(E, K) + 15) / 16 * 16 + (size_t)warps * sizeof(WarpSmem<W>);
 }
 
 // Exit information handed from a walker to the scheduler.
@@ -167,6 +173,7 @@ struct ExitInfo {
     int wall;       // 0..3
     int mlast;      // material of the last point inside
     uint32_t nocc;  // occupation steps (all steps but the exiting one)
+    uint32_t aux;   // interface randomisations (TM walks)
 };
 
 // Scheduler kernel.  W is a walker type providing
@@ -191,9 +198,9 @@ __global__ void __launch_bounds__(256, 3) walk_kernel(const __grid_constant__ Mo
     SharedTables T;
     T.kappa = reinterpret_cast<double *>(smem_raw);
     T.ev = reinterpret_cast<EvalDev *>(smem_raw + ((size_t)M.E * M.K * sizeof(double) + 15) / 16 * 16);
-    WarpSmem<Real, KMAX> &WS = reinterpret_cast<WarpSmem<Real, KMAX> *>(
+    WarpSmem<W> &WS = reinterpret_cast<WarpSmem<W> *>(
         smem_raw + (tables_bytes(M.E, M.K) + 15) / 16 * 16)[threadIdx.x >> 5];
-    Ring<Real, KMAX> &R = WS.ring;
+    Ring<W> &R = WS.ring;
     WarpState &S = WS.st;
 
     for (int i = threadIdx.x; i < M.E * M.K; i += blockDim.x) T.kappa[i] = M.kappa[i];
@@ -214,7 +221,7 @@ __global__ void __launch_bounds__(256, 3) walk_kernel(const __grid_constant__ Mo
 
     // per-lane walk state
     W w;
-    w.bind((uint32_t)__cvta_generic_to_shared(&WS.hist[0][lane]));
+    w.bind(&WS.hist[0][lane]);
     bool active = false;
     int item = 0;
     int model = 0;
@@ -239,14 +246,19 @@ __global__ void __launch_bounds__(256, 3) walk_kernel(const __grid_constant__ Mo
                 const int s = (head + ri) & (kRing - 1);
                 const uint32_t meta = R.meta[s];
                 const bool tr = (meta >> 6) & 1u;
-                uint32_t c[KMAX];
-                uint32_t rest = R.n[s];
+                typename W::Occ c[KMAX];
+                if constexpr (W::kStored == KMAX) {
 #pragma unroll
-                for (int j = 1; j < KMAX; ++j) {
-                    c[j] = R.cnt[j - 1][s];
-                    rest -= c[j];
+                    for (int j = 0; j < KMAX; ++j) c[j] = R.cnt[j][s];
+                } else {
+                    uint32_t rest = R.n[s];
+#pragma unroll
+                    for (int j = 1; j < KMAX; ++j) {
+                        c[j] = R.cnt[j - 1][s];
+                        rest -= c[j];
+                    }
+                    c[0] = rest;
                 }
-                c[0] = rest;
                 if (dump) {
                     if (my_e == 0) {
                         const int64_t o = (int64_t)(R.path[s] - A.items[0].path0);
@@ -255,7 +267,11 @@ __global__ void __launch_bounds__(256, 3) walk_kernel(const __grid_constant__ Mo
                         A.rec_steps[o] = (int64_t)R.n[s] + (tr ? 0 : 1);
 #pragma unroll
                         for (int j = 0; j < KMAX; ++j)
-                            if (j < M.K) A.rec_counts[o * M.K + j] = (int64_t)c[j];
+                            if (j < M.K) {
+                                if (A.rec_counts) A.rec_counts[o * M.K + j] = (int64_t)c[j];
+                                if (A.rec_occ) A.rec_occ[o * M.K + j] = (double)c[j];
+                            }
+                        if (A.rec_hits) A.rec_hits[o] = (int64_t)R.aux[s];
                         A.rec_exit[3 * o + 0] = ex;
                         A.rec_exit[3 * o + 1] = ez;
                         A.rec_exit[3 * o + 2] = (double)R.th[s];
@@ -372,10 +388,11 @@ __global__ void __launch_bounds__(256, 3) walk_kernel(const __grid_constant__ Mo
             R.item[slot] = item;
             R.n[slot] = ei.nocc;
             R.path[slot] = path;
-            uint32_t c[KMAX > 1 ? KMAX - 1 : 1];
+            R.aux[slot] = ei.aux;
+            typename W::Occ c[W::kStored];
             w.counts(c);
 #pragma unroll
-            for (int j = 1; j < KMAX; ++j) R.cnt[j - 1][slot] = c[j - 1];
+            for (int j = 0; j < W::kStored; ++j) R.cnt[j][slot] = c[j];
             S.steps[lane] += (unsigned long long)ei.nocc + (tr ? 0ull : 1ull);
             if (tr && !dump) atomicAdd(&A.item_trunc[item], 1);
         }

@@ -69,6 +69,21 @@ def uniform_model(kappa: float, g=("affine", 1.0, 0.0, 0.0)):
     return _model([[kappa]], g=g, bg=(0, 0))
 
 
+# ------------------------------------------------------------------ TM models
+# Vertical strips with their own diffusion D_m (TM mode): D_m Lap u = i kappa_m u.
+
+def tm_strips(diffusion, interfaces, kappa, g=("tm_flux",), domain=DOMAIN):
+    k = np.atleast_2d(np.asarray(kappa, dtype=np.float64))
+    return {"domain": domain, "kappa": k.tolist(), "diffusion": [float(d) for d in diffusion],
+            "interfaces": [float(x) for x in interfaces], "g": g}
+
+
+def tm_analytic():
+    """The analytic test model of Sec. 4.1: [-1,1]^2, D = 1 | 10 across x = 0,
+    lambda = 10i (kappa = -10), boundary data (z + 1) cosh(a x)."""
+    return tm_strips((1.0, 10.0), (0.0,), [[-10.0, -10.0]], g=("tm_cosh",), domain=(-1.0, 1.0, -1.0, 1.0))
+
+
 # ------------------------------------------------------------------ nodes
 
 def nodes_line(p0, p1, n):
@@ -120,6 +135,13 @@ def workload(name: str):
         return {"name": name, "model": triangle(),
                 "nodes": nodes_on_polygon(TRIANGLE, 128),
                 "n_paths": np.full(128, 1_000_000, dtype=np.int64), "dt": 1e-4, "seed": 4}
+    if name == "tm_analytic":
+        # the analytic test's 51 x 51 grid (interior points), 1e4 walks each
+        g = np.linspace(-1.0, 1.0, 51)[1:-1]
+        X, Z = np.meshgrid(g, g)
+        nodes = np.stack([X.ravel(), Z.ravel()], axis=1)
+        return {"name": name, "model": tm_analytic(), "nodes": nodes,
+                "n_paths": np.full(len(nodes), 10_000, dtype=np.int64), "dt": 1e-4, "seed": 6}
     raise KeyError(name)
 
 

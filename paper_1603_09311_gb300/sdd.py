@@ -10,6 +10,7 @@ The functions carry the names of the C entry points:
     sdd_interface_values(ctx, nodes, n_paths, dt, seed, ...)        host arrays
     sdd_interface_values_device(ctx, d_nodes, n_paths, dt, seed, d_mean, d_se, ...)
     sdd_walk_records(ctx, x0, z0, node_id, p0, count, dt, seed, ...)
+    sdd_walk_occupation(ctx, x0, z0, node_id, p0, count, dt, seed, ...)   TE and TM
     sdd_status_str(status), sdd_last_error()
 Models are the plain dicts of ``inputs.py``.
 """
@@ -55,6 +56,7 @@ class sdd_model_desc(ctypes.Structure):
         ("raster", ctypes.POINTER(ctypes.c_int8)), ("nx", ctypes.c_int32), ("nz", ctypes.c_int32),
         ("g_kind", ctypes.c_int32), ("g_left", ctypes.c_int32), ("g_right", ctypes.c_int32),
         ("g_coef", ctypes.c_double * 6),
+        ("diffusion", ctypes.POINTER(ctypes.c_double)), ("interfaces", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -140,6 +142,10 @@ SIGNATURES = [
      [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32,
       ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, P(sdd_config), P(ctypes.c_int64),
       P(ctypes.c_int64), P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_int32)]),
+    ("sdd_walk_occupation", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32,
+      ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, P(sdd_config), P(ctypes.c_int64),
+      P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int64)]),
     ("sdd_server_create", ctypes.c_int, [P(sdd_server_config), P(ctypes.c_void_p)]),
     ("sdd_server_destroy", None, [ctypes.c_void_p]),
     ("sdd_server_submit", ctypes.c_int, [ctypes.c_void_p, P(sdd_request_desc), P(ctypes.c_uint64)]),
@@ -218,8 +224,20 @@ def make_desc(model: dict):
             d.g_coef[j] = v
     elif g[0] == "x2mz2":
         d.g_kind = 2
+    elif g[0] == "tm_cosh":
+        d.g_kind = 3
+    elif g[0] == "tm_flux":
+        d.g_kind = 4
     else:
         raise ValueError(f"unknown g kind {g[0]}")
+    if "diffusion" in model:
+        # TM mode: strips of their own diffusion between vertical interfaces
+        dif = np.ascontiguousarray(np.asarray(model["diffusion"], dtype=np.float64))
+        xif = np.ascontiguousarray(np.asarray(list(model.get("interfaces", [])) + [0.0], dtype=np.float64))
+        keep += [dif, xif]
+        d.diffusion = _dp(dif)
+        d.interfaces = _dp(xif)
+        d.n_shapes = 0
     return d, keep
 
 
@@ -410,6 +428,29 @@ def sdd_walk_records(ctx: Context, x0: float, z0: float, node_id: int, p0: int, 
     if st != SDD_OK:
         raise SddError(st, "sdd_walk_records")
     return {"steps": steps, "counts": counts, "exit": ext, "wall": wall, "m_last": mlast,
+            "truncated": (wall < 0).astype(np.int32)}
+
+
+def sdd_walk_occupation(ctx: Context, x0: float, z0: float, node_id: int, p0: int, count: int,
+                        dt: float, seed: int, config: sdd_config | None = None, **cfg):
+    """Per-path records with occupation times (TE and TM models): steps,
+    occ [count][K] (units of dt), exit [count][3], wall, m_last, hits."""
+    steps = np.zeros(count, dtype=np.int64)
+    occ = np.zeros((count, ctx.K))
+    ext = np.zeros((count, 3))
+    wall = np.zeros(count, dtype=np.int32)
+    mlast = np.zeros(count, dtype=np.int32)
+    hits = np.zeros(count, dtype=np.int64)
+    c = config if config is not None else make_config(**cfg)
+    st = lib().sdd_walk_occupation(ctx.handle, float(x0), float(z0), int(node_id), int(p0), int(count),
+                                   float(dt), int(seed) & (2 ** 64 - 1), ctypes.byref(c),
+                                   steps.ctypes.data_as(P(ctypes.c_int64)), _dp(occ), _dp(ext),
+                                   wall.ctypes.data_as(P(ctypes.c_int32)),
+                                   mlast.ctypes.data_as(P(ctypes.c_int32)),
+                                   hits.ctypes.data_as(P(ctypes.c_int64)))
+    if st != SDD_OK:
+        raise SddError(st, "sdd_walk_occupation")
+    return {"steps": steps, "occ": occ, "exit": ext, "wall": wall, "m_last": mlast, "hits": hits,
             "truncated": (wall < 0).astype(np.int32)}
 
 
