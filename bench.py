@@ -42,6 +42,12 @@ METRIC = "walk-steps/s"
 # bridge filter (5), the vertical-contact material test (4), two occupation
 # power sums (2), step bookkeeping (2.5).
 INST_PER_STEP = 45
+# The same count for a step of the TM walk (strips of their own diffusion):
+# the TE step without the material test and the occupation power sums
+# (45 - 4 - 2), plus the interface tests (crossing compares 2, nearer
+# interface product and filter 4) and the occupation update in shared memory
+# (address and add, 2).
+TM_INST_PER_STEP = 47
 
 
 def traffic_per_launch():
@@ -290,6 +296,59 @@ def serving(sdd, n_requests: int, seed: int = 5):
             "small_requests": small_out}
 
 
+def tm_measure(sdd, torch, dev, peak_tinst, n_steps, cpu=True):
+    """The TM walk on the analytic test model's 51 x 51 grid (2401 nodes x 1e4
+    walks, dt 1e-4): walk-steps/s of the device entry point (CUDA events on the
+    launching stream, L2 flushed between launches), its issue roofline, and
+    the oracle on the host cores on a bounded sample."""
+    w = I.workload("tm_analytic")
+    n = len(w["nodes"])
+    ctx = sdd.sdd_create(w["model"])
+    d_nodes = torch.tensor(w["nodes"], dtype=torch.float64, device=dev)
+    d_mean = torch.empty((n, ctx.E, 2), dtype=torch.float64, device=dev)
+    d_se = torch.empty_like(d_mean)
+    d_cnt = torch.zeros((n_steps + 1, 3), dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def launch(k):
+        sdd.sdd_interface_values_device(ctx, d_nodes.data_ptr(), n, w["n_paths"], w["dt"], w["seed"] + k,
+                                        d_mean.data_ptr(), d_se.data_ptr(), d_counters_ptr=d_cnt[k].data_ptr(),
+                                        stream=stream.cuda_stream)
+
+    launch(n_steps)  # warm-up
+    torch.cuda.synchronize()
+    ms = []
+    for k in range(n_steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        launch(k)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    steps = d_cnt[:n_steps, 0].cpu().numpy().astype(float)
+    value = float(steps.sum() / (sum(ms) * 1e-3))
+    ctx.close()
+    out = {"metric": METRIC, "value": value, "unit": METRIC, "ms_per_launch": statistics.mean(ms),
+           "launches": n_steps, "steps_per_launch": float(steps.mean()),
+           "workload": "TM analytic test model: [-1,1]^2, D 1|10 across x=0, kappa -10 (lambda 10i), "
+                       "2401 nodes (51x51 grid interior) x 1e4 walks, dt 1e-4, FP32 walk",
+           "roofline": {"bound": "alu", "achieved": TM_INST_PER_STEP * value / 1e12, "peak": peak_tinst,
+                        "unit": "Tinst/s", "frac": TM_INST_PER_STEP * value / 1e12 / peak_tinst,
+                        "inst_per_step": TM_INST_PER_STEP}}
+    if cpu:
+        from oracle import oracle as O
+        idx = np.arange(0, n, 6)
+        t = time.perf_counter()
+        r = O.interface_values(w["model"], w["nodes"][idx], 1000, w["dt"], w["seed"], urule=23)
+        sec = time.perf_counter() - t
+        out["cpu_baseline"] = {"value": r["steps"] / sec, "unit": METRIC, "cores": O.max_threads(),
+                               "kind": "oracle", "sample": f"{len(idx)} of the nodes x 1000 walks "
+                                                           f"({r['steps']:.3e} steps, {sec:.1f} s)"}
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -488,6 +547,9 @@ def main():
         }
         if args.serve_requests > 0 and world == 1 and not args.small:
             line["serving"] = serving(sdd, args.serve_requests)
+        if world == 1 and not args.small:
+            line["tm"] = tm_measure(sdd, torch, dev, peak_tinst, max(1, min(args.steps, 3)),
+                                    cpu=not args.no_cpu_baseline)
         if not args.no_cpu_baseline and world == 1:
             cb = cpu_baseline(w)
             cb.pop("seconds", None)

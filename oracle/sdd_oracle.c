@@ -53,13 +53,18 @@
  * kappa_{e,m}, i.e. D_m Lap u = i kappa_{e,m} u, and the walk weight keeps
  * the form exp(-i (1/2) sum_m kappa_{e,m} T_m).  Per step, in strip i:
  *   1. beta' = beta + sqrt(D_i dt) W (the discretised-process equation).
- *   2. dOmega first: overshoot as in TE; bridge with kappa_i = D_i,
- *      2 d d' / (D_i dt) <= -ln U.
+ *   2. dOmega first: overshoot as in TE; else the bridge with kappa_i = D_i
+ *      for the wall of smallest w = 2 d d' / (D_i dt): hit iff U <= p_w,
+ *      p_w = exp(-w) (0 when w > 40), U the step's bridge uniform.
  *   3. Interfaces to a strip of other D only (equal D: no regime change).
  *      Crossed: hitting fraction |d / (beta'_x - beta_x)| (second case of the
- *      first-hitting-time equation).  Not crossed: the nearer interface of
- *      strip i (smallest 2 d d' / (D_i dt)) against -ln U_g, U_g a separate
- *      uniform (first case).  A hit at fraction th resumes on side i with
+ *      first-hitting-time equation).  Not crossed: the bridge (first case)
+ *      for the nearer such interface, g = 2 d d' / (D_i dt), with the
+ *      uniform U_g = (U - p_w) / (1 - p_w) that the wall test leaves
+ *      (uniform and independent of it given no wall hit): hit iff
+ *      U <= p_w + (1 - p_w) p_g, p_g = exp(-g), and t_g = g dt / (-ln U_g).
+ *      One uniform per step thus serves every barrier, as one serves all
+ *      walls in TE.  A hit at fraction th resumes on side i with
  *      probability p_i = D_i / (D_i + D_j) (crossing-probability equation),
  *      uniformly in the disc of radius h = sqrt(dt max(D_i, D_j)) centred at
  *      (x_g -/+ h, z_g), z_g the hit height, tangent to the interface.
@@ -77,8 +82,8 @@
  * equal D = the TE walk.  Parity unpinned: the occupation split of step 3
  * moves O(dt) per hit, below the resolution of every pin; it is checked only
  * by conservation of time and by path-by-path GPU equality.
- * The TM uniforms (U_g, U_alpha, disc radius, disc angle) are the four
- * words of the Philox call with counter (n, r, node, 2), by the urule.
+ * The TM uniforms U_alpha, disc radius and disc angle are words 1, 2, 3 of
+ * the Philox call with counter (n, r, node, 2), by the urule.
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -shared -fPIC.
  */
@@ -213,8 +218,8 @@ double orc_bridge_uniform(uint64_t seed, uint32_t node, uint32_t path, int64_t n
     return orc_uniform(x[0], urule);
 }
 
-/* The four TM uniforms of step n: U_g (interface bridge), U_alpha (side),
- * disc radius, disc angle, from the Philox call with counter (n, path, node, 2). */
+/* The four words of the TM Philox call of step n (counter (n, path, node, 2))
+ * as uniforms; words 1, 2, 3 are U_alpha (side), disc radius, disc angle. */
 void orc_tm_uniforms(uint64_t seed, uint32_t node, uint32_t path, int64_t n, int urule,
                      double U[4])
 {
@@ -462,8 +467,7 @@ void orc_walk_tm(const orc_model *m, double x0, double z0, uint32_t node, uint32
         double xn = x + s * w0;
         double zn = z + s * w1;
         double U = orc_bridge_uniform(seed, node, path, n, m->urule);
-        double theta, ex, ez;
-        int wall;
+        double ex, ez;
         double th = 2.0, xg = 0.0;
         int side = -1;
         double V[4];
@@ -480,12 +484,40 @@ void orc_walk_tm(const orc_model *m, double x0, double z0, uint32_t node, uint32
             xg = x;
         } else {
             /* 2. the outer boundary first, with the strip's diffusion */
-            if (orc_exit_rule(m, x, z, xn, zn, Di * dt, U, &theta, &wall, &ex, &ez)) {
+            double d[4], dn[4];
+            wall_dist(m, x, z, d);
+            wall_dist(m, xn, zn, dn);
+            int over = 0;
+            for (int w = 0; w < 4; ++w)
+                if (dn[w] <= 0.0) over = 1;
+            if (over) {
+                double best = INFINITY;
+                int bw = -1;
+                for (int w = 0; w < 4; ++w)
+                    if (dn[w] <= 0.0) {
+                        double t = d[w] / (d[w] - dn[w]);
+                        if (t < best) { best = t; bw = w; }
+                    }
                 rec->steps = n + 1;
-                rec->ex = ex;
-                rec->ez = ez;
-                rec->theta = theta;
-                rec->wall = wall;
+                place_on_wall(m, bw, x, z, xn, zn, best, &rec->ex, &rec->ez);
+                rec->theta = best;
+                rec->wall = bw;
+                rec->m_last = i;
+                return;
+            }
+            double wmin = INFINITY;
+            int bw = -1;
+            for (int w = 0; w < 4; ++w) {
+                double q = 2.0 * d[w] * dn[w] / (Di * dt);
+                if (q < wmin) { wmin = q; bw = w; }
+            }
+            double pw = wmin <= 40.0 ? exp(-wmin) : 0.0;
+            if (U <= pw) {
+                double th_w = wmin / -log(U);
+                rec->steps = n + 1;
+                place_on_wall(m, bw, x, z, xn, zn, th_w, &rec->ex, &rec->ez);
+                rec->theta = th_w;
+                rec->wall = bw;
                 rec->m_last = i;
                 return;
             }
@@ -500,19 +532,20 @@ void orc_walk_tm(const orc_model *m, double x0, double z0, uint32_t node, uint32
                     xg = xi;
                 }
             } else {
-                double best = INFINITY, bx = 0.0;
+                double g = INFINITY, bx = 0.0;
                 int bs = -1;
                 if (i > 0 && m->diff[i - 1] != Di) {
                     double e = 2.0 * (x - m->xif[i - 1]) * (xn - m->xif[i - 1]) / (Di * dt);
-                    if (e < best) { best = e; bs = i - 1; bx = m->xif[i - 1]; }
+                    if (e < g) { g = e; bs = i - 1; bx = m->xif[i - 1]; }
                 }
                 if (i < m->K - 1 && m->diff[i + 1] != Di) {
                     double e = 2.0 * (m->xif[i] - x) * (m->xif[i] - xn) / (Di * dt);
-                    if (e < best) { best = e; bs = i + 1; bx = m->xif[i]; }
+                    if (e < g) { g = e; bs = i + 1; bx = m->xif[i]; }
                 }
-                double L = -log(V[0]);
-                if (bs >= 0 && best <= L) {
-                    th = best / L;
+                double pg = (bs >= 0 && g <= 40.0) ? exp(-g) : 0.0;
+                if (pg > 0.0 && U <= pw + (1.0 - pw) * pg) {
+                    double Ug = (U - pw) / (1.0 - pw);
+                    th = g / -log(Ug);
                     side = bs;
                     xg = bx;
                 }

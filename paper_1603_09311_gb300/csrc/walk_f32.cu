@@ -469,7 +469,7 @@ static int occ_one(int block, int E, int K) {
 // The TM walk (vertical strips, K <= KMAX in {2, 3, 4, 8}).
 template <int KMAX>
 static cudaError_t launch_tm(const ModelDev &M, const WalkArgs &A, int grid, int block, cudaStream_t s) {
-    using W = WalkerTM<float, KMAX>;
+    using W = WalkerTM32<KMAX>;
     const size_t sm = shared_bytes<W>(block / 32, M.E, M.K);
     auto k = walk_kernel<W>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -480,7 +480,7 @@ static cudaError_t launch_tm(const ModelDev &M, const WalkArgs &A, int grid, int
 
 template <int KMAX>
 static int occ_tm(int block, int E, int K) {
-    using W = WalkerTM<float, KMAX>;
+    using W = WalkerTM32<KMAX>;
     const size_t sm = shared_bytes<W>(block / 32, E, K);
     auto k = walk_kernel<W>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)

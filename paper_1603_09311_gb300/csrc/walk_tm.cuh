@@ -6,10 +6,13 @@
 // equation per sub-domain).  One step from beta in strip i (Sec. 3.1):
 //   1. beta' = beta + sqrt(D_i dt) W (the discretised-process equation);
 //   2. the outer boundary first: overshoot, or the Brownian-bridge test with
-//      kappa_i = D_i, 2 d d' / (D_i dt) <= -ln U;
+//      kappa_i = D_i for the wall of smallest w = 2 d d' / (D_i dt): hit iff
+//      U <= p_w = exp(-w), U the step's bridge uniform;
 //   3. interfaces to a strip of other D (equal D: no regime change): crossed
 //      -> hitting fraction |d / (beta'_x - beta_x)|; not crossed -> the
-//      bridge test against the nearer interface with its own uniform U_g.
+//      bridge test for the nearer interface, g = 2 d d' / (D_i dt), with the
+//      uniform U_g = (U - p_w) / (1 - p_w) the wall test leaves: hit iff
+//      U <= p_w + (1 - p_w) exp(-g), at fraction g / (-ln U_g).
 //      A hit at fraction th resumes on side i with probability
 //      p_i = D_i / (D_i + D_j) (the crossing-probability equation), uniformly
 //      in the disc of radius h = sqrt(dt max(D_i, D_j)) tangent to the
@@ -19,9 +22,9 @@
 //      resampled point outside the domain ends the walk on the nearest wall.
 //   4. otherwise the step's time goes to the strip of beta'.
 // A walk that starts on an interface has hit it at time 0 (from the left).
-// Random numbers: the step's normals and wall-bridge uniform as in the TE
-// walk of the same precision; U_g, U_alpha and the disc's radius and angle
-// from the Philox call with counter (n, path, node, 2).
+// Random numbers: the step's normals and bridge uniform as in the TE walk of
+// the same precision; U_alpha and the disc's radius and angle from words
+// 1, 2, 3 of the Philox call with counter (n, path, node, 2).
 //
 // Real = double is the parity walk (absolute coordinates, the order of
 // operations of the definition, compiled without contraction); Real = float
@@ -169,13 +172,11 @@ struct WalkerTM {
                 const Real q = Real(2) * d[w] * e[w] / dtD;
                 if (bw < 0 || q < best) { best = q; bw = w; }
             }
-            if (best <= Real(40)) {  // -ln U <= 33 ln 2 for every uniform of either stream
-                const Real U = wall_uniform(A, wa, wb);
-                const Real L = -log(U);
-                if (best <= L) {
-                    place(M, xn, zn, best / L, bw, ei);
-                    return true;
-                }
+            const Real U = wall_uniform(A, wa, wb);
+            const Real pw = best <= Real(40) ? exp(-best) : Real(0);
+            if (U <= pw) {
+                place(M, xn, zn, best / -log(U), bw, ei);
+                return true;
             }
             // 3. the interfaces of strip i
             j = strip(M, xn);
@@ -201,14 +202,11 @@ struct WalkerTM {
                     const Real q = Real(2) * (xr - x) * (xr - xn) / dtD;
                     if (bs < 0 || q < bq) { bq = q; bs = i + 1; bx = xr; }
                 }
-                if (bs >= 0 && bq <= Real(40)) {
-                    const uint4 v = philox4x32_10(make_uint4(n, path_, nid, 2u), A.key0, A.key1);
-                    const Real L = -log(uni(v.x));
-                    if (bq <= L) {
-                        th = bq / L;
-                        side = bs;
-                        xg = bx;
-                    }
+                const Real pg = (bs >= 0 && bq <= Real(40)) ? exp(-bq) : Real(0);
+                if (pg > Real(0) && U <= pw + (Real(1) - pw) * pg) {
+                    th = bq / -log((U - pw) / (Real(1) - pw));
+                    side = bs;
+                    xg = bx;
                 }
             }
         }
@@ -361,6 +359,362 @@ struct WalkerTM {
         (void)wall;
         // (cw - i sw)(gr + i gi)
         return make_double2(cw * gr + sw * gi, cw * gi - sw * gr);
+    }
+};
+
+// Throughput form of the single-precision TM walk: the same steps on the
+// same stream as WalkerTM<float>, arranged like the TE walk.  Coordinates are
+// centred (X = x - xc); the strip's step scale sqrt(D_i dt), filter
+// thresholds and bounds live in registers and change only with the strip.
+// A step takes the short path unless its wall product d d' or its product
+// of distances to the strip's bounds comes within reach of a hit (or the
+// step crossed a bound); the long path decides exactly as WalkerTM does.
+// Whole steps in the current strip are counted in a register and added to
+// the lane's occupation times when the strip changes or the walk ends.
+template <int KMAX_>
+struct WalkerTM32 {
+    using Real = float;
+    static constexpr int KMAX = KMAX_;
+    static constexpr bool kCoop = false;
+    using Occ = float;
+    using HistT = float;
+    static constexpr int kStored = KMAX;
+    static constexpr int kHist = KMAX;
+    // one Philox call (two steps) per iteration: the long path is inlined at
+    // every step of an iteration, and more copies overflow the instruction
+    // cache (measured: 4 calls per iteration ran 4x slower)
+    static constexpr int PAIRS = 1;
+
+    float X, Z, dmin, dI;
+    int i;
+    uint32_t n, hits, run;
+    uint32_t nid, path_, pre_x, pre_y;
+    float s, wthr, c2, xl, xr, Di;
+    bool start_on_if;
+    float *h;
+
+    __device__ __forceinline__ void bind(HistT *p) { h = p; }
+
+    __device__ __forceinline__ static int strip(const ModelDev &M, float Xc) {
+        int k = 0;
+        while (k < M.K - 1 && Xc >= M.fxif[k] - M.fxc) ++k;
+        return k;
+    }
+    // the constants of strip i (bounds in centred coordinates)
+    __device__ __forceinline__ void enter(const ModelDev &M, const WalkArgs &A, int k) {
+        i = k;
+        Di = M.fdiff[k];
+        const float dtD = Di * (float)A.dt;
+        s = sqrtf(dtD);
+        // bands: out of both, p_w and p_g are below 2^-20 each, so no uniform
+        // (>= 2^-19) can hit either: 2 d d' / (D dt) > 20 ln 2 (with a margin)
+        wthr = 6.94f * 1.001f * dtD;
+        c2 = 2.f / dtD;
+        xl = k > 0 ? M.fxif[k - 1] - M.fxc : -3.0e38f;
+        xr = k < M.K - 1 ? M.fxif[k] - M.fxc : 3.0e38f;
+        dI = fminf(X - xl, xr - X);
+    }
+    __device__ __forceinline__ void flush() {
+        h[32 * i] += (float)run;
+        run = 0;
+    }
+
+    __device__ __forceinline__ void start(const ModelDev &M, const WalkArgs &A, double x0, double z0,
+                                          uint32_t path, uint32_t node_id, int) {
+        X = (float)x0 - M.fxc;
+        Z = (float)z0 - M.fzc;
+        dmin = fminf(M.fhw - fabsf(X), M.fhh - fabsf(Z));
+        const float xa = (float)x0;
+        int k = 0;
+        while (k < M.K - 1 && xa >= M.fxif[k]) ++k;
+        start_on_if = k > 0 && xa == M.fxif[k - 1] && M.fdiff[k - 1] != M.fdiff[k];
+        enter(M, A, k);
+        n = 0;
+        hits = 0;
+        run = 0;
+        nid = node_id;
+        path_ = path;
+        pre_x = __umulhi(0xCD9E8D57u, node_id) ^ path ^ A.rk0[0];
+        pre_y = 0xCD9E8D57u * node_id;
+#pragma unroll
+        for (int k2 = 0; k2 < KMAX; ++k2) h[32 * k2] = 0.f;
+    }
+
+    __device__ __forceinline__ void counts(Occ *c) const {
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) c[k] = h[32 * k];
+    }
+
+    __device__ __forceinline__ static float uni(uint32_t w) {
+        return ((float)(w & 0x7fffffu) + 0.5f) * (1.0f / 8388608.0f);
+    }
+    __device__ __forceinline__ static float bridge_u(uint32_t wa, uint32_t wb) {
+        return ((float)(((wa >> 23) << 9) | (wb >> 23)) + 0.5f) * (1.0f / 262144.0f);
+    }
+
+    __device__ __forceinline__ void exit_at(const ModelDev &M, ExitInfo<float> &ei, float ex, float ez,
+                                            float th, int wall, uint32_t k) {
+        flush();
+        ei.x = ex;
+        ei.z = ez;
+        ei.th = th;
+        ei.wall = wall;
+        ei.mlast = i;
+        ei.nocc = n + k;
+        ei.aux = hits;
+    }
+
+    // The long path of step n + k: the exact decisions of WalkerTM.
+    __device__ __forceinline__ bool rare(const ModelDev &M, const WalkArgs &A, float Xn, float Zn, uint32_t wa,
+                                      uint32_t wb, uint32_t k, ExitInfo<float> &ei) {
+        const uint32_t nk = n + k;
+        float th = 2.f, xg = 0.f;
+        int side = -1, j = i;
+        if (nk == 0 && start_on_if) {
+            flush();
+            enter(M, A, i - 1);
+            Xn = X;
+            Zn = Z;
+            th = 0.f;
+            side = i + 1;
+            xg = X;
+        } else {
+            const float d[4] = {X + M.fhw, M.fhw - X, Z + M.fhh, M.fhh - Z};
+            const float e[4] = {Xn + M.fhw, M.fhw - Xn, Zn + M.fhh, M.fhh - Zn};
+            if (e[0] <= 0.f || e[1] <= 0.f || e[2] <= 0.f || e[3] <= 0.f) {
+                float best = 3.f;
+                int bw = 0;
+#pragma unroll
+                for (int w = 0; w < 4; ++w)
+                    if (e[w] <= 0.f) {
+                        const float t = d[w] / (d[w] - e[w]);
+                        if (t < best) { best = t; bw = w; }
+                    }
+                place(M, Xn, Zn, best, bw, k, ei);
+                return true;
+            }
+            const float dtD = Di * (float)A.dt;
+            float best = 0.f;
+            int bw = -1;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const float q = 2.f * d[w] * e[w] / dtD;
+                if (bw < 0 || q < best) { best = q; bw = w; }
+            }
+            const float U = bridge_u(wa, wb);
+            const float pw = best <= 40.f ? __expf(-best) : 0.f;
+            if (U <= pw) {
+                place(M, Xn, Zn, best / -logf(U), bw, k, ei);
+                return true;
+            }
+            j = strip(M, Xn);
+            if (j != i) {
+                const int jn = j > i ? i + 1 : i - 1;
+                const float xi = j > i ? xr : xl;
+                if (M.fdiff[jn] != Di) {
+                    th = fabsf((X - xi) / (Xn - X));
+                    side = jn;
+                    xg = xi;
+                }
+            } else {
+                float bq = 0.f, bx = 0.f;
+                int bs = -1;
+                if (i > 0 && M.fdiff[i - 1] != Di) {
+                    bq = 2.f * (X - xl) * (Xn - xl) / dtD;
+                    bs = i - 1;
+                    bx = xl;
+                }
+                if (i < M.K - 1 && M.fdiff[i + 1] != Di) {
+                    const float q = 2.f * (xr - X) * (xr - Xn) / dtD;
+                    if (bs < 0 || q < bq) { bq = q; bs = i + 1; bx = xr; }
+                }
+                const float pg = (bs >= 0 && bq <= 40.f) ? __expf(-bq) : 0.f;
+                if (pg > 0.f && U <= pw + (1.f - pw) * pg) {
+                    th = bq / -logf((U - pw) / (1.f - pw));
+                    side = bs;
+                    xg = bx;
+                }
+            }
+            if (side >= 0) flush();
+        }
+        if (side >= 0) {
+            const uint4 v = philox_rk(make_uint4(nk, path_, nid, 2u), A.rk0, A.rk1);
+            const float Dj = M.fdiff[side];
+            const float pi_ = Di / (Di + Dj), pj = Dj / (Di + Dj);
+            const float zg = Z + th * (Zn - Z);
+            const float hh = sqrtf((float)A.dt * (Di > Dj ? Di : Dj));
+            const float c = X <= xg ? hh : -hh;
+            const float rest = 1.f - th;
+            float cx;
+            if (uni(v.y) < pi_) {
+                h[32 * i] += 1.f - 0.5f * rest * pi_;
+                h[32 * side] += 0.5f * rest * pi_;
+                cx = xg - c;
+            } else {
+                const float ti = th + 0.5f * rest * pj;
+                h[32 * i] += ti;
+                h[32 * side] += 1.f - ti;
+                cx = xg + c;
+            }
+            float sa, ca;
+            __sincosf(6.28318530718f * uni(v.w), &sa, &ca);
+            const float rho = hh * sqrtf(uni(v.z));
+            Xn = cx + rho * ca;
+            Zn = zg + rho * sa;
+            hits += 1;
+            const float e[4] = {Xn + M.fhw, M.fhw - Xn, Zn + M.fhh, M.fhh - Zn};
+            int bw = -1;
+            float most = 0.f;
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                if (e[w] <= most && (bw < 0 || e[w] < most)) { most = e[w]; bw = w; }
+            if (bw >= 0) {
+                float ex = fminf(fmaxf(Xn, -M.fhw), M.fhw), ez = fminf(fmaxf(Zn, -M.fhh), M.fhh);
+                if (bw == 0) ex = -M.fhw;
+                if (bw == 1) ex = M.fhw;
+                if (bw == 2) ez = -M.fhh;
+                if (bw == 3) ez = M.fhh;
+                exit_at(M, ei, ex, ez, 0.f, bw, k);
+                return true;
+            }
+            X = Xn;
+            Z = Zn;
+            dmin = fminf(M.fhw - fabsf(X), M.fhh - fabsf(Z));
+            enter(M, A, strip(M, X));
+            return false;
+        }
+        // no event: the step's time goes to the strip of beta'
+        if (j != i) {
+            flush();
+            X = Xn;
+            enter(M, A, j);
+        }
+        run += 1;
+        X = Xn;
+        Z = Zn;
+        dmin = fminf(M.fhw - fabsf(X), M.fhh - fabsf(Z));
+        dI = fminf(X - xl, xr - X);
+        return false;
+    }
+
+    __device__ __forceinline__ void place(const ModelDev &M, float Xn, float Zn, float th, int w, uint32_t k,
+                                          ExitInfo<float> &ei) {
+        float ex = fmaf(th, Xn - X, X), ez = fmaf(th, Zn - Z, Z);
+        if (w == 0) ex = -M.fhw;
+        if (w == 1) ex = M.fhw;
+        if (w == 2) ez = -M.fhh;
+        if (w == 3) ez = M.fhh;
+        exit_at(M, ei, ex, ez, th, w, k);
+    }
+
+    // One step: the short path, or the long one near a wall or a strip bound.
+    __device__ __forceinline__ bool substep(const ModelDev &M, const WalkArgs &A, uint32_t wa, uint32_t wb,
+                                            uint32_t k, ExitInfo<float> &ei) {
+        float sn, cs;
+        const float r = s * sqrtf(-2.f * __logf(uni(wa)));
+        __sincosf(6.28318530718f * uni(wb), &sn, &cs);
+        const float Xn = fmaf(r, cs, X);
+        const float Zn = fmaf(r, sn, Z);
+        const float dn = fminf(M.fhw - fabsf(Xn), M.fhh - fabsf(Zn));
+        const float dIn = fminf(Xn - xl, xr - Xn);
+        const float pn = dmin * dn, pI = dI * dIn;
+        if (pn <= wthr || pI <= wthr || (n + k == 0 && start_on_if)) {
+            // exact reject: every wall product is >= pn and every bound's
+            // product >= pI, so p_w + p_g <= exp(-c2 pn) + exp(-c2 pI)
+            if ((n + k != 0 || !start_on_if) &&
+                bridge_u(wa, wb) > __expf(-c2 * pn) + __expf(-c2 * pI)) {
+                run += 1;
+                X = Xn;
+                Z = Zn;
+                dmin = dn;
+                dI = dIn;
+                return false;
+            }
+            return rare(M, A, Xn, Zn, wa, wb, k, ei);
+        }
+        run += 1;
+        X = Xn;
+        Z = Zn;
+        dmin = dn;
+        dI = dIn;
+        return false;
+    }
+
+    // The steps of PAIRS Philox calls.  0 running, 1 exited, 2 truncated.
+    __device__ __forceinline__ int iterate(const ModelDev &M, const WalkArgs &A, uint32_t, ExitInfo<float> &ei) {
+        uint4 w[PAIRS];
+#pragma unroll
+        for (int q = 0; q < PAIRS; ++q) w[q] = philox_rk_pre((n >> 1) + q, 0u, pre_x, pre_y, A.rk0, A.rk1);
+        const uint32_t odd = n & 1u;  // 1 only right after a walk that started on an interface
+#pragma unroll
+        for (int q = 0; q < PAIRS; ++q) {
+            const uint32_t k0 = 2u * q - odd;
+            if ((q > 0 || !odd) && substep(M, A, w[q].x, w[q].y, k0, ei)) return 1;
+            if (substep(M, A, w[q].z, w[q].w, k0 + 1u, ei)) return 1;
+        }
+        n += 2 * PAIRS - odd;
+        if (n >= A.max_steps) {
+            exit_at(M, ei, X, Z, 0.f, 0, 0);
+            ei.nocc = n;
+            return 2;
+        }
+        return 0;
+    }
+
+    __device__ static void to_abs(const ModelDev &M, float Xc, float Zc, double &x, double &z) {
+        x = (double)Xc + M.xc;
+        z = (double)Zc + M.zc;
+    }
+
+    // The sample in single precision past the phase (FP64 is slow on this
+    // GPU): the phase sum in FP64, reduced mod 2 pi, then FP32 functions.
+    __device__ static double2 sample(const ModelDev &M, const SharedTables &T, const WalkArgs &A, int,
+                                     int e, float xe, float ze, float th, int, int mlast, const Occ *c) {
+        const double dt = A.dt;
+        const double *kap = T.kappa + e * M.K;
+        double ph = 0.0;
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+            if (k < M.K) ph = fma(kap[k], (double)c[k], ph);
+        ph = fma(kap[mlast], (double)th, ph);
+        ph *= 0.5 * dt;
+        const double q = rint(ph * 0.15915494309189535);
+        float sw, cw;
+        __sincosf((float)fma(-q, 6.283185307179586, ph), &sw, &cw);
+        const float x = xe + M.fxc, z = ze + M.fzc;
+        float gr, gi;
+        if (M.g_kind == 1) {
+            const double *a = M.g_coef;
+            gr = (float)(a[0] + a[2] * (double)x + a[4] * (double)z);
+            gi = (float)(a[1] + a[3] * (double)x + a[5] * (double)z);
+        } else if (M.g_kind == 2) {
+            gr = x * x - z * z;
+            gi = 0.f;
+        } else if (M.g_kind == 3) {
+            int s = 0;
+            while (s < M.K - 1 && x >= M.fxif[s]) ++s;
+            const float p = (float)M.tm_a[e][s][0] * x, qq = (float)M.tm_a[e][s][1] * x;
+            float sq, cq;
+            sincosf(qq, &sq, &cq);
+            const float ep = expf(p), em = expf(-p);
+            gr = (z + 1.f) * (0.5f * (ep + em) * cq);
+            gi = (z + 1.f) * (0.5f * (ep - em) * sq);
+        } else {
+            float u = 0.f, a = (float)M.xmin;
+            gr = 0.f;
+            for (int k = 0; k < M.K; ++k) {
+                const float b = k < M.K - 1 ? M.fxif[k] : (float)M.xmax;
+                if (x <= b) {
+                    gr = u + (x - a) / M.fdiff[k];
+                    break;
+                }
+                u += (b - a) / M.fdiff[k];
+                a = b;
+                gr = u;
+            }
+            gi = 0.f;
+        }
+        return make_double2((double)(cw * gr + sw * gi), (double)(cw * gi - sw * gr));
     }
 };
 
