@@ -368,9 +368,12 @@ struct WalkerTM {
 // thresholds and bounds live in registers and change only with the strip.
 // A step takes the short path unless its wall product d d' or its product
 // of distances to the strip's bounds comes within reach of a hit (or the
-// step crossed a bound); the long path decides exactly as WalkerTM does.
-// Whole steps in the current strip are counted in a register and added to
-// the lane's occupation times when the strip changes or the walk ends.
+// step crossed a bound); the long path decides exactly as WalkerTM does.  A
+// lane whose step needs the long path stops for the rest of the iteration;
+// the long path and the interface randomisation then run once for all such
+// lanes of the warp.  Whole steps in the current strip are counted in a
+// register and added to the lane's occupation times when the strip changes
+// or the walk ends.
 template <int KMAX_>
 struct WalkerTM32 {
     using Real = float;
@@ -380,10 +383,11 @@ struct WalkerTM32 {
     using HistT = float;
     static constexpr int kStored = KMAX;
     static constexpr int kHist = KMAX;
-    // one Philox call (two steps) per iteration: the long path is inlined at
-    // every step of an iteration, and more copies overflow the instruction
-    // cache (measured: 4 calls per iteration ran 4x slower)
-    static constexpr int PAIRS = 1;
+    // four Philox calls (8 steps) per iteration: the per-step code is the
+    // short path only (the long path and the events run once per iteration),
+    // so the iteration fits the instruction cache (measured: 1, 2, 4 calls ->
+    // 1.26e11, 1.50e11, 1.64e11 walk-steps/s on the analytic test model)
+    static constexpr int PAIRS = 4;
 
     float X, Z, dmin, dI;
     int i;
@@ -452,164 +456,182 @@ struct WalkerTM32 {
         return ((float)(((wa >> 23) << 9) | (wb >> 23)) + 0.5f) * (1.0f / 262144.0f);
     }
 
+    // the walk ends at step nk (its steps before the exiting one: nk)
     __device__ __forceinline__ void exit_at(const ModelDev &M, ExitInfo<float> &ei, float ex, float ez,
-                                            float th, int wall, uint32_t k) {
+                                            float th, int wall, uint32_t nk) {
         flush();
         ei.x = ex;
         ei.z = ez;
         ei.th = th;
         ei.wall = wall;
         ei.mlast = i;
-        ei.nocc = n + k;
+        ei.nocc = nk;
         ei.aux = hits;
     }
 
+    // A step that needs the long path (its proposed point and Philox words),
+    // and a step that hit an interface (hit fraction, interface, side beyond
+    // it).  Both wait until the end of the iteration, where every lane of the
+    // warp that has one runs it together: the per-step code stays short.
+    float pXn, pZn, pth, pxg;
+    uint32_t pwa, pwb;
+    int pside;
+
     // The long path of step n + k: the exact decisions of WalkerTM.
-    __device__ __forceinline__ bool rare(const ModelDev &M, const WalkArgs &A, float Xn, float Zn, uint32_t wa,
-                                      uint32_t wb, uint32_t k, ExitInfo<float> &ei) {
+    // 0 no event, 1 exited, 2 interface hit (pending).
+    __device__ __forceinline__ int rare(const ModelDev &M, const WalkArgs &A, float Xn, float Zn, uint32_t wa,
+                                        uint32_t wb, uint32_t k, ExitInfo<float> &ei) {
         const uint32_t nk = n + k;
-        float th = 2.f, xg = 0.f;
-        int side = -1, j = i;
         if (nk == 0 && start_on_if) {
             flush();
             enter(M, A, i - 1);
-            Xn = X;
-            Zn = Z;
-            th = 0.f;
-            side = i + 1;
-            xg = X;
-        } else {
-            const float d[4] = {X + M.fhw, M.fhw - X, Z + M.fhh, M.fhh - Z};
-            const float e[4] = {Xn + M.fhw, M.fhw - Xn, Zn + M.fhh, M.fhh - Zn};
-            if (e[0] <= 0.f || e[1] <= 0.f || e[2] <= 0.f || e[3] <= 0.f) {
-                float best = 3.f;
-                int bw = 0;
-#pragma unroll
-                for (int w = 0; w < 4; ++w)
-                    if (e[w] <= 0.f) {
-                        const float t = d[w] / (d[w] - e[w]);
-                        if (t < best) { best = t; bw = w; }
-                    }
-                place(M, Xn, Zn, best, bw, k, ei);
-                return true;
-            }
-            const float dtD = Di * (float)A.dt;
-            float best = 0.f;
-            int bw = -1;
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                const float q = 2.f * d[w] * e[w] / dtD;
-                if (bw < 0 || q < best) { best = q; bw = w; }
-            }
-            const float U = bridge_u(wa, wb);
-            const float pw = best <= 40.f ? __expf(-best) : 0.f;
-            if (U <= pw) {
-                place(M, Xn, Zn, best / -logf(U), bw, k, ei);
-                return true;
-            }
-            j = strip(M, Xn);
-            if (j != i) {
-                const int jn = j > i ? i + 1 : i - 1;
-                const float xi = j > i ? xr : xl;
-                if (M.fdiff[jn] != Di) {
-                    th = fabsf((X - xi) / (Xn - X));
-                    side = jn;
-                    xg = xi;
-                }
-            } else {
-                float bq = 0.f, bx = 0.f;
-                int bs = -1;
-                if (i > 0 && M.fdiff[i - 1] != Di) {
-                    bq = 2.f * (X - xl) * (Xn - xl) / dtD;
-                    bs = i - 1;
-                    bx = xl;
-                }
-                if (i < M.K - 1 && M.fdiff[i + 1] != Di) {
-                    const float q = 2.f * (xr - X) * (xr - Xn) / dtD;
-                    if (bs < 0 || q < bq) { bq = q; bs = i + 1; bx = xr; }
-                }
-                const float pg = (bs >= 0 && bq <= 40.f) ? __expf(-bq) : 0.f;
-                if (pg > 0.f && U <= pw + (1.f - pw) * pg) {
-                    th = bq / -logf((U - pw) / (1.f - pw));
-                    side = bs;
-                    xg = bx;
-                }
-            }
-            if (side >= 0) flush();
+            pXn = X;
+            pZn = Z;
+            pth = 0.f;
+            pside = i + 1;
+            pxg = X;
+            return 2;
         }
-        if (side >= 0) {
-            const uint4 v = philox_rk(make_uint4(nk, path_, nid, 2u), A.rk0, A.rk1);
-            const float Dj = M.fdiff[side];
-            const float pi_ = Di / (Di + Dj), pj = Dj / (Di + Dj);
-            const float zg = Z + th * (Zn - Z);
-            const float hh = sqrtf((float)A.dt * (Di > Dj ? Di : Dj));
-            const float c = X <= xg ? hh : -hh;
-            const float rest = 1.f - th;
-            float cx;
-            if (uni(v.y) < pi_) {
-                h[32 * i] += 1.f - 0.5f * rest * pi_;
-                h[32 * side] += 0.5f * rest * pi_;
-                cx = xg - c;
-            } else {
-                const float ti = th + 0.5f * rest * pj;
-                h[32 * i] += ti;
-                h[32 * side] += 1.f - ti;
-                cx = xg + c;
-            }
-            float sa, ca;
-            __sincosf(6.28318530718f * uni(v.w), &sa, &ca);
-            const float rho = hh * sqrtf(uni(v.z));
-            Xn = cx + rho * ca;
-            Zn = zg + rho * sa;
-            hits += 1;
-            const float e[4] = {Xn + M.fhw, M.fhw - Xn, Zn + M.fhh, M.fhh - Zn};
-            int bw = -1;
-            float most = 0.f;
+        const float d[4] = {X + M.fhw, M.fhw - X, Z + M.fhh, M.fhh - Z};
+        const float e[4] = {Xn + M.fhw, M.fhw - Xn, Zn + M.fhh, M.fhh - Zn};
+        if (e[0] <= 0.f || e[1] <= 0.f || e[2] <= 0.f || e[3] <= 0.f) {
+            float best = 3.f;
+            int bw = 0;
 #pragma unroll
             for (int w = 0; w < 4; ++w)
-                if (e[w] <= most && (bw < 0 || e[w] < most)) { most = e[w]; bw = w; }
-            if (bw >= 0) {
-                float ex = fminf(fmaxf(Xn, -M.fhw), M.fhw), ez = fminf(fmaxf(Zn, -M.fhh), M.fhh);
-                if (bw == 0) ex = -M.fhw;
-                if (bw == 1) ex = M.fhw;
-                if (bw == 2) ez = -M.fhh;
-                if (bw == 3) ez = M.fhh;
-                exit_at(M, ei, ex, ez, 0.f, bw, k);
-                return true;
-            }
-            X = Xn;
-            Z = Zn;
-            dmin = fminf(M.fhw - fabsf(X), M.fhh - fabsf(Z));
-            enter(M, A, strip(M, X));
-            return false;
+                if (e[w] <= 0.f) {
+                    const float t = d[w] / (d[w] - e[w]);
+                    if (t < best) { best = t; bw = w; }
+                }
+            place(M, Xn, Zn, best, bw, nk, ei);
+            return 1;
         }
-        // no event: the step's time goes to the strip of beta'
+        const float dtD = Di * (float)A.dt;
+        float best = 0.f;
+        int bw = -1;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const float q = 2.f * d[w] * e[w] / dtD;
+            if (bw < 0 || q < best) { best = q; bw = w; }
+        }
+        const float U = bridge_u(wa, wb);
+        const float pw = best <= 40.f ? __expf(-best) : 0.f;
+        if (U <= pw) {
+            place(M, Xn, Zn, best / -logf(U), bw, nk, ei);
+            return 1;
+        }
+        const int j = strip(M, Xn);
         if (j != i) {
+            const int jn = j > i ? i + 1 : i - 1;
+            const float xi = j > i ? xr : xl;
+            if (M.fdiff[jn] != Di) {
+                flush();
+                pXn = Xn;
+                pZn = Zn;
+                pth = fabsf((X - xi) / (Xn - X));
+                pside = jn;
+                pxg = xi;
+                return 2;
+            }
+            // no regime change: the step's time goes to the strip of beta'
             flush();
             X = Xn;
             enter(M, A, j);
+        } else {
+            float bq = 0.f, bx = 0.f;
+            int bs = -1;
+            if (i > 0 && M.fdiff[i - 1] != Di) {
+                bq = 2.f * (X - xl) * (Xn - xl) / dtD;
+                bs = i - 1;
+                bx = xl;
+            }
+            if (i < M.K - 1 && M.fdiff[i + 1] != Di) {
+                const float q = 2.f * (xr - X) * (xr - Xn) / dtD;
+                if (bs < 0 || q < bq) { bq = q; bs = i + 1; bx = xr; }
+            }
+            const float pg = (bs >= 0 && bq <= 40.f) ? __expf(-bq) : 0.f;
+            if (pg > 0.f && U <= pw + (1.f - pw) * pg) {
+                flush();
+                pXn = Xn;
+                pZn = Zn;
+                pth = bq / -logf((U - pw) / (1.f - pw));
+                pside = bs;
+                pxg = bx;
+                return 2;
+            }
         }
         run += 1;
         X = Xn;
         Z = Zn;
         dmin = fminf(M.fhw - fabsf(X), M.fhh - fabsf(Z));
         dI = fminf(X - xl, xr - X);
+        return 0;
+    }
+
+    // The randomisation of a pending hit of step nk (crossing probability,
+    // disc point, time split).  Returns true when the resampled point left
+    // the domain (the walk ends on the nearest wall).
+    __device__ __forceinline__ bool event(const ModelDev &M, const WalkArgs &A, uint32_t nk, ExitInfo<float> &ei) {
+        const uint4 v = philox_rk(make_uint4(nk, path_, nid, 2u), A.rk0, A.rk1);
+        const float Dj = M.fdiff[pside];
+        const float pi_ = Di / (Di + Dj), pj = Dj / (Di + Dj);
+        const float zg = Z + pth * (pZn - Z);
+        const float hh = sqrtf((float)A.dt * (Di > Dj ? Di : Dj));
+        const float c = X <= pxg ? hh : -hh;
+        const float rest = 1.f - pth;
+        float cx;
+        if (uni(v.y) < pi_) {
+            h[32 * i] += 1.f - 0.5f * rest * pi_;
+            h[32 * pside] += 0.5f * rest * pi_;
+            cx = pxg - c;
+        } else {
+            const float ti = pth + 0.5f * rest * pj;
+            h[32 * i] += ti;
+            h[32 * pside] += 1.f - ti;
+            cx = pxg + c;
+        }
+        float sa, ca;
+        __sincosf(6.28318530718f * uni(v.w), &sa, &ca);
+        const float rho = hh * sqrtf(uni(v.z));
+        const float Xn = cx + rho * ca;
+        const float Zn = zg + rho * sa;
+        hits += 1;
+        const float e[4] = {Xn + M.fhw, M.fhw - Xn, Zn + M.fhh, M.fhh - Zn};
+        int bw = -1;
+        float most = 0.f;
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+            if (e[w] <= most && (bw < 0 || e[w] < most)) { most = e[w]; bw = w; }
+        if (bw >= 0) {
+            float ex = fminf(fmaxf(Xn, -M.fhw), M.fhw), ez = fminf(fmaxf(Zn, -M.fhh), M.fhh);
+            if (bw == 0) ex = -M.fhw;
+            if (bw == 1) ex = M.fhw;
+            if (bw == 2) ez = -M.fhh;
+            if (bw == 3) ez = M.fhh;
+            exit_at(M, ei, ex, ez, 0.f, bw, nk);
+            return true;
+        }
+        X = Xn;
+        Z = Zn;
+        dmin = fminf(M.fhw - fabsf(X), M.fhh - fabsf(Z));
+        enter(M, A, strip(M, X));
         return false;
     }
 
-    __device__ __forceinline__ void place(const ModelDev &M, float Xn, float Zn, float th, int w, uint32_t k,
+    __device__ __forceinline__ void place(const ModelDev &M, float Xn, float Zn, float th, int w, uint32_t nk,
                                           ExitInfo<float> &ei) {
         float ex = fmaf(th, Xn - X, X), ez = fmaf(th, Zn - Z, Z);
         if (w == 0) ex = -M.fhw;
         if (w == 1) ex = M.fhw;
         if (w == 2) ez = -M.fhh;
         if (w == 3) ez = M.fhh;
-        exit_at(M, ei, ex, ez, th, w, k);
+        exit_at(M, ei, ex, ez, th, w, nk);
     }
 
-    // One step: the short path, or the long one near a wall or a strip bound.
-    __device__ __forceinline__ bool substep(const ModelDev &M, const WalkArgs &A, uint32_t wa, uint32_t wb,
-                                            uint32_t k, ExitInfo<float> &ei) {
+    // One step: the short path, or 3 when the long one is needed (the step
+    // is recorded and left for the end of the iteration).
+    __device__ __forceinline__ int substep(const ModelDev &M, const WalkArgs &A, uint32_t wa, uint32_t wb,
+                                           uint32_t k, ExitInfo<float> &ei) {
         float sn, cs;
         const float r = s * sqrtf(-2.f * __logf(uni(wa)));
         __sincosf(6.28318530718f * uni(wb), &sn, &cs);
@@ -618,41 +640,54 @@ struct WalkerTM32 {
         const float dn = fminf(M.fhw - fabsf(Xn), M.fhh - fabsf(Zn));
         const float dIn = fminf(Xn - xl, xr - Xn);
         const float pn = dmin * dn, pI = dI * dIn;
-        if (pn <= wthr || pI <= wthr || (n + k == 0 && start_on_if)) {
+        const bool first = n + k == 0 && start_on_if;
+        if (pn <= wthr || pI <= wthr || first) {
             // exact reject: every wall product is >= pn and every bound's
             // product >= pI, so p_w + p_g <= exp(-c2 pn) + exp(-c2 pI)
-            if ((n + k != 0 || !start_on_if) &&
-                bridge_u(wa, wb) > __expf(-c2 * pn) + __expf(-c2 * pI)) {
-                run += 1;
-                X = Xn;
-                Z = Zn;
-                dmin = dn;
-                dI = dIn;
-                return false;
+            if (first || bridge_u(wa, wb) <= __expf(-c2 * pn) + __expf(-c2 * pI)) {
+                pXn = Xn;
+                pZn = Zn;
+                pwa = wa;
+                pwb = wb;
+                return 3;
             }
-            return rare(M, A, Xn, Zn, wa, wb, k, ei);
         }
         run += 1;
         X = Xn;
         Z = Zn;
         dmin = dn;
         dI = dIn;
-        return false;
+        return 0;
     }
 
-    // The steps of PAIRS Philox calls.  0 running, 1 exited, 2 truncated.
+    // The steps of PAIRS Philox calls (fewer at max_steps), a lane stopping at
+    // its first step that needs the long path; then the long path and the
+    // interface events of the warp's lanes, once.  0 running, 1 exited,
+    // 2 truncated.
     __device__ __forceinline__ int iterate(const ModelDev &M, const WalkArgs &A, uint32_t, ExitInfo<float> &ei) {
         uint4 w[PAIRS];
 #pragma unroll
         for (int q = 0; q < PAIRS; ++q) w[q] = philox_rk_pre((n >> 1) + q, 0u, pre_x, pre_y, A.rk0, A.rk1);
-        const uint32_t odd = n & 1u;  // 1 only right after a walk that started on an interface
+        const uint32_t odd = n & 1u;
+        const uint32_t lim = min((uint32_t)(2 * PAIRS) - odd, A.max_steps - n);
+        int st = 0;
+        uint32_t done = 0;
 #pragma unroll
         for (int q = 0; q < PAIRS; ++q) {
-            const uint32_t k0 = 2u * q - odd;
-            if ((q > 0 || !odd) && substep(M, A, w[q].x, w[q].y, k0, ei)) return 1;
-            if (substep(M, A, w[q].z, w[q].w, k0 + 1u, ei)) return 1;
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                if (q == 0 && hh == 0 && odd) continue;
+                const uint32_t k = 2u * q + hh - odd;
+                if (st == 0 && k < lim) {
+                    st = substep(M, A, hh ? w[q].z : w[q].x, hh ? w[q].w : w[q].y, k, ei);
+                    done = k + 1;
+                }
+            }
         }
-        n += 2 * PAIRS - odd;
+        if (st == 3) st = rare(M, A, pXn, pZn, pwa, pwb, done - 1, ei);
+        if (st == 1) return 1;
+        if (st == 2 && event(M, A, n + done - 1, ei)) return 1;
+        n += done;
         if (n >= A.max_steps) {
             exit_at(M, ei, X, Z, 0.f, 0, 0);
             ei.nocc = n;
