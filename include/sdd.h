@@ -253,16 +253,17 @@ sdd_status sdd_batch_values(const sdd_batch_entry *entries, int32_t n_entries, d
                             uint64_t seed, const sdd_config *cfg, sdd_stats *stats);
 
 /* Pick the launch shape for a workload by timing it: threads per CTA in
- * {128, 192, 256} x work items per warp in {2, 4, 6, 10, 16} (which sets the
- * paths per work item), two runs each of sdd_interface_values on the given
- * nodes.  The fastest shape is kept in the context and used by later calls
- * whose block_threads and chunk_paths are automatic; with the environment
- * variable SDD_TUNE_CACHE naming a file, it is also appended there and read
- * by new contexts with the same device, lookup program, materials bound,
- * evaluations, precision and decade of dt.
- *   base   options whose block_threads and chunk_paths are 0, or NULL
- *   best   out (nullable): base with the chosen block_threads and the
- *          chunk_paths they give for this workload
+ * {128, 192, 256} x guided factor in {1, 2, 4, 8} (which sets the sizes of
+ * the work items), two runs each of sdd_interface_values on the given nodes.
+ * The fastest shape is kept in the context and used by later calls whose
+ * block_threads, chunk_paths and guided_factor are automatic; with the
+ * environment variable SDD_TUNE_CACHE naming a file, it is also appended
+ * there and read by new contexts with the same device, lookup program,
+ * materials bound, evaluations, precision and decade of dt.
+ *   base   options whose block_threads, chunk_paths and guided_factor are 0,
+ *          or NULL
+ *   best   out (nullable): base with the chosen block_threads and
+ *          guided_factor (chunk_paths 0: guided items)
  *   best_steps_per_s  out (nullable): walk-steps/s of the chosen shape
  * Library-level design choice: the paper has no launch shapes. */
 sdd_status sdd_autotune(sdd_ctx *ctx, const double *nodes_xz, int32_t n_nodes,
