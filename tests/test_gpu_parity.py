@@ -422,3 +422,37 @@ def test_autotune_keeps_results_and_caches_the_shape(tmp_path, monkeypatch):
     fresh = sdd.sdd_create(w["model"])  # reads the cached shape
     _, _, st2 = sdd.sdd_interface_values(fresh, w["nodes"], w["n_paths"], w["dt"], 5)
     assert st2["block"] == cfg["block_threads"]
+
+
+def test_limits_32_evaluations_8_materials_many_nodes():
+    # the largest tables (E = 32 evaluations x K = 8 materials; one lane per
+    # evaluation in the sample pass) in both precisions, and a plan of 3000
+    # nodes with 1..9 walks each (many tiny work items)
+    base = _many_materials()
+    rng = np.random.default_rng(17)
+    kap = np.concatenate([np.array(base["kappa"]) * s for s in np.logspace(-1, 1.5, 32)])
+    model = dict(base, kappa=kap)
+    nodes = np.array([[0.0, 0.45], [-0.55, 0.6], [0.3, 0.1]])
+    n_paths = np.array([700, 33, 2049])
+    ctx = sdd.sdd_create(model)
+    assert ctx.E == 32 and ctx.K == 8
+    m64, _, st = sdd.sdd_interface_values(ctx, nodes, n_paths, 1e-3, 12, precision="fp64")
+    r64 = O.interface_values(model, nodes, n_paths, 1e-3, 12, urule=32)
+    tol = FP64_REL * _gmax(model)
+    assert m64.shape == (3, 32)
+    assert np.allclose(m64.real, r64["mean"].real, rtol=0, atol=tol)
+    assert np.allclose(m64.imag, r64["mean"].imag, rtol=0, atol=tol)
+    m32, s32, _ = sdd.sdd_interface_values(ctx, nodes, n_paths, 1e-3, 12)
+    r32 = O.interface_values(model, nodes, n_paths, 1e-3, 12, urule=23)
+    t32 = FP32_NSE * np.sqrt(s32 ** 2 + r32["se"] ** 2) + FP32_ABS
+    d = m32 - r32["mean"]
+    assert np.all(np.abs(d.real) <= t32[..., 0]) and np.all(np.abs(d.imag) <= t32[..., 1])
+    many = np.stack([rng.uniform(-0.9, 0.9, 3000), rng.uniform(-0.4, 0.9, 3000)], axis=1)
+    small = rng.integers(1, 10, 3000)
+    mm, ss, st2 = sdd.sdd_interface_values(ctx, many, small, 1e-3, 13)
+    assert st2["walks"] == small.sum() and np.all(np.isfinite(mm))
+    # a node computed alone under its node id in the big call equals its value there
+    for j in (0, 1234, 2999):
+        one, _, _ = sdd.sdd_interface_values(ctx, many[j:j + 1], small[j:j + 1], 1e-3, 13,
+                                             node_ids=np.array([j], dtype=np.uint32))
+        assert np.allclose(one, mm[j:j + 1], rtol=0, atol=1e-12 * max(1.0, np.abs(mm).max()))
