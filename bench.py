@@ -349,6 +349,75 @@ def tm_measure(sdd, torch, dev, peak_tinst, n_steps, cpu=True):
     return out
 
 
+def interp_measure(sdd, reps=3, cpu=True):
+    """Interpolation along an interface (Sec. 5): the quarter-space line of 64
+    nodes at 1e5 walks per walked node, walks at every 4th node and the last
+    (17 of 64), the others interpolated in arc length; against walks at all 64
+    nodes.  Host-buffer calls timed end to end (wall clock, best of reps), the
+    interpolation kernels by CUDA events inside the call.  The deviation of
+    an interpolated node from its own walks is given in units of their
+    combined standard error."""
+    w = I.workload("quarterspace")
+    nodes, n = w["nodes"], len(w["nodes"])
+    stride, paths = 4, int(w["n_paths"][0])
+    knots = list(range(0, n, stride))
+    if knots[-1] != n - 1:
+        knots.append(n - 1)
+    ctx = sdd.sdd_create(w["model"])
+    ids = np.arange(n, dtype=np.uint32)
+
+    def best(f):
+        out, t_best = None, float("inf")
+        for _ in range(reps):
+            t = time.perf_counter()
+            r = f()
+            t_best = min(t_best, time.perf_counter() - t)
+            out = r
+        return out, t_best
+
+    sdd.sdd_interface_values(ctx, nodes, paths, w["dt"], w["seed"], node_ids=ids)  # warm-up
+    (full, fse, fst), t_full = best(lambda: sdd.sdd_interface_values(ctx, nodes, paths, w["dt"], w["seed"],
+                                                                     node_ids=ids))
+    skip = np.setdiff1d(np.arange(n), knots)
+    out = {"workload": (f"quarterspace line: {n} nodes on x=0, z in [0,0.9], {paths} walks per walked "
+                        f"node, dt 1e-4; walks at every {stride}th node and the last ({len(knots)} of {n}), "
+                        "the others interpolated in arc length"),
+           "unit": "interface-node values/s", "full": {"value": n / t_full, "ms": 1e3 * t_full,
+                                                      "walk_kernel_ms": fst["kernel_ms"]}}
+    for name, kind in (("spline", sdd.SDD_INTERP_SPLINE), ("linear", sdd.SDD_INTERP_LINEAR)):
+        sdd.sdd_interface_values_interp(ctx, nodes, stride, paths, kind, w["dt"], w["seed"])
+        (m, se, st), t = best(lambda: sdd.sdd_interface_values_interp(ctx, nodes, stride, paths, kind,
+                                                                      w["dt"], w["seed"]))
+        zr = np.abs(m[skip].real - full[skip].real) / np.sqrt(se[skip, :, 0] ** 2 + fse[skip, :, 0] ** 2)
+        zi = np.abs(m[skip].imag - full[skip].imag) / np.sqrt(se[skip, :, 1] ** 2 + fse[skip, :, 1] ** 2)
+        z = np.concatenate([zr.ravel(), zi.ravel()])
+        out[name] = {"value": n / t, "ms": 1e3 * t, "speedup": t_full / t, "walks": int(st["walks"]),
+                     "walk_kernel_ms": st["kernel_ms"], "interp_kernel_ms": st["interp_ms"],
+                     "interp_launches": int(st["launches"]) - 2,
+                     "max_dev_in_se": float(z.max()), "rms_dev_in_se": float(np.sqrt((z ** 2).mean()))}
+    out["value"] = out["spline"]["value"]
+    out["roofline"] = {"bound": "latency",
+                       "note": "the interpolation kernels move a few KB in a few launches of microseconds; "
+                               "the walks at the knots are the time, bounded as the main line's kernel"}
+    ctx.close()
+    if cpu:
+        from oracle import interp as OI
+        s = OI.arc_length(nodes)
+        kv = np.stack([full[knots].real, full[knots].imag], axis=-1).reshape(len(knots), -1)
+        ke = fse[knots].reshape(len(knots), -1)
+        t = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t < 1.0:
+            OI.interpolate(s[knots], kv, ke, s, OI.SPLINE)
+            k += 1
+        sec = (time.perf_counter() - t) / k
+        out["cpu_baseline"] = {"value": n / sec, "unit": "interface-node values/s (interpolation only)",
+                               "cores": 1, "kind": "oracle",
+                               "sample": f"the spline interpolation of the {len(knots)} knots to {n} nodes, "
+                                         f"{k} repetitions ({1e3 * sec:.2f} ms each)"}
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -550,6 +619,8 @@ def main():
         if world == 1 and not args.small:
             line["tm"] = tm_measure(sdd, torch, dev, peak_tinst, max(1, min(args.steps, 3)),
                                     cpu=not args.no_cpu_baseline)
+        if world == 1 and not args.small:
+            line["interp"] = interp_measure(sdd, cpu=not args.no_cpu_baseline)
         if not args.no_cpu_baseline and world == 1:
             cb = cpu_baseline(w)
             cb.pop("seconds", None)

@@ -161,6 +161,8 @@ typedef struct {
     int32_t block;       /* threads per CTA */
     uint64_t h2d_bytes;  /* host-to-device bytes copied by the call */
     uint64_t d2h_bytes;  /* device-to-host bytes copied by the call */
+    double interp_ms;    /* device time of the interpolation kernels (CUDA events;
+                            sdd_interface_values_interp, 0 elsewhere) */
 } sdd_stats;
 
 /* Create a context on the current CUDA device and copy the model to it.
@@ -331,6 +333,69 @@ sdd_status sdd_interface_values_noalloc(sdd_ctx *ctx, const double *d_nodes_xz,
                                         const int64_t *n_paths, double dt, uint64_t seed,
                                         const sdd_config *cfg, double *d_mean, double *d_se,
                                         uint64_t *d_counters, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Interpolation along an interface (Sec. 5: the stochastic solution is
+ * computed at some points of an interface only and the other interface
+ * values are interpolated).  The paper names the idea and gives no scheme;
+ * the one implemented here is:
+ *  - the nodes of one interface are an ordered polyline p_0 .. p_{n-1} and
+ *    the interpolation variable is its arc length s_i = sum_{k<i} |p_{k+1} - p_k|;
+ *  - each real component (re and im of each evaluation) is interpolated on
+ *    its own, piecewise linearly in s (SDD_INTERP_LINEAR) or by the natural
+ *    cubic spline in s, second derivative zero at both end knots
+ *    (SDD_INTERP_SPLINE);
+ *  - both interpolants are linear in the knot values, v(s) = sum_j c_j(s) v_j,
+ *    and the knots' estimates are independent, so the standard error given
+ *    at s is sqrt(sum_j c_j(s)^2 se_j^2): the Monte Carlo part of the error,
+ *    not the interpolation error.
+ * Both entry points run on the current CUDA device in FP64, allocate their
+ * own device scratch and return when the results are in the host arrays. */
+#define SDD_INTERP_LINEAR 0
+#define SDD_INTERP_SPLINE 1
+#define SDD_INTERP_MAX_SPLINE_KNOTS 4096 /* the spline keeps an n x n FP64 table */
+#define SDD_INTERP_MAX_NODES (1 << 20)
+
+/* Interpolate knot data to target arc lengths.
+ *   knots_s     host, [n_knots] strictly increasing, finite; n_knots >= 2
+ *               (<= SDD_INTERP_MAX_SPLINE_KNOTS for the spline)
+ *   values      host, [n_knots][n_vals] real components at the knots
+ *   se          host, [n_knots][n_vals] their standard errors, or NULL
+ *   targets_s   host, [n_targets] within [knots_s[0], knots_s[n_knots-1]]
+ *   kind        SDD_INTERP_LINEAR or SDD_INTERP_SPLINE
+ *   out_values  host out, [n_targets][n_vals]
+ *   out_se      host out, [n_targets][n_vals], or NULL (written only when se
+ *               is given)
+ * A target belongs to the segment [s_i, s_{i+1}] with the largest i <= n-2
+ * such that s_i <= target; a target on a knot gets that knot's value.
+ * Errors: SDD_E_ARG (sizes, kind, knots not increasing, a target outside the
+ * knot range, NULL arrays), SDD_E_CUDA.  n_targets == 0 does nothing. */
+sdd_status sdd_interpolate(const double *knots_s, int32_t n_knots, const double *values,
+                           const double *se, int32_t n_vals, const double *targets_s,
+                           int32_t n_targets, int32_t kind, double *out_values, double *out_se);
+
+/* Interface values at every node of an interface polyline from walks at every
+ * stride-th node: the Monte Carlo nodes ("knots") are nodes 0, stride,
+ * 2 stride, ... and always node n_nodes-1.  Each knot runs n_paths walks with
+ * its index along the polyline as RNG node id, so its estimate equals the one
+ * sdd_interface_values gives that node in a call on the whole polyline with
+ * node ids 0 .. n_nodes-1; the other nodes get the interpolated values and
+ * propagated standard errors described above.
+ *   nodes_xz   host, [n_nodes][2] in interface order, 2 <= n_nodes <=
+ *              SDD_INTERP_MAX_NODES, consecutive nodes distinct, each strictly
+ *              inside the domain
+ *   stride     >= 1 (1: every node runs walks)
+ *   n_paths    walks per Monte Carlo node, 1 .. 2^31-1
+ *   kind       SDD_INTERP_LINEAR or SDD_INTERP_SPLINE (at most
+ *              SDD_INTERP_MAX_SPLINE_KNOTS knots)
+ *   mean, se   host out, [n_nodes][n_eval][2], layouts as sdd_interface_values
+ *   stats      host out, nullable: the walks of the knots
+ *   dt, seed, cfg as sdd_interface_values.
+ * Returns the status of the walks (SDD_OK or SDD_E_TRUNCATED) or an error. */
+sdd_status sdd_interface_values_interp(sdd_ctx *ctx, const double *nodes_xz, int32_t n_nodes,
+                                       int32_t stride, int64_t n_paths, int32_t kind, double dt,
+                                       uint64_t seed, const sdd_config *cfg, double *mean,
+                                       double *se, sdd_stats *stats);
 
 /* ------------------------------------------------------------------------
  * Serving: a request loop with continuous batching.

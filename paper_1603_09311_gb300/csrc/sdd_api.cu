@@ -686,6 +686,8 @@ sdd_status run(sdd_ctx *ctx, const Plan &P, const Launch &L, WalkArgs A, cudaStr
 
 }  // namespace
 
+int sdd::report_error(int status, const char *msg) { return (int)fail((sdd_status)status, msg); }
+
 extern "C" {
 
 const char *sdd_status_str(sdd_status s) {

@@ -167,6 +167,10 @@ cudaError_t launch_walk_f32(int kmax, int geo, const ModelDev &M, const WalkArgs
                             int block, cudaStream_t s);
 cudaError_t launch_walk_f64(int kmax, int geo, const ModelDev &M, const WalkArgs &A, int grid,
                             int block, cudaStream_t s);
+// Record msg as the calling thread's last error (sdd_last_error) and return
+// status.
+int report_error(int status, const char *msg);
+
 // Largest number of resident CTAs per SM for a configuration.
 int occupancy_f32(int kmax, int gcode, int block, int E, int K);
 int occupancy_f64(int kmax, int geo, int block, int E, int K);

@@ -11,6 +11,8 @@ The functions carry the names of the C entry points:
     sdd_interface_values_device(ctx, d_nodes, n_paths, dt, seed, d_mean, d_se, ...)
     sdd_walk_records(ctx, x0, z0, node_id, p0, count, dt, seed, ...)
     sdd_walk_occupation(ctx, x0, z0, node_id, p0, count, dt, seed, ...)   TE and TM
+    sdd_interpolate(knots_s, values, se, targets_s, kind)
+    sdd_interface_values_interp(ctx, nodes, stride, n_paths, kind, dt, seed, ...)
     sdd_status_str(status), sdd_last_error()
 Models are the plain dicts of ``inputs.py``.
 """
@@ -27,6 +29,8 @@ LIB_PATH = os.path.join(HERE, "libsdd.so")
 SDD_OK, SDD_E_ARG, SDD_E_OOM, SDD_E_CUDA, SDD_E_TRUNCATED = 0, 1, 2, 3, 4
 SDD_E_CANCELLED, SDD_E_TIMEOUT, SDD_E_UNSUPPORTED, SDD_E_BUSY = 5, 6, 7, 8
 SDD_FP32, SDD_FP64 = 0, 1
+SDD_INTERP_LINEAR, SDD_INTERP_SPLINE = 0, 1
+SDD_INTERP_MAX_SPLINE_KNOTS, SDD_INTERP_MAX_NODES = 4096, 1 << 20
 MAX_K, MAX_E, MAX_SHAPES = 8, 32, 16
 
 
@@ -79,7 +83,8 @@ class sdd_stats(ctypes.Structure):
                 ("truncated", ctypes.c_uint64), ("kernel_ms", ctypes.c_double),
                 ("launches", ctypes.c_int32), ("items", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64)]
+                ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
+                ("interp_ms", ctypes.c_double)]
 
 
 class sdd_server_config(ctypes.Structure):
@@ -146,6 +151,13 @@ SIGNATURES = [
      [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, ctypes.c_uint32, ctypes.c_uint32,
       ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, P(sdd_config), P(ctypes.c_int64),
       P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_int64)]),
+    ("sdd_interpolate", ctypes.c_int,
+     [P(ctypes.c_double), ctypes.c_int32, P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int32,
+      P(ctypes.c_double), ctypes.c_int32, ctypes.c_int32, P(ctypes.c_double), P(ctypes.c_double)]),
+    ("sdd_interface_values_interp", ctypes.c_int,
+     [ctypes.c_void_p, P(ctypes.c_double), ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+      ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, P(sdd_config), P(ctypes.c_double),
+      P(ctypes.c_double), P(sdd_stats)]),
     ("sdd_server_create", ctypes.c_int, [P(sdd_server_config), P(ctypes.c_void_p)]),
     ("sdd_server_destroy", None, [ctypes.c_void_p]),
     ("sdd_server_submit", ctypes.c_int, [ctypes.c_void_p, P(sdd_request_desc), P(ctypes.c_uint64)]),
@@ -452,6 +464,43 @@ def sdd_walk_occupation(ctx: Context, x0: float, z0: float, node_id: int, p0: in
         raise SddError(st, "sdd_walk_occupation")
     return {"steps": steps, "occ": occ, "exit": ext, "wall": wall, "m_last": mlast, "hits": hits,
             "truncated": (wall < 0).astype(np.int32)}
+
+
+def sdd_interpolate(knots_s, values, se, targets_s, kind: int):
+    """Interpolate knot data [n_knots][V] (and standard errors, or None) to
+    targets_s.  Returns (values [n_targets][V], se [n_targets][V] or None)."""
+    ks = np.ascontiguousarray(np.asarray(knots_s, dtype=np.float64))
+    v = np.ascontiguousarray(np.asarray(values, dtype=np.float64).reshape(len(ks), -1))
+    e = None if se is None else np.ascontiguousarray(np.asarray(se, dtype=np.float64).reshape(v.shape))
+    t = np.ascontiguousarray(np.asarray(targets_s, dtype=np.float64).reshape(-1))
+    ov = np.zeros((len(t), v.shape[1]))
+    oe = None if e is None else np.zeros_like(ov)
+    st = lib().sdd_interpolate(_dp(ks), len(ks), _dp(v), None if e is None else _dp(e), v.shape[1],
+                               _dp(t), len(t), int(kind), _dp(ov), None if oe is None else _dp(oe))
+    if st != SDD_OK:
+        raise SddError(st, "sdd_interpolate")
+    return ov, oe
+
+
+def sdd_interface_values_interp(ctx: Context, nodes, stride: int, n_paths: int, kind: int, dt: float,
+                                seed: int, config: sdd_config | None = None, **cfg):
+    """Walks at every stride-th node of an interface polyline (and its last
+    node), interpolation in arc length for the others.  Returns (mean complex
+    [n][E], se [n][E][2], stats dict of the walks)."""
+    nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64).reshape(-1, 2))
+    n = nodes.shape[0]
+    mean = np.zeros((n, ctx.E, 2))
+    se = np.zeros((n, ctx.E, 2))
+    st_out = sdd_stats()
+    c = config if config is not None else make_config(**cfg)
+    st = lib().sdd_interface_values_interp(ctx.handle, _dp(nodes), n, int(stride), int(n_paths), int(kind),
+                                           float(dt), int(seed) & (2 ** 64 - 1), ctypes.byref(c),
+                                           _dp(mean), _dp(se), ctypes.byref(st_out))
+    if st not in (SDD_OK, SDD_E_TRUNCATED):
+        raise SddError(st, "sdd_interface_values_interp")
+    stats = {f: getattr(st_out, f) for f, _ in sdd_stats._fields_}
+    stats["status"] = st
+    return mean[..., 0] + 1j * mean[..., 1], se, stats
 
 
 def sdd_autotune(ctx: Context, nodes, n_paths, dt: float, seed: int, **base):

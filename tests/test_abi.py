@@ -107,3 +107,57 @@ def test_null_context_is_an_argument_error(L):
                                 None, None, None)
     assert st == sdd.SDD_E_ARG
     L.sdd_destroy(None)  # allowed
+
+
+@pytest.mark.parametrize("case,msg", [
+    ("kind", "kind must be"),
+    ("one_knot", "n_knots must be at least 2"),
+    ("not_increasing", "strictly increasing"),
+    ("nan_knot", "finite"),
+    ("target_outside", "targets must lie within"),
+    ("spline_too_many", "SDD_INTERP_MAX_SPLINE_KNOTS"),
+    ("no_values", "must not be NULL"),
+])
+def test_interpolate_arguments_rejected_before_any_cuda_call(L, case, msg):
+    k = np.array([0.0, 0.5, 1.0])
+    kind = sdd.SDD_INTERP_LINEAR
+    v = np.zeros((3, 2))
+    t = np.array([0.25])
+    if case == "kind":
+        kind = 7
+    elif case == "one_knot":
+        k = k[:1]
+    elif case == "not_increasing":
+        k = np.array([0.0, 0.5, 0.5])
+    elif case == "nan_knot":
+        k = np.array([0.0, np.nan, 1.0])
+    elif case == "target_outside":
+        t = np.array([1.5])
+    elif case == "spline_too_many":
+        kind = sdd.SDD_INTERP_SPLINE
+        k = np.linspace(0, 1, sdd.SDD_INTERP_MAX_SPLINE_KNOTS + 1)
+        v = np.zeros((len(k), 2))
+    if case == "no_values":
+        with pytest.raises(sdd.SddError) as e:
+            dp = ctypes.POINTER(ctypes.c_double)
+            st = L.sdd_interpolate(k.ctypes.data_as(dp), 3, None, None, 2, t.ctypes.data_as(dp), 1, 0,
+                                   None, None)
+            raise sdd.SddError(st, "sdd_interpolate")
+    else:
+        with pytest.raises(sdd.SddError) as e:
+            sdd.sdd_interpolate(k, v, None, t, kind)
+    assert e.value.status == sdd.SDD_E_ARG
+    assert msg in sdd.sdd_last_error()
+
+
+def test_interpolate_without_targets_does_nothing(L):
+    v, e = sdd.sdd_interpolate([0.0, 1.0], np.ones((2, 3)), None, np.zeros(0), sdd.SDD_INTERP_SPLINE)
+    assert v.shape == (0, 3) and e is None
+
+
+def test_interface_interp_null_context(L):
+    dp = ctypes.POINTER(ctypes.c_double)
+    n = np.zeros(4)
+    st = L.sdd_interface_values_interp(None, n.ctypes.data_as(dp), 2, 1, 10, 0, 1e-3, 0, None, None,
+                                       None, None)
+    assert st == sdd.SDD_E_ARG
