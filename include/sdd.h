@@ -161,8 +161,9 @@ typedef struct {
     int32_t block;       /* threads per CTA */
     uint64_t h2d_bytes;  /* host-to-device bytes copied by the call */
     uint64_t d2h_bytes;  /* device-to-host bytes copied by the call */
-    double interp_ms;    /* device time of the interpolation kernels (CUDA events;
-                            sdd_interface_values_interp, 0 elsewhere) */
+    double post_ms;      /* device time of the kernels that follow the walks (CUDA
+                            events; sdd_interface_values_interp and
+                            sdd_apparent_resistivity, 0 elsewhere) */
 } sdd_stats;
 
 /* Create a context on the current CUDA device and copy the model to it.
@@ -396,6 +397,48 @@ sdd_status sdd_interface_values_interp(sdd_ctx *ctx, const double *nodes_xz, int
                                        int32_t stride, int64_t n_paths, int32_t kind, double dt,
                                        uint64_t seed, const sdd_config *cfg, double *mean,
                                        double *se, sdd_stats *stats);
+
+/* ------------------------------------------------------------------------
+ * Apparent resistivity and phase at measurement sites (Sec. 2.1: the
+ * secondary fields H^x = -(1/(i omega mu)) dE^y/dz (TE) and
+ * E^x = (1/sigma) dH^y/dz (TM), rho_a = |E/H|^2 / (omega mu) and
+ * phi = arg(E/H) with E/H = E^y/H^x (TE) or E^x/H^y (TM); Sec. 4.2: the
+ * solution at three points near the surface of each site, the z-derivative
+ * by the centred difference).
+ *
+ * Site i = (x, z0) runs n_paths walks at (x, z0 - h), (x, z0), (x, z0 + h)
+ * under node ids 3i, 3i+1, 3i+2.  With u the primary field there (E^y of a
+ * TE model, H^y of a TM model), u_z = (u(z0 + h) - u(z0 - h)) / (2h), and
+ * kappa_ref[e] = omega_e mu sigma_ref L^2 the rate a reference conductivity
+ * sigma_ref would have in evaluation e, the library returns, in units of
+ * rho_ref = 1/sigma_ref:
+ *   TE  rho = kappa_ref |u / u_z|^2,        phi = arg(-i u / u_z)
+ *   TM  rho = D^2 |u_z / u|^2 / kappa_ref,  phi = arg(u_z / u)
+ * where D = sigma_ref / sigma is the diffusion of the strip holding x (a TM
+ * model's D_m Lap u = i kappa u is the TM equation times sigma_ref / sigma_m
+ * when kappa = omega mu sigma_ref L^2 in every strip).  A uniform half-space
+ * gives rho = sigma_ref / sigma and phi = 45 degrees (TE) or -135 degrees
+ * (TM); phases are in radians in (-pi, pi].
+ * Standard errors are first order in the six real inputs (re and im of the
+ * three points, taken as independent).
+ *   sites_xz   host, [n_sites][2]; every point strictly inside the domain
+ *   h          > 0, the centred-difference half step
+ *   n_paths    walks per point, 1 .. 2^31-1
+ *   kappa_ref  host, [n_eval], finite and > 0
+ *   rho, phase host out, [n_sites][n_eval]
+ *   rho_se, phase_se  host out, [n_sites][n_eval], nullable
+ *   u0, uz     host out, [n_sites][n_eval][2] (re, im): the primary field at
+ *              the site and its centred z-derivative (dimensionless), nullable
+ *   stats      host out, nullable: the walks of all 3 n_sites points
+ *   dt, seed, cfg as sdd_interface_values.
+ * Returns the status of the walks (SDD_OK or SDD_E_TRUNCATED) or an error.
+ * Runs on the current device; host arrays in and out. */
+#define SDD_MT_MAX_SITES (1 << 20)
+sdd_status sdd_apparent_resistivity(sdd_ctx *ctx, const double *sites_xz, int32_t n_sites, double h,
+                                    int64_t n_paths, const double *kappa_ref, double dt,
+                                    uint64_t seed, const sdd_config *cfg, double *rho, double *phase,
+                                    double *rho_se, double *phase_se, double *u0, double *uz,
+                                    sdd_stats *stats);
 
 /* ------------------------------------------------------------------------
  * Serving: a request loop with continuous batching.

@@ -1,11 +1,12 @@
 """Build libsdd.so in-tree with nvcc for sm_103a (GB300).
 
-Four translation units compiled in parallel and linked into one shared
+Five translation units compiled in parallel and linked into one shared
 library with the static CUDA runtime:
   walk_f32.cu  single-precision walk  (-ftz=true -prec-div=false -prec-sqrt=false)
   walk_f64.cu  double-precision walk  (-fmad=false: no fused multiply-add)
   sdd_api.cu   C ABI, planning, reduction
   interp.cu    interpolation between Monte Carlo interface nodes (FP64)
+  mt.cu        apparent resistivity and phase at measurement sites (FP64)
 """
 from __future__ import annotations
 
@@ -27,6 +28,7 @@ UNITS = {
     "walk_f64": ["-fmad=false"],
     "sdd_api": [],
     "interp": [],
+    "mt": [],
 }
 
 

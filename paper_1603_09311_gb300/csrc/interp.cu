@@ -391,7 +391,7 @@ extern "C" sdd_status sdd_interface_values_interp(sdd_ctx *ctx, const double *no
     if (stats) {
         float ms = 0.f;
         INTERP_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
-        stats->interp_ms = ms;
+        stats->post_ms = ms;
         // arc length, knot gather, knot check, [spline factor, spline columns], interpolation, scatter
         stats->launches += (kind == SDD_INTERP_SPLINE && nk > 2) ? 7 : 5;
         stats->h2d_bytes += 2 * (uint64_t)n_nodes * sizeof(double) + (uint64_t)nk * sizeof(int32_t) +

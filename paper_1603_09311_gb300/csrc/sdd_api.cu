@@ -688,6 +688,14 @@ sdd_status run(sdd_ctx *ctx, const Plan &P, const Launch &L, WalkArgs A, cudaStr
 
 int sdd::report_error(int status, const char *msg) { return (int)fail((sdd_status)status, msg); }
 
+int sdd::ctx_site_diffusion(const sdd_ctx *c, double x, double *D) {
+    if (!c || c->geo != GEO_TM) return 0;
+    int m = 0;
+    while (m < c->K - 1 && x >= c->M.xif[m]) ++m;
+    *D = c->M.diff[m];
+    return 1;
+}
+
 extern "C" {
 
 const char *sdd_status_str(sdd_status s) {

@@ -10,6 +10,8 @@
 
 #include <cuda_runtime.h>
 
+struct sdd_ctx;
+
 namespace sdd {
 
 constexpr int kMaxK = 8;
@@ -170,6 +172,10 @@ cudaError_t launch_walk_f64(int kmax, int geo, const ModelDev &M, const WalkArgs
 // Record msg as the calling thread's last error (sdd_last_error) and return
 // status.
 int report_error(int status, const char *msg);
+
+// TM models: *D = the diffusion of the strip holding x ([x_{m-1}, x_m)), 1
+// returned; TE models: 0.
+int ctx_site_diffusion(const ::sdd_ctx *c, double x, double *D);
 
 // Largest number of resident CTAs per SM for a configuration.
 int occupancy_f32(int kmax, int gcode, int block, int E, int K);

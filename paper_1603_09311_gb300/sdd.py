@@ -13,6 +13,7 @@ The functions carry the names of the C entry points:
     sdd_walk_occupation(ctx, x0, z0, node_id, p0, count, dt, seed, ...)   TE and TM
     sdd_interpolate(knots_s, values, se, targets_s, kind)
     sdd_interface_values_interp(ctx, nodes, stride, n_paths, kind, dt, seed, ...)
+    sdd_apparent_resistivity(ctx, sites, h, n_paths, kappa_ref, dt, seed, ...)
     sdd_status_str(status), sdd_last_error()
 Models are the plain dicts of ``inputs.py``.
 """
@@ -31,6 +32,7 @@ SDD_E_CANCELLED, SDD_E_TIMEOUT, SDD_E_UNSUPPORTED, SDD_E_BUSY = 5, 6, 7, 8
 SDD_FP32, SDD_FP64 = 0, 1
 SDD_INTERP_LINEAR, SDD_INTERP_SPLINE = 0, 1
 SDD_INTERP_MAX_SPLINE_KNOTS, SDD_INTERP_MAX_NODES = 4096, 1 << 20
+SDD_MT_MAX_SITES = 1 << 20
 MAX_K, MAX_E, MAX_SHAPES = 8, 32, 16
 
 
@@ -84,7 +86,7 @@ class sdd_stats(ctypes.Structure):
                 ("launches", ctypes.c_int32), ("items", ctypes.c_int32),
                 ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
-                ("interp_ms", ctypes.c_double)]
+                ("post_ms", ctypes.c_double)]
 
 
 class sdd_server_config(ctypes.Structure):
@@ -157,6 +159,11 @@ SIGNATURES = [
     ("sdd_interface_values_interp", ctypes.c_int,
      [ctypes.c_void_p, P(ctypes.c_double), ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
       ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, P(sdd_config), P(ctypes.c_double),
+      P(ctypes.c_double), P(sdd_stats)]),
+    ("sdd_apparent_resistivity", ctypes.c_int,
+     [ctypes.c_void_p, P(ctypes.c_double), ctypes.c_int32, ctypes.c_double, ctypes.c_int64,
+      P(ctypes.c_double), ctypes.c_double, ctypes.c_uint64, P(sdd_config), P(ctypes.c_double),
+      P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
       P(ctypes.c_double), P(sdd_stats)]),
     ("sdd_server_create", ctypes.c_int, [P(sdd_server_config), P(ctypes.c_void_p)]),
     ("sdd_server_destroy", None, [ctypes.c_void_p]),
@@ -501,6 +508,34 @@ def sdd_interface_values_interp(ctx: Context, nodes, stride: int, n_paths: int, 
     stats = {f: getattr(st_out, f) for f, _ in sdd_stats._fields_}
     stats["status"] = st
     return mean[..., 0] + 1j * mean[..., 1], se, stats
+
+
+def sdd_apparent_resistivity(ctx: Context, sites, h: float, n_paths: int, kappa_ref, dt: float, seed: int,
+                             config: sdd_config | None = None, **cfg):
+    """Apparent resistivity (units of rho_ref) and phase (radians) at sites
+    [n][2] from walks at (x, z0 - h), (x, z0), (x, z0 + h).  Returns a dict of
+    rho, phase, rho_se, phase_se [n][E], u0, uz (complex [n][E]) and the
+    walks' stats."""
+    sites = np.ascontiguousarray(np.asarray(sites, dtype=np.float64).reshape(-1, 2))
+    n = sites.shape[0]
+    kr = np.ascontiguousarray(np.broadcast_to(np.asarray(kappa_ref, dtype=np.float64), (ctx.E,)))
+    out = {k: np.zeros((n, ctx.E)) for k in ("rho", "phase", "rho_se", "phase_se")}
+    u0 = np.zeros((n, ctx.E, 2))
+    uz = np.zeros((n, ctx.E, 2))
+    st_out = sdd_stats()
+    c = config if config is not None else make_config(**cfg)
+    st = lib().sdd_apparent_resistivity(ctx.handle, _dp(sites), n, float(h), int(n_paths), _dp(kr), float(dt),
+                                        int(seed) & (2 ** 64 - 1), ctypes.byref(c), _dp(out["rho"]),
+                                        _dp(out["phase"]), _dp(out["rho_se"]), _dp(out["phase_se"]), _dp(u0),
+                                        _dp(uz), ctypes.byref(st_out))
+    if st not in (SDD_OK, SDD_E_TRUNCATED):
+        raise SddError(st, "sdd_apparent_resistivity")
+    out["u0"] = u0[..., 0] + 1j * u0[..., 1]
+    out["uz"] = uz[..., 0] + 1j * uz[..., 1]
+    stats = {f: getattr(st_out, f) for f, _ in sdd_stats._fields_}
+    stats["status"] = st
+    out["stats"] = stats
+    return out
 
 
 def sdd_autotune(ctx: Context, nodes, n_paths, dt: float, seed: int, **base):

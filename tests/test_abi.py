@@ -161,3 +161,13 @@ def test_interface_interp_null_context(L):
     st = L.sdd_interface_values_interp(None, n.ctypes.data_as(dp), 2, 1, 10, 0, 1e-3, 0, None, None,
                                        None, None)
     assert st == sdd.SDD_E_ARG
+
+
+def test_apparent_resistivity_null_context(L):
+    dp = ctypes.POINTER(ctypes.c_double)
+    s = np.zeros(2)
+    k = np.ones(1)
+    st = L.sdd_apparent_resistivity(None, s.ctypes.data_as(dp), 1, 0.05, 10, k.ctypes.data_as(dp), 1e-3, 0,
+                                    None, None, None, None, None, None, None, None)
+    assert st == sdd.SDD_E_ARG
+    assert "ctx" in sdd.sdd_last_error()
