@@ -86,6 +86,19 @@ def tm_analytic():
 
 # ------------------------------------------------------------------ nodes
 
+def rect_grid(x0, x1, z0, z1, nx, nz):
+    """Nodes of an nx x nz grid on [x0, x1] x [z0, z1] (row-major in z, then
+    x) and a flag per node: 1 on the rectangle's edge, else 0."""
+    xs = np.linspace(x0, x1, nx)
+    zs = np.linspace(z0, z1, nz)
+    X, Z = np.meshgrid(xs, zs)
+    nodes = np.stack([X.ravel(), Z.ravel()], axis=1)
+    edge = np.zeros((nz, nx), dtype=np.uint8)
+    edge[0, :] = edge[-1, :] = 1
+    edge[:, 0] = edge[:, -1] = 1
+    return np.ascontiguousarray(nodes), edge.ravel()
+
+
 def nodes_line(p0, p1, n):
     t = np.linspace(0.0, 1.0, n)
     return np.stack([p0[0] + t * (p1[0] - p0[0]), p0[1] + t * (p1[1] - p0[1])], axis=1)
