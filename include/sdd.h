@@ -441,6 +441,60 @@ sdd_status sdd_apparent_resistivity(sdd_ctx *ctx, const double *sites_xz, int32_
                                     sdd_stats *stats);
 
 /* ------------------------------------------------------------------------
+ * RBF-FD sub-domain solve (Sec. 3.2).  Once the interface values are known,
+ * a sub-domain of constant rate kappa (TE: Lap u = i kappa u; a TM strip of
+ * diffusion D: the same with kappa / D) is solved on its own nodes by
+ * radial-basis-function finite differences:
+ *  - the stencil of a node is the node and its n_stencil - 1 nearest nodes
+ *    (by squared distance dx*dx + dz*dz, ties to the lower index);
+ *  - the weights of the Laplacian at node x_0 solve A w = b, A_ij =
+ *    phi(|x_i - x_j|) over the stencil, b_j = Lap phi(|x - x_j|) at x_0, with
+ *    the multiquadric phi(r) = sqrt(1 + (eps r)^2), so
+ *    Lap phi = (2 eps^2 + eps^4 r^2) / phi^3 (the paper builds d^2/dx^2 and
+ *    d^2/dz^2 separately; their sum has these weights);
+ *  - every non-Dirichlet node i gets sum_j w_ij u_j - i kappa_i u_i = 0, the
+ *    Dirichlet nodes' terms on the right-hand side, and the system is solved
+ *    by BiCGStab with a Jacobi preconditioner to |b - K x| <= tol |b|.
+ * The paper uses n_stencil = 9 and eps = 1/2000 per metre with 100-125 m
+ * spacing (eps h about 0.05).  FP64 on the current device; host arrays. */
+#define SDD_RBFFD_MAX_NODES (1 << 18) /* the neighbour search scans all nodes */
+#define SDD_RBFFD_MAX_STENCIL 16
+
+typedef struct {
+    int32_t unknowns;     /* non-Dirichlet nodes */
+    int32_t iterations;   /* BiCGStab iterations */
+    double rel_residual;  /* |b - K x| / |b| of the returned solution */
+    double knn_ms;        /* device time of the neighbour search */
+    double weights_ms;    /* device time of the weights */
+    double solve_ms;      /* device time of assembly and BiCGStab (with its polls) */
+} sdd_rbffd_stats;
+
+/* Stencils and Laplacian weights of every node.
+ *   nodes_xz   host, [n][2] finite, distinct; n_stencil <= n <= SDD_RBFFD_MAX_NODES
+ *   n_stencil  2 .. SDD_RBFFD_MAX_STENCIL (9 in the paper)
+ *   eps        shape parameter, > 0
+ *   stencil    host out, [n][n_stencil] node indices, the node itself first
+ *   weights    host out, [n][n_stencil]
+ * Errors: SDD_E_ARG (sizes, eps, non-finite nodes, a singular stencil
+ * matrix from coincident nodes), SDD_E_CUDA. */
+sdd_status sdd_rbffd_weights(const double *nodes_xz, int32_t n, int32_t n_stencil, double eps,
+                             int32_t *stencil, double *weights);
+
+/* Sub-domain solution.
+ *   dirichlet  host, [n] 1 = value given (interface or outer boundary), 0 = unknown
+ *   values     host, [n][2] (re, im), read at Dirichlet nodes
+ *   kappa      host, [n] rate of the equation at each node
+ *   tol        relative residual to reach, > 0; max_iter >= 1
+ *   u          host out, [n][2]: the values at Dirichlet nodes, the solution
+ *              elsewhere (the last iterate when not converged)
+ *   stats      host out, nullable
+ * Errors: SDD_E_ARG, SDD_E_CUDA; SDD_E_TIMEOUT when BiCGStab did not reach
+ * tol within max_iter or broke down (u and stats are still written). */
+sdd_status sdd_rbffd_solve(const double *nodes_xz, int32_t n, const uint8_t *dirichlet,
+                           const double *values, const double *kappa, int32_t n_stencil, double eps,
+                           double tol, int32_t max_iter, double *u, sdd_rbffd_stats *stats);
+
+/* ------------------------------------------------------------------------
  * Serving: a request loop with continuous batching.
  *
  * A server evaluates requests -- one raster model and its interface nodes

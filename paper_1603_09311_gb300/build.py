@@ -1,12 +1,13 @@
 """Build libsdd.so in-tree with nvcc for sm_103a (GB300).
 
-Five translation units compiled in parallel and linked into one shared
+Six translation units compiled in parallel and linked into one shared
 library with the static CUDA runtime:
   walk_f32.cu  single-precision walk  (-ftz=true -prec-div=false -prec-sqrt=false)
   walk_f64.cu  double-precision walk  (-fmad=false: no fused multiply-add)
   sdd_api.cu   C ABI, planning, reduction
   interp.cu    interpolation between Monte Carlo interface nodes (FP64)
   mt.cu        apparent resistivity and phase at measurement sites (FP64)
+  rbffd.cu     RBF-FD sub-domain solve (FP64, -fmad=false)
 """
 from __future__ import annotations
 
@@ -29,6 +30,7 @@ UNITS = {
     "sdd_api": [],
     "interp": [],
     "mt": [],
+    "rbffd": ["-fmad=false"],
 }
 
 

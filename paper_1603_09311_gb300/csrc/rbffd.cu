@@ -1,0 +1,538 @@
+// RBF-FD sub-domain solver (Sec. 3.2 of arXiv:1603.09311): once the
+// interface values are known, a sub-domain is solved on its own nodes with
+// radial-basis-function finite differences.
+//
+// At node x_0 with stencil x_1 .. x_n (the node and its n - 1 nearest
+// neighbours), the weights of an operator L solve A w = b with
+// A_ij = phi(|x_i - x_j|) and b_j = L phi(|x - x_j|) at x_0, for the
+// multiquadric phi(r) = sqrt(1 + (eps r)^2).  The operator is the Laplacian
+// (the sum of the paper's d^2/dx^2 and d^2/dz^2 matrices; the weights are
+// linear in b): Lap phi = (2 eps^2 + eps^4 r^2) / phi^3 in two dimensions.
+// Every unknown node i gets the equation
+//     sum_{j in stencil(i)} w_ij u_j - i kappa_i u_i = 0,
+// the Dirichlet nodes' terms moved to the right-hand side, and the sparse
+// complex system is solved by BiCGStab with a Jacobi preconditioner.
+//
+// Kernels (FP64, this unit compiled without FMA contraction so that the
+// squared distances of the neighbour search round as in plain arithmetic):
+//   knn_kernel       each node's nearest nodes by (squared distance, index),
+//                    one thread per node, all nodes scanned
+//   weights_kernel   one thread per node: the n x n multiquadric system,
+//                    Gaussian elimination with partial pivoting
+//   assemble_kernel  one thread per unknown: the row (ELL, n slots, column
+//                    -1 for a Dirichlet neighbour), the diagonal and the
+//                    right-hand side
+//   BiCGStab         ELL matrix-vector product, two-stage dot products in
+//                    fixed order (block partials, then one CTA), scalar
+//                    updates on the device; the host polls a stop flag
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "sdd.h"
+#include "sdd_internal.cuh"
+
+namespace sdd {
+namespace {
+
+constexpr int kMaxStencil = 16;
+constexpr int kDotThreads = 256;
+constexpr int kDotBlocks = 1024;
+
+struct Z {
+    double re, im;
+};
+__device__ __forceinline__ Z zadd(Z a, Z b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ Z zsub(Z a, Z b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ Z zmul(Z a, Z b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ Z zdiv(Z a, Z b) {
+    const double d = b.re * b.re + b.im * b.im;
+    return {(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+// conj(a) b
+__device__ __forceinline__ Z zcdot(Z a, Z b) { return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re}; }
+
+__device__ __forceinline__ double mq(double r2, double eps) { return sqrt(1.0 + eps * eps * r2); }
+
+__global__ void knn_kernel(const double *p, int n, int ns, int32_t *st) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double bd[kMaxStencil];
+    int bi[kMaxStencil];
+    int cnt = 0;
+    const double xi = p[2 * i], zi = p[2 * i + 1];
+    for (int j = 0; j < n; ++j) {
+        const double dx = p[2 * j] - xi, dz = p[2 * j + 1] - zi;
+        const double d2 = dx * dx + dz * dz;
+        if (cnt == ns && !(d2 < bd[ns - 1])) continue;  // equal distance: the lower index stays
+        int k = cnt < ns ? cnt++ : ns - 1;
+        while (k > 0 && bd[k - 1] > d2) {
+            bd[k] = bd[k - 1];
+            bi[k] = bi[k - 1];
+            --k;
+        }
+        bd[k] = d2;
+        bi[k] = j;
+    }
+    for (int k = 0; k < ns; ++k) st[(size_t)i * ns + k] = bi[k];
+}
+
+// Weights of node i, w[i][k] for stencil entry k.  *err = 1 on a zero pivot
+// (coincident nodes).
+__global__ void weights_kernel(const double *p, int n, const int32_t *st, int ns, double eps,
+                               double *w, int *err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double A[kMaxStencil][kMaxStencil + 1];
+    const double xi = p[2 * i], zi = p[2 * i + 1];
+    for (int a = 0; a < ns; ++a) {
+        const int ja = st[(size_t)i * ns + a];
+        const double xa = p[2 * ja], za = p[2 * ja + 1];
+        for (int b = 0; b < ns; ++b) {
+            const int jb = st[(size_t)i * ns + b];
+            const double r = hypot(xa - p[2 * jb], za - p[2 * jb + 1]);
+            A[a][b] = mq(r * r, eps);
+        }
+        const double r = hypot(xa - xi, za - zi);
+        const double ph = mq(r * r, eps);
+        A[a][ns] = (2.0 * eps * eps + eps * eps * eps * eps * r * r) / (ph * ph * ph);
+    }
+    for (int c = 0; c < ns; ++c) {
+        int piv = c;
+        double best = fabs(A[c][c]);
+        for (int r = c + 1; r < ns; ++r)
+            if (fabs(A[r][c]) > best) {
+                best = fabs(A[r][c]);
+                piv = r;
+            }
+        if (!(best > 0.0)) {
+            atomicExch(err, 1);
+            return;
+        }
+        if (piv != c)
+            for (int k = c; k <= ns; ++k) {
+                const double t = A[c][k];
+                A[c][k] = A[piv][k];
+                A[piv][k] = t;
+            }
+        for (int r = c + 1; r < ns; ++r) {
+            const double f = A[r][c] / A[c][c];
+            for (int k = c; k <= ns; ++k) A[r][k] -= f * A[c][k];
+        }
+    }
+    for (int c = ns - 1; c >= 0; --c) {
+        double s = A[c][ns];
+        for (int k = c + 1; k < ns; ++k) s -= A[c][k] * A[k][ns];
+        A[c][ns] = s / A[c][c];
+    }
+    for (int k = 0; k < ns; ++k) w[(size_t)i * ns + k] = A[k][ns];
+}
+
+// Row r (node unk[r]): ELL slots k-major (ew[k nu + r], ecol[k nu + r]),
+// diagonal d = w_ii - i kappa_i, right-hand side -sum_{Dirichlet j} w_ij u_j.
+__global__ void assemble_kernel(const int32_t *unk, const int32_t *pos, int nu, const int32_t *st,
+                                const double *w, int ns, const double *kappa, const double *vals,
+                                double *ew, int32_t *ecol, Z *diag, Z *rhs) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nu) return;
+    const int i = unk[r];
+    Z b = {0.0, 0.0};
+    double wii = 0.0;
+    for (int k = 0; k < ns; ++k) {
+        const int j = st[(size_t)i * ns + k];
+        const double wij = w[(size_t)i * ns + k];
+        const int c = pos[j];
+        ew[(size_t)k * nu + r] = wij;
+        ecol[(size_t)k * nu + r] = c;
+        if (c < 0) {
+            b.re -= wij * vals[2 * j];
+            b.im -= wij * vals[2 * j + 1];
+        }
+        if (j == i) wii = wij;
+    }
+    diag[r] = {wii, -kappa[i]};
+    rhs[r] = b;
+}
+
+// y = K x: sum over the slots, minus i kappa x on the diagonal
+__global__ void spmv_kernel(const double *ew, const int32_t *ecol, int nu, int ns, const int32_t *unk,
+                            const double *kappa, const Z *x, Z *y) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nu) return;
+    Z acc = {0.0, 0.0};
+    for (int k = 0; k < ns; ++k) {
+        const int c = ecol[(size_t)k * nu + r];
+        if (c >= 0) {
+            const double wv = ew[(size_t)k * nu + r];
+            acc.re += wv * x[c].re;
+            acc.im += wv * x[c].im;
+        }
+    }
+    const double kap = kappa[unk[r]];
+    // - i kappa x = kappa (x.im, -x.re)
+    acc.re += kap * x[r].im;
+    acc.im -= kap * x[r].re;
+    y[r] = acc;
+}
+
+// Block partials of sum conj(a_i) b_i (and of sum conj(a_i) c_i when c).
+__global__ void __launch_bounds__(kDotThreads) dot_partial_kernel(const Z *a, const Z *b, const Z *c,
+                                                                  int n, Z *part_b, Z *part_c) {
+    __shared__ Z sb[kDotThreads], sc[kDotThreads];
+    Z ab = {0.0, 0.0}, ac = {0.0, 0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        ab = zadd(ab, zcdot(a[i], b[i]));
+        if (c) ac = zadd(ac, zcdot(a[i], c[i]));
+    }
+    sb[threadIdx.x] = ab;
+    sc[threadIdx.x] = ac;
+    __syncthreads();
+    for (int off = kDotThreads / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            sb[threadIdx.x] = zadd(sb[threadIdx.x], sb[threadIdx.x + off]);
+            sc[threadIdx.x] = zadd(sc[threadIdx.x], sc[threadIdx.x + off]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part_b[blockIdx.x] = sb[0];
+        if (c) part_c[blockIdx.x] = sc[0];
+    }
+}
+
+__device__ Z block_sum(const Z *part, int np) {
+    __shared__ Z s[kDotThreads];
+    Z acc = {0.0, 0.0};
+    for (int i = threadIdx.x; i < np; i += blockDim.x) acc = zadd(acc, part[i]);
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = kDotThreads / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) s[threadIdx.x] = zadd(s[threadIdx.x], s[threadIdx.x + off]);
+        __syncthreads();
+    }
+    const Z out = s[0];
+    __syncthreads();
+    return out;
+}
+
+// Device-side BiCGStab scalars.  stop: 0 running, 1 converged, 2 breakdown.
+struct Scal {
+    Z rho, rho_prev, alpha, omega, beta;
+    double rnorm2, bnorm2, tol2;
+    int iter, stop;
+};
+
+// rho = <r^, r>; beta = (rho / rho_prev) (alpha / omega)
+__global__ void scal_rho_kernel(const Z *part, int np, Scal *S) {
+    const Z rho = block_sum(part, np);
+    if (threadIdx.x != 0 || S->stop) return;
+    if (rho.re == 0.0 && rho.im == 0.0) {
+        S->stop = 2;
+        return;
+    }
+    S->beta = S->iter == 0 ? Z{0.0, 0.0} : zmul(zdiv(rho, S->rho_prev), zdiv(S->alpha, S->omega));
+    S->rho = rho;
+}
+
+// alpha = rho / <r^, v>
+__global__ void scal_alpha_kernel(const Z *part, int np, Scal *S) {
+    const Z rv = block_sum(part, np);
+    if (threadIdx.x != 0 || S->stop) return;
+    if (rv.re == 0.0 && rv.im == 0.0) {
+        S->stop = 2;
+        return;
+    }
+    S->alpha = zdiv(S->rho, rv);
+}
+
+// omega = <t, s> / <t, t>
+__global__ void scal_omega_kernel(const Z *part_ts, const Z *part_tt, int np, Scal *S) {
+    const Z ts = block_sum(part_ts, np);
+    const Z tt = block_sum(part_tt, np);
+    if (threadIdx.x != 0 || S->stop) return;
+    if (tt.re == 0.0) {
+        S->stop = 2;
+        return;
+    }
+    S->omega = zdiv(ts, tt);
+}
+
+// |r|^2 after the update; convergence test
+__global__ void scal_norm_kernel(const Z *part, int np, Scal *S) {
+    const Z rr = block_sum(part, np);
+    if (threadIdx.x != 0 || S->stop) return;
+    S->rnorm2 = rr.re;
+    S->rho_prev = S->rho;
+    S->iter += 1;
+    if (S->rnorm2 <= S->tol2 * S->bnorm2) S->stop = 1;
+    if (S->omega.re == 0.0 && S->omega.im == 0.0) S->stop = 2;
+}
+
+// p = r + beta (p - omega v); y = p / d
+__global__ void update_p_kernel(int n, const Scal *S, const Z *r, const Z *v, const Z *d, Z *p, Z *y) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || S->stop) return;
+    const Z pi = zadd(r[i], zmul(S->beta, zsub(p[i], zmul(S->omega, v[i]))));
+    p[i] = pi;
+    y[i] = zdiv(pi, d[i]);
+}
+
+// s = r - alpha v; z = s / d
+__global__ void update_s_kernel(int n, const Scal *S, const Z *r, const Z *v, const Z *d, Z *s, Z *z) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || S->stop) return;
+    const Z si = zsub(r[i], zmul(S->alpha, v[i]));
+    s[i] = si;
+    z[i] = zdiv(si, d[i]);
+}
+
+// x += alpha y + omega z; r = s - omega t
+__global__ void update_x_kernel(int n, const Scal *S, const Z *y, const Z *z, const Z *s, const Z *t, Z *x,
+                                Z *r) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || S->stop) return;
+    x[i] = zadd(x[i], zadd(zmul(S->alpha, y[i]), zmul(S->omega, z[i])));
+    r[i] = zsub(s[i], zmul(S->omega, t[i]));
+}
+
+__global__ void scatter_u_kernel(const int32_t *unk, int nu, const Z *x, double *u) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nu) return;
+    u[2 * unk[r]] = x[r].re;
+    u[2 * unk[r] + 1] = x[r].im;
+}
+
+__global__ void residual_kernel(const Z *Kx, const Z *b, int n, Z *res) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) res[i] = zsub(b[i], Kx[i]);
+}
+
+sdd_status rb_arg(const char *msg) { return (sdd_status)report_error(SDD_E_ARG, msg); }
+sdd_status rb_cuda(cudaError_t e, const char *what) {
+    return (sdd_status)report_error(SDD_E_CUDA, (std::string(what) + ": " + cudaGetErrorString(e)).c_str());
+}
+#define RB_CUDA(call)                                                \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return rb_cuda(e_, #call);            \
+    } while (0)
+
+struct RbScratch {
+    std::vector<void *> ptrs;
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    ~RbScratch() {
+        for (void *p : ptrs) cudaFree(p);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        if (st) cudaStreamDestroy(st);
+    }
+    template <class T>
+    cudaError_t alloc(T **p, size_t count) {
+        cudaError_t e = cudaMalloc((void **)p, (count ? count : 1) * sizeof(T));
+        if (e == cudaSuccess) ptrs.push_back(*p);
+        return e;
+    }
+};
+
+sdd_status check_nodes_eps(const double *nodes_xz, int32_t n, int32_t ns, double eps) {
+    if (ns < 2 || ns > kMaxStencil) return rb_arg("n_stencil must be in 2 .. SDD_RBFFD_MAX_STENCIL");
+    if (n < ns || n > SDD_RBFFD_MAX_NODES) return rb_arg("n must be in n_stencil .. SDD_RBFFD_MAX_NODES");
+    if (!(eps > 0.0) || !std::isfinite(eps)) return rb_arg("eps must be finite and > 0");
+    if (!nodes_xz) return rb_arg("nodes_xz must not be NULL");
+    for (int i = 0; i < 2 * n; ++i)
+        if (!std::isfinite(nodes_xz[i])) return rb_arg("nodes must be finite");
+    return SDD_OK;
+}
+
+// Stencils and weights on the device (d_p: nodes), timed by ev[0..2].
+sdd_status weights_device(const double *d_p, int n, int ns, double eps, int32_t *d_st, double *d_w,
+                          RbScratch &S) {
+    int *d_err;
+    RB_CUDA(S.alloc(&d_err, 1));
+    RB_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), S.st));
+    RB_CUDA(cudaEventRecord(S.ev[0], S.st));
+    knn_kernel<<<(n + 127) / 128, 128, 0, S.st>>>(d_p, n, ns, d_st);
+    RB_CUDA(cudaGetLastError());
+    RB_CUDA(cudaEventRecord(S.ev[1], S.st));
+    weights_kernel<<<(n + 63) / 64, 64, 0, S.st>>>(d_p, n, d_st, ns, eps, d_w, d_err);
+    RB_CUDA(cudaGetLastError());
+    RB_CUDA(cudaEventRecord(S.ev[2], S.st));
+    int h_err = 0;
+    RB_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, S.st));
+    RB_CUDA(cudaStreamSynchronize(S.st));
+    if (h_err) return rb_arg("a stencil matrix is singular (coincident nodes)");
+    return SDD_OK;
+}
+
+}  // namespace
+}  // namespace sdd
+
+using namespace sdd;
+
+extern "C" sdd_status sdd_rbffd_weights(const double *nodes_xz, int32_t n, int32_t n_stencil, double eps,
+                                        int32_t *stencil, double *weights) {
+    sdd_status r = check_nodes_eps(nodes_xz, n, n_stencil, eps);
+    if (r != SDD_OK) return r;
+    if (!stencil || !weights) return rb_arg("stencil and weights must not be NULL");
+    RbScratch S;
+    double *d_p, *d_w;
+    int32_t *d_st;
+    RB_CUDA(S.alloc(&d_p, 2 * (size_t)n));
+    RB_CUDA(S.alloc(&d_st, (size_t)n * n_stencil));
+    RB_CUDA(S.alloc(&d_w, (size_t)n * n_stencil));
+    RB_CUDA(cudaStreamCreateWithFlags(&S.st, cudaStreamNonBlocking));
+    for (int k = 0; k < 3; ++k) RB_CUDA(cudaEventCreate(&S.ev[k]));
+    RB_CUDA(cudaMemcpyAsync(d_p, nodes_xz, 2 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, S.st));
+    r = weights_device(d_p, n, n_stencil, eps, d_st, d_w, S);
+    if (r != SDD_OK) return r;
+    RB_CUDA(cudaMemcpyAsync(stencil, d_st, (size_t)n * n_stencil * sizeof(int32_t), cudaMemcpyDeviceToHost, S.st));
+    RB_CUDA(cudaMemcpyAsync(weights, d_w, (size_t)n * n_stencil * sizeof(double), cudaMemcpyDeviceToHost, S.st));
+    RB_CUDA(cudaStreamSynchronize(S.st));
+    return SDD_OK;
+}
+
+extern "C" sdd_status sdd_rbffd_solve(const double *nodes_xz, int32_t n, const uint8_t *dirichlet,
+                                      const double *values, const double *kappa, int32_t n_stencil,
+                                      double eps, double tol, int32_t max_iter, double *u,
+                                      sdd_rbffd_stats *stats) {
+    if (stats) *stats = sdd_rbffd_stats{};
+    sdd_status r = check_nodes_eps(nodes_xz, n, n_stencil, eps);
+    if (r != SDD_OK) return r;
+    if (!dirichlet || !values || !kappa || !u) return rb_arg("dirichlet, values, kappa and u must not be NULL");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return rb_arg("tol must be finite and > 0");
+    if (max_iter < 1) return rb_arg("max_iter must be at least 1");
+    std::vector<int32_t> unk, pos(n, -1);
+    for (int i = 0; i < n; ++i) {
+        if (dirichlet[i] > 1) return rb_arg("dirichlet flags must be 0 or 1");
+        if (!std::isfinite(kappa[i])) return rb_arg("kappa must be finite");
+        if (dirichlet[i]) {
+            if (!std::isfinite(values[2 * i]) || !std::isfinite(values[2 * i + 1]))
+                return rb_arg("Dirichlet values must be finite");
+        } else {
+            pos[i] = (int32_t)unk.size();
+            unk.push_back(i);
+        }
+    }
+    const int nu = (int)unk.size();
+    for (int i = 0; i < n; ++i) {
+        u[2 * i] = dirichlet[i] ? values[2 * i] : 0.0;
+        u[2 * i + 1] = dirichlet[i] ? values[2 * i + 1] : 0.0;
+    }
+    if (stats) stats->unknowns = nu;
+    if (nu == 0) return SDD_OK;
+
+    const int ns = n_stencil;
+    RbScratch S;
+    double *d_p, *d_w, *d_vals, *d_kap, *d_ew, *d_u;
+    int32_t *d_st, *d_unk, *d_pos, *d_ecol;
+    Z *d_diag, *d_b, *x, *rr, *rh, *p, *v, *y, *s, *zz, *t, *part0, *part1;
+    Scal *d_S;
+    RB_CUDA(S.alloc(&d_p, 2 * (size_t)n));
+    RB_CUDA(S.alloc(&d_st, (size_t)n * ns));
+    RB_CUDA(S.alloc(&d_w, (size_t)n * ns));
+    RB_CUDA(S.alloc(&d_vals, 2 * (size_t)n));
+    RB_CUDA(S.alloc(&d_kap, (size_t)n));
+    RB_CUDA(S.alloc(&d_unk, (size_t)nu));
+    RB_CUDA(S.alloc(&d_pos, (size_t)n));
+    RB_CUDA(S.alloc(&d_ew, (size_t)nu * ns));
+    RB_CUDA(S.alloc(&d_ecol, (size_t)nu * ns));
+    RB_CUDA(S.alloc(&d_u, 2 * (size_t)n));
+    for (Z **q : {&d_diag, &d_b, &x, &rr, &rh, &p, &v, &y, &s, &zz, &t}) RB_CUDA(S.alloc(q, (size_t)nu));
+    RB_CUDA(S.alloc(&part0, (size_t)kDotBlocks));
+    RB_CUDA(S.alloc(&part1, (size_t)kDotBlocks));
+    RB_CUDA(S.alloc(&d_S, 1));
+    RB_CUDA(cudaStreamCreateWithFlags(&S.st, cudaStreamNonBlocking));
+    for (int k = 0; k < 5; ++k) RB_CUDA(cudaEventCreate(&S.ev[k]));
+    cudaStream_t st = S.st;
+    RB_CUDA(cudaMemcpyAsync(d_p, nodes_xz, 2 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st));
+    RB_CUDA(cudaMemcpyAsync(d_vals, u, 2 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st));
+    RB_CUDA(cudaMemcpyAsync(d_kap, kappa, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st));
+    RB_CUDA(cudaMemcpyAsync(d_unk, unk.data(), (size_t)nu * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    RB_CUDA(cudaMemcpyAsync(d_pos, pos.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    r = weights_device(d_p, n, ns, eps, d_st, d_w, S);
+    if (r != SDD_OK) return r;
+
+    const int gb = (nu + 127) / 128;
+    const int gd = std::min(kDotBlocks, (nu + kDotThreads - 1) / kDotThreads);
+    assemble_kernel<<<gb, 128, 0, st>>>(d_unk, d_pos, nu, d_st, d_w, ns, d_kap, d_vals, d_ew, d_ecol, d_diag, d_b);
+    RB_CUDA(cudaGetLastError());
+    // x = 0, r = r^ = b, p = v = 0
+    RB_CUDA(cudaMemsetAsync(x, 0, (size_t)nu * sizeof(Z), st));
+    RB_CUDA(cudaMemsetAsync(p, 0, (size_t)nu * sizeof(Z), st));
+    RB_CUDA(cudaMemsetAsync(v, 0, (size_t)nu * sizeof(Z), st));
+    RB_CUDA(cudaMemcpyAsync(rr, d_b, (size_t)nu * sizeof(Z), cudaMemcpyDeviceToDevice, st));
+    RB_CUDA(cudaMemcpyAsync(rh, d_b, (size_t)nu * sizeof(Z), cudaMemcpyDeviceToDevice, st));
+    dot_partial_kernel<<<gd, kDotThreads, 0, st>>>(d_b, d_b, nullptr, nu, part0, nullptr);
+    RB_CUDA(cudaGetLastError());
+    std::vector<Z> h_part(gd);
+    RB_CUDA(cudaMemcpyAsync(h_part.data(), part0, gd * sizeof(Z), cudaMemcpyDeviceToHost, st));
+    RB_CUDA(cudaStreamSynchronize(st));
+    double bnorm2 = 0.0;
+    for (int k = 0; k < gd; ++k) bnorm2 += h_part[k].re;
+    Scal h_S{};
+    h_S.alpha = h_S.omega = h_S.rho_prev = Z{1.0, 0.0};
+    h_S.bnorm2 = bnorm2;
+    h_S.rnorm2 = bnorm2;
+    h_S.tol2 = tol * tol;
+    if (bnorm2 == 0.0) h_S.stop = 1;  // zero right-hand side: x = 0
+    RB_CUDA(cudaMemcpyAsync(d_S, &h_S, sizeof(Scal), cudaMemcpyHostToDevice, st));
+    RB_CUDA(cudaEventRecord(S.ev[3], st));
+
+    const int kPoll = 8;
+    int it = 0;
+    while (it < max_iter && !h_S.stop) {
+        const int batch = std::min(kPoll, max_iter - it);
+        for (int q = 0; q < batch; ++q) {
+            dot_partial_kernel<<<gd, kDotThreads, 0, st>>>(rh, rr, nullptr, nu, part0, nullptr);
+            scal_rho_kernel<<<1, kDotThreads, 0, st>>>(part0, gd, d_S);
+            update_p_kernel<<<gb, 128, 0, st>>>(nu, d_S, rr, v, d_diag, p, y);
+            spmv_kernel<<<gb, 128, 0, st>>>(d_ew, d_ecol, nu, ns, d_unk, d_kap, y, v);
+            dot_partial_kernel<<<gd, kDotThreads, 0, st>>>(rh, v, nullptr, nu, part0, nullptr);
+            scal_alpha_kernel<<<1, kDotThreads, 0, st>>>(part0, gd, d_S);
+            update_s_kernel<<<gb, 128, 0, st>>>(nu, d_S, rr, v, d_diag, s, zz);
+            spmv_kernel<<<gb, 128, 0, st>>>(d_ew, d_ecol, nu, ns, d_unk, d_kap, zz, t);
+            dot_partial_kernel<<<gd, kDotThreads, 0, st>>>(t, s, t, nu, part0, part1);
+            scal_omega_kernel<<<1, kDotThreads, 0, st>>>(part0, part1, gd, d_S);
+            update_x_kernel<<<gb, 128, 0, st>>>(nu, d_S, y, zz, s, t, x, rr);
+            dot_partial_kernel<<<gd, kDotThreads, 0, st>>>(rr, rr, nullptr, nu, part0, nullptr);
+            scal_norm_kernel<<<1, kDotThreads, 0, st>>>(part0, gd, d_S);
+        }
+        RB_CUDA(cudaGetLastError());
+        RB_CUDA(cudaMemcpyAsync(&h_S, d_S, sizeof(Scal), cudaMemcpyDeviceToHost, st));
+        RB_CUDA(cudaStreamSynchronize(st));
+        it += batch;
+    }
+    // the true residual |b - K x| / |b|
+    spmv_kernel<<<gb, 128, 0, st>>>(d_ew, d_ecol, nu, ns, d_unk, d_kap, x, t);
+    residual_kernel<<<gb, 128, 0, st>>>(t, d_b, nu, s);
+    dot_partial_kernel<<<gd, kDotThreads, 0, st>>>(s, s, nullptr, nu, part0, nullptr);
+    RB_CUDA(cudaGetLastError());
+    RB_CUDA(cudaMemcpyAsync(d_u, u, 2 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st));
+    scatter_u_kernel<<<gb, 128, 0, st>>>(d_unk, nu, x, d_u);
+    RB_CUDA(cudaGetLastError());
+    RB_CUDA(cudaMemcpyAsync(u, d_u, 2 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RB_CUDA(cudaMemcpyAsync(h_part.data(), part0, gd * sizeof(Z), cudaMemcpyDeviceToHost, st));
+    RB_CUDA(cudaEventRecord(S.ev[4], st));
+    RB_CUDA(cudaStreamSynchronize(st));
+    double res2 = 0.0;
+    for (int k = 0; k < gd; ++k) res2 += h_part[k].re;
+    if (stats) {
+        float ms = 0.f;
+        stats->iterations = h_S.iter;
+        stats->rel_residual = bnorm2 > 0.0 ? std::sqrt(res2 / bnorm2) : 0.0;
+        RB_CUDA(cudaEventElapsedTime(&ms, S.ev[0], S.ev[1]));
+        stats->knn_ms = ms;
+        RB_CUDA(cudaEventElapsedTime(&ms, S.ev[1], S.ev[2]));
+        stats->weights_ms = ms;
+        RB_CUDA(cudaEventElapsedTime(&ms, S.ev[3], S.ev[4]));
+        stats->solve_ms = ms;
+    }
+    if (h_S.stop == 2) return (sdd_status)report_error(SDD_E_TIMEOUT, "BiCGStab broke down before convergence");
+    if (h_S.stop != 1) return (sdd_status)report_error(SDD_E_TIMEOUT, "BiCGStab did not reach tol within max_iter");
+    return SDD_OK;
+}

@@ -14,6 +14,7 @@ The functions carry the names of the C entry points:
     sdd_interpolate(knots_s, values, se, targets_s, kind)
     sdd_interface_values_interp(ctx, nodes, stride, n_paths, kind, dt, seed, ...)
     sdd_apparent_resistivity(ctx, sites, h, n_paths, kappa_ref, dt, seed, ...)
+    sdd_rbffd_weights(nodes, n_stencil, eps), sdd_rbffd_solve(nodes, dirichlet, values, kappa, ...)
     sdd_status_str(status), sdd_last_error()
 Models are the plain dicts of ``inputs.py``.
 """
@@ -33,6 +34,7 @@ SDD_FP32, SDD_FP64 = 0, 1
 SDD_INTERP_LINEAR, SDD_INTERP_SPLINE = 0, 1
 SDD_INTERP_MAX_SPLINE_KNOTS, SDD_INTERP_MAX_NODES = 4096, 1 << 20
 SDD_MT_MAX_SITES = 1 << 20
+SDD_RBFFD_MAX_NODES, SDD_RBFFD_MAX_STENCIL = 1 << 18, 16
 MAX_K, MAX_E, MAX_SHAPES = 8, 32, 16
 
 
@@ -87,6 +89,12 @@ class sdd_stats(ctypes.Structure):
                 ("grid", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
                 ("post_ms", ctypes.c_double)]
+
+
+class sdd_rbffd_stats(ctypes.Structure):
+    _fields_ = [("unknowns", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("rel_residual", ctypes.c_double), ("knn_ms", ctypes.c_double),
+                ("weights_ms", ctypes.c_double), ("solve_ms", ctypes.c_double)]
 
 
 class sdd_server_config(ctypes.Structure):
@@ -165,6 +173,13 @@ SIGNATURES = [
       P(ctypes.c_double), ctypes.c_double, ctypes.c_uint64, P(sdd_config), P(ctypes.c_double),
       P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
       P(ctypes.c_double), P(sdd_stats)]),
+    ("sdd_rbffd_weights", ctypes.c_int,
+     [P(ctypes.c_double), ctypes.c_int32, ctypes.c_int32, ctypes.c_double, P(ctypes.c_int32),
+      P(ctypes.c_double)]),
+    ("sdd_rbffd_solve", ctypes.c_int,
+     [P(ctypes.c_double), ctypes.c_int32, P(ctypes.c_uint8), P(ctypes.c_double), P(ctypes.c_double),
+      ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_int32, P(ctypes.c_double),
+      P(sdd_rbffd_stats)]),
     ("sdd_server_create", ctypes.c_int, [P(sdd_server_config), P(ctypes.c_void_p)]),
     ("sdd_server_destroy", None, [ctypes.c_void_p]),
     ("sdd_server_submit", ctypes.c_int, [ctypes.c_void_p, P(sdd_request_desc), P(ctypes.c_uint64)]),
@@ -536,6 +551,43 @@ def sdd_apparent_resistivity(ctx: Context, sites, h: float, n_paths: int, kappa_
     stats["status"] = st
     out["stats"] = stats
     return out
+
+
+def sdd_rbffd_weights(nodes, n_stencil: int = 9, eps: float = 1.0):
+    """Stencils [n][n_stencil] (int32) and Laplacian weights [n][n_stencil]."""
+    p = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64).reshape(-1, 2))
+    n = p.shape[0]
+    st = np.zeros((n, n_stencil), dtype=np.int32)
+    w = np.zeros((n, n_stencil))
+    s = lib().sdd_rbffd_weights(_dp(p), n, int(n_stencil), float(eps), st.ctypes.data_as(P(ctypes.c_int32)),
+                                _dp(w))
+    if s != SDD_OK:
+        raise SddError(s, "sdd_rbffd_weights")
+    return st, w
+
+
+def sdd_rbffd_solve(nodes, dirichlet, values, kappa, n_stencil: int = 9, eps: float = 1.0, tol: float = 1e-12,
+                    max_iter: int = 20000, allow_unconverged: bool = False):
+    """RBF-FD solution u (complex [n]) of Lap u = i kappa u with the values at
+    Dirichlet nodes; returns (u, stats dict).  Raises SddError on
+    SDD_E_TIMEOUT unless allow_unconverged."""
+    p = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64).reshape(-1, 2))
+    n = p.shape[0]
+    fl = np.ascontiguousarray(np.asarray(dirichlet, dtype=np.uint8).reshape(n))
+    v = np.asarray(values)
+    if np.iscomplexobj(v):
+        v = np.stack([v.real, v.imag], axis=-1)
+    v = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(n, 2))
+    k = np.ascontiguousarray(np.broadcast_to(np.asarray(kappa, dtype=np.float64), (n,)))
+    u = np.zeros((n, 2))
+    so = sdd_rbffd_stats()
+    s = lib().sdd_rbffd_solve(_dp(p), n, fl.ctypes.data_as(P(ctypes.c_uint8)), _dp(v), _dp(k), int(n_stencil),
+                              float(eps), float(tol), int(max_iter), _dp(u), ctypes.byref(so))
+    stats = {f: getattr(so, f) for f, _ in sdd_rbffd_stats._fields_}
+    stats["status"] = s
+    if s != SDD_OK and not (allow_unconverged and s == SDD_E_TIMEOUT):
+        raise SddError(s, "sdd_rbffd_solve")
+    return u[:, 0] + 1j * u[:, 1], stats
 
 
 def sdd_autotune(ctx: Context, nodes, n_paths, dt: float, seed: int, **base):

@@ -55,6 +55,8 @@ int main(void) {{
   printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(sdd_server_config), offsetof(sdd_server_config, launch),
          sizeof(sdd_request_desc), offsetof(sdd_request_desc, n_max), sizeof(sdd_request_stats),
          sizeof(sdd_server_stats), sizeof(sdd_batch_entry));
+  printf("%zu %zu %zu\\n", sizeof(sdd_rbffd_stats), offsetof(sdd_rbffd_stats, rel_residual),
+         offsetof(sdd_stats, post_ms));
   return 0;
 }}''')
     exe = tmp_path / "probe"
@@ -67,7 +69,9 @@ int main(void) {{
             ctypes.sizeof(sdd.sdd_server_config), sdd.sdd_server_config.launch.offset,
             ctypes.sizeof(sdd.sdd_request_desc), sdd.sdd_request_desc.n_max.offset,
             ctypes.sizeof(sdd.sdd_request_stats), ctypes.sizeof(sdd.sdd_server_stats),
-            ctypes.sizeof(sdd.sdd_batch_entry)]
+            ctypes.sizeof(sdd.sdd_batch_entry),
+            ctypes.sizeof(sdd.sdd_rbffd_stats), sdd.sdd_rbffd_stats.rel_residual.offset,
+            sdd.sdd_stats.post_ms.offset]
     assert [int(v) for v in out] == want
 
 
@@ -171,3 +175,61 @@ def test_apparent_resistivity_null_context(L):
                                     None, None, None, None, None, None, None, None)
     assert st == sdd.SDD_E_ARG
     assert "ctx" in sdd.sdd_last_error()
+
+
+@pytest.mark.parametrize("case,msg", [
+    ("stencil", "n_stencil"),
+    ("few_nodes", "n must be in"),
+    ("eps", "eps"),
+    ("nan", "finite"),
+])
+def test_rbffd_weights_arguments_rejected_before_any_cuda_call(L, case, msg):
+    nodes, _ = I.rect_grid(0, 1, 0, 1, 4, 4)
+    ns, eps = 9, 1.0
+    if case == "stencil":
+        ns = 17
+    elif case == "few_nodes":
+        nodes = nodes[:5]
+    elif case == "eps":
+        eps = 0.0
+    elif case == "nan":
+        nodes = nodes.copy()
+        nodes[3, 0] = np.nan
+    with pytest.raises(sdd.SddError) as e:
+        sdd.sdd_rbffd_weights(nodes, ns, eps)
+    assert e.value.status == sdd.SDD_E_ARG
+    assert msg in sdd.sdd_last_error()
+
+
+@pytest.mark.parametrize("case,msg", [
+    ("tol", "tol"),
+    ("iters", "max_iter"),
+    ("flag", "dirichlet flags"),
+    ("kappa", "kappa"),
+])
+def test_rbffd_solve_arguments_rejected_before_any_cuda_call(L, case, msg):
+    nodes, edge = I.rect_grid(0, 1, 0, 1, 4, 4)
+    vals = np.zeros((16, 2))
+    kap = np.ones(16)
+    tol, iters = 1e-10, 100
+    if case == "tol":
+        tol = -1.0
+    elif case == "iters":
+        iters = 0
+    elif case == "flag":
+        edge = edge.copy()
+        edge[5] = 2
+    elif case == "kappa":
+        kap[2] = np.inf
+    with pytest.raises(sdd.SddError) as e:
+        sdd.sdd_rbffd_solve(nodes, edge, vals, kap, tol=tol, max_iter=iters)
+    assert e.value.status == sdd.SDD_E_ARG
+    assert msg in sdd.sdd_last_error()
+
+
+def test_rbffd_solve_all_dirichlet_needs_no_gpu(L):
+    nodes, _ = I.rect_grid(0, 1, 0, 1, 4, 4)
+    vals = np.arange(32, dtype=float).reshape(16, 2)
+    u, st = sdd.sdd_rbffd_solve(nodes, np.ones(16, dtype=np.uint8), vals, np.ones(16))
+    np.testing.assert_array_equal(u, vals[:, 0] + 1j * vals[:, 1])
+    assert st["unknowns"] == 0
