@@ -249,16 +249,13 @@ __global__ void scal_alpha_kernel(const Z *part, int np, Scal *S) {
     S->alpha = zdiv(S->rho, rv);
 }
 
-// omega = <t, s> / <t, t>
+// omega = <t, s> / <t, t>; t = 0 means s = 0 (x + alpha y solves the
+// system): omega = 0, and the residual test that follows stops
 __global__ void scal_omega_kernel(const Z *part_ts, const Z *part_tt, int np, Scal *S) {
     const Z ts = block_sum(part_ts, np);
     const Z tt = block_sum(part_tt, np);
     if (threadIdx.x != 0 || S->stop) return;
-    if (tt.re == 0.0) {
-        S->stop = 2;
-        return;
-    }
-    S->omega = zdiv(ts, tt);
+    S->omega = tt.re == 0.0 ? Z{0.0, 0.0} : zdiv(ts, tt);
 }
 
 // |r|^2 after the update; convergence test
@@ -269,7 +266,7 @@ __global__ void scal_norm_kernel(const Z *part, int np, Scal *S) {
     S->rho_prev = S->rho;
     S->iter += 1;
     if (S->rnorm2 <= S->tol2 * S->bnorm2) S->stop = 1;
-    if (S->omega.re == 0.0 && S->omega.im == 0.0) S->stop = 2;
+    else if (S->omega.re == 0.0 && S->omega.im == 0.0) S->stop = 2;
 }
 
 // p = r + beta (p - omega v); y = p / d

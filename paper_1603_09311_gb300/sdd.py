@@ -575,7 +575,8 @@ def sdd_rbffd_solve(nodes, dirichlet, values, kappa, n_stencil: int = 9, eps: fl
     n = p.shape[0]
     fl = np.ascontiguousarray(np.asarray(dirichlet, dtype=np.uint8).reshape(n))
     v = np.asarray(values)
-    if np.iscomplexobj(v):
+    if np.iscomplexobj(v) or v.shape == (n,):
+        v = v.astype(np.complex128)
         v = np.stack([v.real, v.imag], axis=-1)
     v = np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(n, 2))
     k = np.ascontiguousarray(np.broadcast_to(np.asarray(kappa, dtype=np.float64), (n,)))

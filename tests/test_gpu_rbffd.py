@@ -89,23 +89,48 @@ def test_solution_matches_oracle_and_exact(n, kappa, theta):
         assert np.abs(ug - exact).max() < 1e-2 * np.abs(exact).max()
 
 
-def test_scattered_nodes_with_varying_kappa():
-    """Interior nodes scattered in a disc, Dirichlet nodes on its circle;
-    kappa varies per node (the system's diagonal)."""
-    rng = np.random.default_rng(9)
-    m = 120
+def _disc_nodes(seed, h=0.06):
+    """A jittered grid (+-0.2 h) inside the unit disc, and Dirichlet nodes on
+    its circle at spacing h."""
+    rng = np.random.default_rng(seed)
+    g = np.arange(-1, 1 + 1e-9, h)
+    X, Z = np.meshgrid(g, g)
+    p = np.stack([X.ravel(), Z.ravel()], axis=1)
+    p = p + rng.uniform(-0.2 * h, 0.2 * h, p.shape)
+    p = p[np.hypot(p[:, 0], p[:, 1]) < 1 - 0.7 * h]
+    m = int(round(2 * math.pi / h))
     a = np.linspace(0, 2 * math.pi, m, endpoint=False)
-    ring = np.stack([np.cos(a), np.sin(a)], axis=1)
-    r = np.sqrt(rng.uniform(0, 0.85 ** 2, 600))
-    t = rng.uniform(0, 2 * math.pi, 600)
-    inner = np.stack([r * np.cos(t), r * np.sin(t)], axis=1)
-    nodes = np.concatenate([ring, inner])
-    flag = np.concatenate([np.ones(m), np.zeros(600)]).astype(np.uint8)
+    nodes = np.concatenate([np.stack([np.cos(a), np.sin(a)], axis=1), p])
+    return nodes, np.concatenate([np.ones(m), np.zeros(len(p))]).astype(np.uint8)
+
+
+def test_scattered_nodes_with_varying_kappa():
+    """Jittered nodes in a disc, Dirichlet values on its circle; kappa
+    varies per node (the system's diagonal)."""
+    nodes, flag = _disc_nodes(9)
     vals = np.where(flag == 1, np.exp(nodes[:, 0] - 0.5j * nodes[:, 1]), 0.0)
     kap = 3.0 + nodes[:, 0]
     ug, st = sdd.sdd_rbffd_solve(nodes, flag, vals, kap, 9, 1.0, tol=1e-12)
     uo = R.solve(nodes, flag, vals, kap, 9, 1.0)
     assert np.abs(ug - uo).max() <= 1e-8 * np.abs(uo).max()
+
+
+def test_badly_spread_nodes_report_a_breakdown():
+    """Uniformly random nodes (some pairs 1e-3 apart) give an RBF-FD matrix
+    with eigenvalues of positive real part; BiCGStab breaks down on it and
+    the call says so."""
+    rng = np.random.default_rng(9)
+    m = 120
+    a = np.linspace(0, 2 * math.pi, m, endpoint=False)
+    r = np.sqrt(rng.uniform(0, 0.85 ** 2, 600))
+    t = rng.uniform(0, 2 * math.pi, 600)
+    nodes = np.concatenate([np.stack([np.cos(a), np.sin(a)], axis=1),
+                            np.stack([r * np.cos(t), r * np.sin(t)], axis=1)])
+    flag = np.concatenate([np.ones(m), np.zeros(600)]).astype(np.uint8)
+    vals = np.where(flag == 1, np.exp(nodes[:, 0] - 0.5j * nodes[:, 1]), 0.0)
+    u, st = sdd.sdd_rbffd_solve(nodes, flag, vals, 3.0 + nodes[:, 0], 9, 1.0, tol=1e-12,
+                                allow_unconverged=True)
+    assert st["status"] == sdd.SDD_E_TIMEOUT and st["rel_residual"] > 1e-12
 
 
 def test_unconverged_and_bad_nodes():
