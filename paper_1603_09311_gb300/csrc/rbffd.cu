@@ -22,9 +22,12 @@
 //   assemble_kernel  one thread per unknown: the row (ELL, n slots, column
 //                    -1 for a Dirichlet neighbour), the diagonal and the
 //                    right-hand side
-//   BiCGStab         ELL matrix-vector product, two-stage dot products in
-//                    fixed order (block partials, then one CTA), scalar
-//                    updates on the device; the host polls a stop flag
+//   BiCGStab         five launches per iteration: element-wise updates and
+//                    ELL matrix-vector products, each dot product finished
+//                    by the last block of its launch (block partials summed
+//                    in block order), scalars on the device; batches of 8
+//                    iterations replayed as a CUDA graph, the host reading
+//                    the stop flag after each batch
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -133,10 +136,11 @@ __global__ void weights_kernel(const double *p, int n, const int32_t *st, int ns
 }
 
 // Row r (node unk[r]): ELL slots k-major (ew[k nu + r], ecol[k nu + r]),
-// diagonal d = w_ii - i kappa_i, right-hand side -sum_{Dirichlet j} w_ij u_j.
+// the reciprocal of the diagonal d = w_ii - i kappa_i (the Jacobi
+// preconditioner), right-hand side -sum_{Dirichlet j} w_ij u_j.
 __global__ void assemble_kernel(const int32_t *unk, const int32_t *pos, int nu, const int32_t *st,
                                 const double *w, int ns, const double *kappa, const double *vals,
-                                double *ew, int32_t *ecol, Z *diag, Z *rhs) {
+                                double *ew, int32_t *ecol, Z *dinv, Z *rhs) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= nu) return;
     const int i = unk[r];
@@ -154,7 +158,7 @@ __global__ void assemble_kernel(const int32_t *unk, const int32_t *pos, int nu, 
         }
         if (j == i) wii = wij;
     }
-    diag[r] = {wii, -kappa[i]};
+    dinv[r] = zdiv(Z{1.0, 0.0}, Z{wii, -kappa[i]});
     rhs[r] = b;
 }
 
@@ -204,10 +208,49 @@ __global__ void __launch_bounds__(kDotThreads) dot_partial_kernel(const Z *a, co
     }
 }
 
-__device__ Z block_sum(const Z *part, int np) {
+// Device-side BiCGStab scalars.  stop: 0 running, 1 converged, 2 breakdown.
+// ticket: the block counter of the launch that is finishing a dot product.
+struct Scal {
+    Z rho, alpha, omega, beta;
+    double rnorm2, bnorm2, tol2;
+    int iter, stop;
+    unsigned ticket;
+};
+
+// Block reduction of one or two complex values; thread 0 writes the block's
+// partials, then takes a ticket.  Returns true in every thread of the last
+// block to finish, which then holds all partials (read past L1).
+__device__ bool partial_and_ticket(Z v0, Z v1, bool two, Z *part0, Z *part1, unsigned *ticket) {
+    __shared__ Z s0[kDotThreads], s1[kDotThreads];
+    __shared__ bool last;
+    s0[threadIdx.x] = v0;
+    s1[threadIdx.x] = v1;
+    __syncthreads();
+    for (int off = kDotThreads / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            s0[threadIdx.x] = zadd(s0[threadIdx.x], s0[threadIdx.x + off]);
+            if (two) s1[threadIdx.x] = zadd(s1[threadIdx.x], s1[threadIdx.x + off]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part0[blockIdx.x] = s0[0];
+        if (two) part1[blockIdx.x] = s1[0];
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    return last;
+}
+
+// The sum of the partials in block order (the last block only).
+__device__ Z sum_partials(const Z *part, int np) {
     __shared__ Z s[kDotThreads];
     Z acc = {0.0, 0.0};
-    for (int i = threadIdx.x; i < np; i += blockDim.x) acc = zadd(acc, part[i]);
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const double2 v = __ldcg(reinterpret_cast<const double2 *>(part) + i);
+        acc = zadd(acc, Z{v.x, v.y});
+    }
     s[threadIdx.x] = acc;
     __syncthreads();
     for (int off = kDotThreads / 2; off > 0; off >>= 1) {
@@ -219,81 +262,124 @@ __device__ Z block_sum(const Z *part, int np) {
     return out;
 }
 
-// Device-side BiCGStab scalars.  stop: 0 running, 1 converged, 2 breakdown.
-struct Scal {
-    Z rho, rho_prev, alpha, omega, beta;
-    double rnorm2, bnorm2, tol2;
-    int iter, stop;
-};
-
-// rho = <r^, r>; beta = (rho / rho_prev) (alpha / omega)
-__global__ void scal_rho_kernel(const Z *part, int np, Scal *S) {
-    const Z rho = block_sum(part, np);
-    if (threadIdx.x != 0 || S->stop) return;
-    if (rho.re == 0.0 && rho.im == 0.0) {
-        S->stop = 2;
-        return;
+__device__ __forceinline__ Z spmv_row(const double *ew, const int32_t *ecol, int nu, int ns, double kap,
+                                      const Z *x, int r) {
+    Z acc = {0.0, 0.0};
+    for (int k = 0; k < ns; ++k) {
+        const int c = ecol[(size_t)k * nu + r];
+        if (c >= 0) {
+            const double wv = ew[(size_t)k * nu + r];
+            acc.re += wv * x[c].re;
+            acc.im += wv * x[c].im;
+        }
     }
-    S->beta = S->iter == 0 ? Z{0.0, 0.0} : zmul(zdiv(rho, S->rho_prev), zdiv(S->alpha, S->omega));
-    S->rho = rho;
+    // - i kappa x = kappa (x.im, -x.re)
+    acc.re += kap * x[r].im;
+    acc.im -= kap * x[r].re;
+    return acc;
 }
 
-// alpha = rho / <r^, v>
-__global__ void scal_alpha_kernel(const Z *part, int np, Scal *S) {
-    const Z rv = block_sum(part, np);
-    if (threadIdx.x != 0 || S->stop) return;
-    if (rv.re == 0.0 && rv.im == 0.0) {
-        S->stop = 2;
-        return;
+// One BiCGStab iteration is five launches (grid-stride loops over the rows,
+// the dot products finished by each launch's last block; dinv = 1 / d):
+//   update_p      p = r + beta (p - omega v),  y = p / d
+//   spmv_alpha    v = K y,  alpha = rho / <r^, v>
+//   update_s      s = r - alpha v,  z = s / d
+//   spmv_omega    t = K z,  omega = <t, s> / <t, t>  (t = 0: s = 0, omega = 0)
+//   update_x      x += alpha y + omega z,  r = s - omega t,  |r|^2 and the
+//                 stop test, rho' = <r^, r>,  beta = (rho' / rho)(alpha / omega)
+// Every launch does nothing once stop is set.
+__global__ void __launch_bounds__(kDotThreads) update_p_kernel(int n, const Scal *S, const Z *r, const Z *v,
+                                                               const Z *dinv, Z *p, Z *y) {
+    if (S->stop) return;
+    const Z beta = S->beta, omega = S->omega;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Z pi = zadd(r[i], zmul(beta, zsub(p[i], zmul(omega, v[i]))));
+        p[i] = pi;
+        y[i] = zmul(pi, dinv[i]);
     }
-    S->alpha = zdiv(S->rho, rv);
 }
 
-// omega = <t, s> / <t, t>; t = 0 means s = 0 (x + alpha y solves the
-// system): omega = 0, and the residual test that follows stops
-__global__ void scal_omega_kernel(const Z *part_ts, const Z *part_tt, int np, Scal *S) {
-    const Z ts = block_sum(part_ts, np);
-    const Z tt = block_sum(part_tt, np);
-    if (threadIdx.x != 0 || S->stop) return;
-    S->omega = tt.re == 0.0 ? Z{0.0, 0.0} : zdiv(ts, tt);
+__global__ void __launch_bounds__(kDotThreads) spmv_alpha_kernel(const double *ew, const int32_t *ecol, int nu,
+                                                                 int ns, const int32_t *unk, const double *kappa,
+                                                                 const Z *y, const Z *rh, Z *v, Z *part,
+                                                                 Scal *S) {
+    if (S->stop) return;
+    Z acc = {0.0, 0.0};
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nu; r += gridDim.x * blockDim.x) {
+        const Z vr = spmv_row(ew, ecol, nu, ns, kappa[unk[r]], y, r);
+        v[r] = vr;
+        acc = zadd(acc, zcdot(rh[r], vr));
+    }
+    if (!partial_and_ticket(acc, Z{0.0, 0.0}, false, part, nullptr, &S->ticket)) return;
+    const Z rv = sum_partials(part, gridDim.x);
+    if (threadIdx.x == 0) {
+        S->ticket = 0;
+        if (rv.re == 0.0 && rv.im == 0.0) S->stop = 2;
+        else S->alpha = zdiv(S->rho, rv);
+    }
 }
 
-// |r|^2 after the update; convergence test
-__global__ void scal_norm_kernel(const Z *part, int np, Scal *S) {
-    const Z rr = block_sum(part, np);
-    if (threadIdx.x != 0 || S->stop) return;
-    S->rnorm2 = rr.re;
-    S->rho_prev = S->rho;
-    S->iter += 1;
-    if (S->rnorm2 <= S->tol2 * S->bnorm2) S->stop = 1;
-    else if (S->omega.re == 0.0 && S->omega.im == 0.0) S->stop = 2;
+__global__ void __launch_bounds__(kDotThreads) update_s_kernel(int n, const Scal *S, const Z *r, const Z *v,
+                                                               const Z *dinv, Z *s, Z *z) {
+    if (S->stop) return;
+    const Z alpha = S->alpha;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Z si = zsub(r[i], zmul(alpha, v[i]));
+        s[i] = si;
+        z[i] = zmul(si, dinv[i]);
+    }
 }
 
-// p = r + beta (p - omega v); y = p / d
-__global__ void update_p_kernel(int n, const Scal *S, const Z *r, const Z *v, const Z *d, Z *p, Z *y) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || S->stop) return;
-    const Z pi = zadd(r[i], zmul(S->beta, zsub(p[i], zmul(S->omega, v[i]))));
-    p[i] = pi;
-    y[i] = zdiv(pi, d[i]);
+__global__ void __launch_bounds__(kDotThreads) spmv_omega_kernel(const double *ew, const int32_t *ecol, int nu,
+                                                                 int ns, const int32_t *unk, const double *kappa,
+                                                                 const Z *z, const Z *s, Z *t, Z *part0,
+                                                                 Z *part1, Scal *S) {
+    if (S->stop) return;
+    Z ts = {0.0, 0.0}, tt = {0.0, 0.0};
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nu; r += gridDim.x * blockDim.x) {
+        const Z tr = spmv_row(ew, ecol, nu, ns, kappa[unk[r]], z, r);
+        t[r] = tr;
+        ts = zadd(ts, zcdot(tr, s[r]));
+        tt = zadd(tt, zcdot(tr, tr));
+    }
+    if (!partial_and_ticket(ts, tt, true, part0, part1, &S->ticket)) return;
+    const Z sts = sum_partials(part0, gridDim.x);
+    const Z stt = sum_partials(part1, gridDim.x);
+    if (threadIdx.x == 0) {
+        S->ticket = 0;
+        S->omega = stt.re == 0.0 ? Z{0.0, 0.0} : zdiv(sts, stt);
+    }
 }
 
-// s = r - alpha v; z = s / d
-__global__ void update_s_kernel(int n, const Scal *S, const Z *r, const Z *v, const Z *d, Z *s, Z *z) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || S->stop) return;
-    const Z si = zsub(r[i], zmul(S->alpha, v[i]));
-    s[i] = si;
-    z[i] = zdiv(si, d[i]);
-}
-
-// x += alpha y + omega z; r = s - omega t
-__global__ void update_x_kernel(int n, const Scal *S, const Z *y, const Z *z, const Z *s, const Z *t, Z *x,
-                                Z *r) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || S->stop) return;
-    x[i] = zadd(x[i], zadd(zmul(S->alpha, y[i]), zmul(S->omega, z[i])));
-    r[i] = zsub(s[i], zmul(S->omega, t[i]));
+__global__ void __launch_bounds__(kDotThreads) update_x_kernel(int n, const Z *y, const Z *z, const Z *s,
+                                                               const Z *t, const Z *rh, Z *x, Z *r, Z *part0,
+                                                               Z *part1, Scal *S) {
+    if (S->stop) return;
+    const Z alpha = S->alpha, omega = S->omega;
+    Z rr = {0.0, 0.0}, hr = {0.0, 0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        x[i] = zadd(x[i], zadd(zmul(alpha, y[i]), zmul(omega, z[i])));
+        const Z ri = zsub(s[i], zmul(omega, t[i]));
+        r[i] = ri;
+        rr = zadd(rr, zcdot(ri, ri));
+        hr = zadd(hr, zcdot(rh[i], ri));
+    }
+    if (!partial_and_ticket(rr, hr, true, part0, part1, &S->ticket)) return;
+    const Z srr = sum_partials(part0, gridDim.x);
+    const Z rho = sum_partials(part1, gridDim.x);
+    if (threadIdx.x == 0) {
+        S->ticket = 0;
+        S->rnorm2 = srr.re;
+        S->iter += 1;
+        if (S->rnorm2 <= S->tol2 * S->bnorm2) {
+            S->stop = 1;
+        } else if ((omega.re == 0.0 && omega.im == 0.0) || (rho.re == 0.0 && rho.im == 0.0)) {
+            S->stop = 2;
+        } else {
+            S->beta = zmul(zdiv(rho, S->rho), zdiv(alpha, omega));
+            S->rho = rho;
+        }
+    }
 }
 
 __global__ void scatter_u_kernel(const int32_t *unk, int nu, const Z *x, double *u) {
@@ -427,7 +513,7 @@ extern "C" sdd_status sdd_rbffd_solve(const double *nodes_xz, int32_t n, const u
     RbScratch S;
     double *d_p, *d_w, *d_vals, *d_kap, *d_ew, *d_u;
     int32_t *d_st, *d_unk, *d_pos, *d_ecol;
-    Z *d_diag, *d_b, *x, *rr, *rh, *p, *v, *y, *s, *zz, *t, *part0, *part1;
+    Z *d_dinv, *d_b, *x, *rr, *rh, *p, *v, *y, *s, *zz, *t, *part0, *part1;
     Scal *d_S;
     RB_CUDA(S.alloc(&d_p, 2 * (size_t)n));
     RB_CUDA(S.alloc(&d_st, (size_t)n * ns));
@@ -439,7 +525,7 @@ extern "C" sdd_status sdd_rbffd_solve(const double *nodes_xz, int32_t n, const u
     RB_CUDA(S.alloc(&d_ew, (size_t)nu * ns));
     RB_CUDA(S.alloc(&d_ecol, (size_t)nu * ns));
     RB_CUDA(S.alloc(&d_u, 2 * (size_t)n));
-    for (Z **q : {&d_diag, &d_b, &x, &rr, &rh, &p, &v, &y, &s, &zz, &t}) RB_CUDA(S.alloc(q, (size_t)nu));
+    for (Z **q : {&d_dinv, &d_b, &x, &rr, &rh, &p, &v, &y, &s, &zz, &t}) RB_CUDA(S.alloc(q, (size_t)nu));
     RB_CUDA(S.alloc(&part0, (size_t)kDotBlocks));
     RB_CUDA(S.alloc(&part1, (size_t)kDotBlocks));
     RB_CUDA(S.alloc(&d_S, 1));
@@ -456,7 +542,7 @@ extern "C" sdd_status sdd_rbffd_solve(const double *nodes_xz, int32_t n, const u
 
     const int gb = (nu + 127) / 128;
     const int gd = std::min(kDotBlocks, (nu + kDotThreads - 1) / kDotThreads);
-    assemble_kernel<<<gb, 128, 0, st>>>(d_unk, d_pos, nu, d_st, d_w, ns, d_kap, d_vals, d_ew, d_ecol, d_diag, d_b);
+    assemble_kernel<<<gb, 128, 0, st>>>(d_unk, d_pos, nu, d_st, d_w, ns, d_kap, d_vals, d_ew, d_ecol, d_dinv, d_b);
     RB_CUDA(cudaGetLastError());
     // x = 0, r = r^ = b, p = v = 0
     RB_CUDA(cudaMemsetAsync(x, 0, (size_t)nu * sizeof(Z), st));
@@ -472,7 +558,9 @@ extern "C" sdd_status sdd_rbffd_solve(const double *nodes_xz, int32_t n, const u
     double bnorm2 = 0.0;
     for (int k = 0; k < gd; ++k) bnorm2 += h_part[k].re;
     Scal h_S{};
-    h_S.alpha = h_S.omega = h_S.rho_prev = Z{1.0, 0.0};
+    h_S.alpha = h_S.omega = Z{1.0, 0.0};
+    h_S.beta = Z{0.0, 0.0};
+    h_S.rho = Z{bnorm2, 0.0};  // <r^, r> with r^ = r = b
     h_S.bnorm2 = bnorm2;
     h_S.rnorm2 = bnorm2;
     h_S.tol2 = tol * tol;
@@ -480,26 +568,43 @@ extern "C" sdd_status sdd_rbffd_solve(const double *nodes_xz, int32_t n, const u
     RB_CUDA(cudaMemcpyAsync(d_S, &h_S, sizeof(Scal), cudaMemcpyHostToDevice, st));
     RB_CUDA(cudaEventRecord(S.ev[3], st));
 
+    // iterations in batches of kPoll, replayed as one CUDA graph; the host
+    // reads the scalars after each batch
+    const int gi = std::min(kDotBlocks, (nu + kDotThreads - 1) / kDotThreads);
+    auto iteration = [&]() {
+        update_p_kernel<<<gi, kDotThreads, 0, st>>>(nu, d_S, rr, v, d_dinv, p, y);
+        spmv_alpha_kernel<<<gi, kDotThreads, 0, st>>>(d_ew, d_ecol, nu, ns, d_unk, d_kap, y, rh, v, part0, d_S);
+        update_s_kernel<<<gi, kDotThreads, 0, st>>>(nu, d_S, rr, v, d_dinv, s, zz);
+        spmv_omega_kernel<<<gi, kDotThreads, 0, st>>>(d_ew, d_ecol, nu, ns, d_unk, d_kap, zz, s, t, part0, part1,
+                                                      d_S);
+        update_x_kernel<<<gi, kDotThreads, 0, st>>>(nu, y, zz, s, t, rh, x, rr, part0, part1, d_S);
+    };
     const int kPoll = 8;
+    cudaGraphExec_t gexec = nullptr;
+    if (max_iter >= kPoll && !h_S.stop) {
+        cudaGraph_t graph;
+        RB_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        for (int q = 0; q < kPoll; ++q) iteration();
+        RB_CUDA(cudaStreamEndCapture(st, &graph));
+        const cudaError_t e = cudaGraphInstantiate(&gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        RB_CUDA(e);
+    }
+    struct GraphGuard {
+        cudaGraphExec_t g;
+        ~GraphGuard() {
+            if (g) cudaGraphExecDestroy(g);
+        }
+    } gguard{gexec};
     int it = 0;
     while (it < max_iter && !h_S.stop) {
         const int batch = std::min(kPoll, max_iter - it);
-        for (int q = 0; q < batch; ++q) {
-            dot_partial_kernel<<<gd, kDotThreads, 0, st>>>(rh, rr, nullptr, nu, part0, nullptr);
-            scal_rho_kernel<<<1, kDotThreads, 0, st>>>(part0, gd, d_S);
-            update_p_kernel<<<gb, 128, 0, st>>>(nu, d_S, rr, v, d_diag, p, y);
-            spmv_kernel<<<gb, 128, 0, st>>>(d_ew, d_ecol, nu, ns, d_unk, d_kap, y, v);
-            dot_partial_kernel<<<gd, kDotThreads, 0, st>>>(rh, v, nullptr, nu, part0, nullptr);
-            scal_alpha_kernel<<<1, kDotThreads, 0, st>>>(part0, gd, d_S);
-            update_s_kernel<<<gb, 128, 0, st>>>(nu, d_S, rr, v, d_diag, s, zz);
-            spmv_kernel<<<gb, 128, 0, st>>>(d_ew, d_ecol, nu, ns, d_unk, d_kap, zz, t);
-            dot_partial_kernel<<<gd, kDotThreads, 0, st>>>(t, s, t, nu, part0, part1);
-            scal_omega_kernel<<<1, kDotThreads, 0, st>>>(part0, part1, gd, d_S);
-            update_x_kernel<<<gb, 128, 0, st>>>(nu, d_S, y, zz, s, t, x, rr);
-            dot_partial_kernel<<<gd, kDotThreads, 0, st>>>(rr, rr, nullptr, nu, part0, nullptr);
-            scal_norm_kernel<<<1, kDotThreads, 0, st>>>(part0, gd, d_S);
+        if (batch == kPoll && gexec) {
+            RB_CUDA(cudaGraphLaunch(gexec, st));
+        } else {
+            for (int q = 0; q < batch; ++q) iteration();
+            RB_CUDA(cudaGetLastError());
         }
-        RB_CUDA(cudaGetLastError());
         RB_CUDA(cudaMemcpyAsync(&h_S, d_S, sizeof(Scal), cudaMemcpyDeviceToHost, st));
         RB_CUDA(cudaStreamSynchronize(st));
         it += batch;
