@@ -15,8 +15,9 @@
 //
 // Kernels (FP64, this unit compiled without FMA contraction so that the
 // squared distances of the neighbour search round as in plain arithmetic):
-//   knn_kernel       each node's nearest nodes by (squared distance, index),
-//                    one thread per node, all nodes scanned
+//   cell_*, knn_kernel  each node's nearest nodes by (squared distance,
+//                    index): nodes binned into a cell grid, one thread per
+//                    node scanning rings of cells
 //   weights_kernel   one thread per node: the n x n multiquadric system,
 //                    Gaussian elimination with partial pivoting
 //   assemble_kernel  one thread per unknown: the row (ELL, n slots, column
@@ -61,25 +62,107 @@ __device__ __forceinline__ Z zcdot(Z a, Z b) { return {a.re * b.re + a.im * b.im
 
 __device__ __forceinline__ double mq(double r2, double eps) { return sqrt(1.0 + eps * eps * r2); }
 
-__global__ void knn_kernel(const double *p, int n, int ns, int32_t *st) {
+// Nearest-neighbour search on a grid of square cells of side c over the
+// nodes' bounding box: nodes are binned (count, scan, fill), then each node
+// scans rings of cells around its own (ring R: Chebyshev cell distance R).
+// Every node in ring R + 1 or beyond is at least R c away, so the search
+// stops after ring R once the list is full and (R c)^2 exceeds its last
+// squared distance (with a relative margin of 1e-9 for the binning's
+// rounding).  The order is (squared distance, index), as a scan of all nodes
+// gives.
+struct CellGrid {
+    double x0, z0, c;
+    int gx, gz;
+};
+
+__device__ __forceinline__ int cell_x(const CellGrid &g, double x) {
+    return min(max((int)floor((x - g.x0) / g.c), 0), g.gx - 1);
+}
+__device__ __forceinline__ int cell_z(const CellGrid &g, double z) {
+    return min(max((int)floor((z - g.z0) / g.c), 0), g.gz - 1);
+}
+
+__global__ void cell_count_kernel(const double *p, int n, CellGrid g, int32_t *cell, int32_t *count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int id = cell_z(g, p[2 * i + 1]) * g.gx + cell_x(g, p[2 * i]);
+    cell[i] = id;
+    atomicAdd(&count[id], 1);
+}
+
+// start[0 .. m] = exclusive prefix sums of count[0 .. m-1] (one CTA).
+__global__ void __launch_bounds__(1024) cell_scan_kernel(const int32_t *count, int m, int32_t *start) {
+    __shared__ int32_t part[1024];
+    const int t = threadIdx.x;
+    const int per = (m + 1023) / 1024;
+    const int a = min(t * per, m), b = min(a + per, m);
+    int32_t acc = 0;
+    for (int k = a; k < b; ++k) acc += count[k];
+    part[t] = acc;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int32_t v = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int32_t run = t > 0 ? part[t - 1] : 0;
+    for (int k = a; k < b; ++k) {
+        start[k] = run;
+        run += count[k];
+    }
+    if (t == 1023) start[m] = part[1023];
+}
+
+__global__ void cell_fill_kernel(const int32_t *cell, int n, int32_t *cursor, int32_t *list) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    list[atomicAdd(&cursor[cell[i]], 1)] = i;
+}
+
+__device__ __forceinline__ bool before(double d2, int j, double bd, int bj) {
+    return d2 < bd || (d2 == bd && j < bj);
+}
+
+__global__ void knn_kernel(const double *p, int n, int ns, CellGrid g, const int32_t *start,
+                           const int32_t *list, int32_t *st) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double bd[kMaxStencil];
     int bi[kMaxStencil];
     int cnt = 0;
     const double xi = p[2 * i], zi = p[2 * i + 1];
-    for (int j = 0; j < n; ++j) {
-        const double dx = p[2 * j] - xi, dz = p[2 * j + 1] - zi;
-        const double d2 = dx * dx + dz * dz;
-        if (cnt == ns && !(d2 < bd[ns - 1])) continue;  // equal distance: the lower index stays
-        int k = cnt < ns ? cnt++ : ns - 1;
-        while (k > 0 && bd[k - 1] > d2) {
-            bd[k] = bd[k - 1];
-            bi[k] = bi[k - 1];
-            --k;
+    const int cx = cell_x(g, xi), cz = cell_z(g, zi);
+    const int rmax = max(g.gx, g.gz);
+    for (int R = 0; R <= rmax; ++R) {
+        for (int dz = -R; dz <= R; ++dz) {
+            const int iz = cz + dz;
+            if (iz < 0 || iz >= g.gz) continue;
+            const int step = (dz == -R || dz == R) ? 1 : 2 * R;
+            for (int dx = -R; dx <= R; dx += (step > 0 ? step : 1)) {
+                const int ix = cx + dx;
+                if (ix < 0 || ix >= g.gx) continue;
+                const int id = iz * g.gx + ix;
+                for (int q = start[id]; q < start[id + 1]; ++q) {
+                    const int j = list[q];
+                    const double ddx = p[2 * j] - xi, ddz = p[2 * j + 1] - zi;
+                    const double d2 = ddx * ddx + ddz * ddz;
+                    if (cnt == ns && !before(d2, j, bd[ns - 1], bi[ns - 1])) continue;
+                    int k = cnt < ns ? cnt++ : ns - 1;
+                    while (k > 0 && before(d2, j, bd[k - 1], bi[k - 1])) {
+                        bd[k] = bd[k - 1];
+                        bi[k] = bi[k - 1];
+                        --k;
+                    }
+                    bd[k] = d2;
+                    bi[k] = j;
+                }
+            }
         }
-        bd[k] = d2;
-        bi[k] = j;
+        if (cnt == ns) {
+            const double rc = R * g.c;
+            if (rc * rc * (1.0 - 1e-9) > bd[ns - 1]) break;
+        }
     }
     for (int k = 0; k < ns; ++k) st[(size_t)i * ns + k] = bi[k];
 }
@@ -433,13 +516,48 @@ sdd_status check_nodes_eps(const double *nodes_xz, int32_t n, int32_t ns, double
 }
 
 // Stencils and weights on the device (d_p: nodes), timed by ev[0..2].
-sdd_status weights_device(const double *d_p, int n, int ns, double eps, int32_t *d_st, double *d_w,
-                          RbScratch &S) {
+sdd_status weights_device(const double *h_p, const double *d_p, int n, int ns, double eps, int32_t *d_st,
+                          double *d_w, RbScratch &S) {
+    // the cell grid: about 2 nodes per cell over the bounding box, at most
+    // 4 n + 16 cells
+    double x0 = h_p[0], x1 = h_p[0], z0 = h_p[1], z1 = h_p[1];
+    for (int i = 1; i < n; ++i) {
+        x0 = std::min(x0, h_p[2 * i]);
+        x1 = std::max(x1, h_p[2 * i]);
+        z0 = std::min(z0, h_p[2 * i + 1]);
+        z1 = std::max(z1, h_p[2 * i + 1]);
+    }
+    const double W = x1 - x0, H = z1 - z0, L = std::max(W, H);
+    CellGrid g;
+    g.x0 = x0;
+    g.z0 = z0;
+    g.c = W > 0.0 && H > 0.0 ? std::sqrt(2.0 * W * H / n) : (L > 0.0 ? 2.0 * L / n : 1.0);
+    for (;;) {
+        const double gx = std::floor(W / g.c) + 1.0, gz = std::floor(H / g.c) + 1.0;
+        if (gx * gz <= 4.0 * n + 16.0) {
+            g.gx = (int)gx;
+            g.gz = (int)gz;
+            break;
+        }
+        g.c *= 1.5;
+    }
+    const int m = g.gx * g.gz;
     int *d_err;
+    int32_t *d_cell, *d_count, *d_start, *d_cursor, *d_list;
     RB_CUDA(S.alloc(&d_err, 1));
+    RB_CUDA(S.alloc(&d_cell, (size_t)n));
+    RB_CUDA(S.alloc(&d_count, (size_t)m));
+    RB_CUDA(S.alloc(&d_start, (size_t)m + 1));
+    RB_CUDA(S.alloc(&d_cursor, (size_t)m));
+    RB_CUDA(S.alloc(&d_list, (size_t)n));
     RB_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), S.st));
+    RB_CUDA(cudaMemsetAsync(d_count, 0, (size_t)m * sizeof(int32_t), S.st));
     RB_CUDA(cudaEventRecord(S.ev[0], S.st));
-    knn_kernel<<<(n + 127) / 128, 128, 0, S.st>>>(d_p, n, ns, d_st);
+    cell_count_kernel<<<(n + 127) / 128, 128, 0, S.st>>>(d_p, n, g, d_cell, d_count);
+    cell_scan_kernel<<<1, 1024, 0, S.st>>>(d_count, m, d_start);
+    RB_CUDA(cudaMemcpyAsync(d_cursor, d_start, (size_t)m * sizeof(int32_t), cudaMemcpyDeviceToDevice, S.st));
+    cell_fill_kernel<<<(n + 127) / 128, 128, 0, S.st>>>(d_cell, n, d_cursor, d_list);
+    knn_kernel<<<(n + 127) / 128, 128, 0, S.st>>>(d_p, n, ns, g, d_start, d_list, d_st);
     RB_CUDA(cudaGetLastError());
     RB_CUDA(cudaEventRecord(S.ev[1], S.st));
     weights_kernel<<<(n + 63) / 64, 64, 0, S.st>>>(d_p, n, d_st, ns, eps, d_w, d_err);
@@ -471,7 +589,7 @@ extern "C" sdd_status sdd_rbffd_weights(const double *nodes_xz, int32_t n, int32
     RB_CUDA(cudaStreamCreateWithFlags(&S.st, cudaStreamNonBlocking));
     for (int k = 0; k < 3; ++k) RB_CUDA(cudaEventCreate(&S.ev[k]));
     RB_CUDA(cudaMemcpyAsync(d_p, nodes_xz, 2 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, S.st));
-    r = weights_device(d_p, n, n_stencil, eps, d_st, d_w, S);
+    r = weights_device(nodes_xz, d_p, n, n_stencil, eps, d_st, d_w, S);
     if (r != SDD_OK) return r;
     RB_CUDA(cudaMemcpyAsync(stencil, d_st, (size_t)n * n_stencil * sizeof(int32_t), cudaMemcpyDeviceToHost, S.st));
     RB_CUDA(cudaMemcpyAsync(weights, d_w, (size_t)n * n_stencil * sizeof(double), cudaMemcpyDeviceToHost, S.st));
@@ -537,7 +655,7 @@ extern "C" sdd_status sdd_rbffd_solve(const double *nodes_xz, int32_t n, const u
     RB_CUDA(cudaMemcpyAsync(d_kap, kappa, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st));
     RB_CUDA(cudaMemcpyAsync(d_unk, unk.data(), (size_t)nu * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     RB_CUDA(cudaMemcpyAsync(d_pos, pos.data(), (size_t)n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    r = weights_device(d_p, n, ns, eps, d_st, d_w, S);
+    r = weights_device(nodes_xz, d_p, n, ns, eps, d_st, d_w, S);
     if (r != SDD_OK) return r;
 
     const int gb = (nu + 127) / 128;
