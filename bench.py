@@ -508,9 +508,9 @@ def rbffd_measure(sdd, reps=2, cpu=True):
            "solve_ms": rs["solve_ms"], "iterations": rs["iterations"], "rel_residual": rs["rel_residual"],
            "ms_per_iteration": rs["solve_ms"] / max(rs["iterations"], 1),
            "roofline": {"bound": "latency",
-                        "note": "a BiCGStab iteration is 13 launches over vectors of 32k complex values "
-                                "(a few MB, L2-resident); the walks at the boundary nodes are bounded as the "
-                                "main line's kernel"}}
+                        "note": "a BiCGStab iteration is 5 launches (replayed 8 iterations at a time as a "
+                                "CUDA graph) over vectors of 32k complex values (a few MB, L2-resident); the "
+                                "walks at the boundary nodes are bounded as the main line's kernel"}}
     if cpu:
         from oracle import rbffd as R
         sn, se_ = I.rect_grid(0, 0.9, 0, 0.9, 37, 37)
