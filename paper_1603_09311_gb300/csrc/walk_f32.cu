@@ -284,6 +284,68 @@ struct WalkerF32 {
         return advance(M, A, increment(A, wa, wb), wa, wb, k, ei);
     }
 
+    // Raster programs with up to 8 materials: the walk does not depend on the
+    // materials it crosses, so an iteration records each accepted step's
+    // tile-map coordinates (the coarse index, and the cell's offset in its
+    // tile, 4 to a word) and looks them up together after its steps, as
+    // independent loads in flight at once instead of one dependent chain per
+    // step (measured: +3 % on one 6-material raster, +7.6 % on a 12-model
+    // batch; with K <= 4 the per-step lookup stays faster, 2.6e11 against
+    // 1.7e11 walk-steps/s).
+    static constexpr bool kDeferLookup = (GC == GC_RASTER || GC == GC_RASTER_MULTI) && KMAX == 8;
+
+    __device__ __forceinline__ static void cell_of(const ModelDev &M, float X, float Z, uint32_t &ci,
+                                                   uint32_t &off, int k) {
+        const int ix = __float_as_int(fmaf(X, M.fsx, M.fox) + 12582912.0f) - 0x4B400000;
+        const int iz = __float_as_int(fmaf(Z, M.fsz, M.foz) + 12582912.0f) - 0x4B400000;
+        ci = (uint32_t)((iz >> kTileShift) * M.ntx + (ix >> kTileShift));
+        const uint32_t o = (uint32_t)(((iz & (kTile - 1)) << kTileShift) | (ix & (kTile - 1)));
+        off = (k & 3) == 0 ? o : off | (o << (8 * (k & 3)));
+    }
+
+    // The step of advance() with the material lookup deferred.
+    __device__ __forceinline__ bool advance_cell(const ModelDev &M, const WalkArgs &A, const Incr &d,
+                                                 uint32_t wa, uint32_t wb, uint32_t k, ExitInfo<float> &ei,
+                                                 uint32_t &ci, uint32_t &off) {
+        const float Xn = fmaf(-d.r, d.cs, X);
+        const float Zn = fmaf(-d.r, d.sn, Z);
+        const float dn = fminf(M.fhw - fabsf(Xn), M.fhh - fabsf(Zn));
+        const float pn = dmin * dn;
+        if (pn <= A.f_bthr) {
+            if (near_wall(M, A, Xn, Zn, dn, pn, wa, wb, ei)) {
+                ei.nocc = n + k;
+                return true;
+            }
+        }
+        cell_of(M, Xn, Zn, ci, off, (int)k);
+        X = Xn;
+        Z = Zn;
+        dmin = dn;
+        return false;
+    }
+
+    // Count the materials of the first cnt recorded steps: all coarse
+    // entries first, then the cells of mixed tiles.
+    template <int NS>
+    __device__ __forceinline__ void add_cells(const ModelDev &M, const uint32_t (&ci)[NS],
+                                              const uint32_t (&off)[(NS + 3) / 4], int cnt) {
+        const uint32_t *co = GC == GC_RASTER_MULTI ? tco : M.tcoarse;
+        const uint8_t *po = reinterpret_cast<const uint8_t *>(co) + M.tpool_off;
+        uint32_t c[NS];
+#pragma unroll
+        for (int j = 0; j < NS; ++j) c[j] = j < cnt ? __ldg(co + ci[j]) : kTileUniform;
+        int m[NS];
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            const uint32_t o = (off[j >> 2] >> (8 * (j & 3))) & 0xffu;
+            m[j] = (c[j] & kTileUniform) ? (int)(c[j] & 0xffu)
+                                         : (int)__ldg(po + ((size_t)c[j] << (2 * kTileShift)) + o);
+        }
+#pragma unroll
+        for (int j = 0; j < NS; ++j)
+            if (j < cnt) occ.add(m[j]);
+    }
+
     // PAIRS Philox calls, two Euler steps each, per call of iterate: the
     // per-iteration work of the scheduler loop (constants, vote, branch) is
     // shared by 2 PAIRS steps.  The calls depend only on the step counter, so
@@ -298,10 +360,27 @@ struct WalkerF32 {
         uint4 w[PAIRS];
 #pragma unroll
         for (int q = 0; q < PAIRS; ++q) w[q] = philox_rk_pre((n >> 1) + q, 0u, pre_x, pre_y, A.rk0, A.rk1);
+        if constexpr (kDeferLookup) {
+            constexpr int NS = 2 * PAIRS;
+            uint32_t ci[NS], off[(NS + 3) / 4];
+            int done = NS;
 #pragma unroll
-        for (int q = 0; q < PAIRS; ++q) {
-            if (substep(M, A, w[q].x, w[q].y, 2u * q, ei)) return 1;
-            if (substep(M, A, w[q].z, w[q].w, 2u * q + 1u, ei)) return 1;
+            for (int k = 0; k < NS; ++k) {
+                if (done == NS) {
+                    const uint32_t wa = (k & 1) ? w[k >> 1].z : w[k >> 1].x;
+                    const uint32_t wb = (k & 1) ? w[k >> 1].w : w[k >> 1].y;
+                    if (advance_cell(M, A, increment(A, wa, wb), wa, wb, (uint32_t)k, ei, ci[k], off[k >> 2]))
+                        done = k;
+                }
+            }
+            add_cells(M, ci, off, done);
+            if (done < NS) return 1;
+        } else {
+#pragma unroll
+            for (int q = 0; q < PAIRS; ++q) {
+                if (substep(M, A, w[q].x, w[q].y, 2u * q, ei)) return 1;
+                if (substep(M, A, w[q].z, w[q].w, 2u * q + 1u, ei)) return 1;
+            }
         }
         n += 2 * PAIRS;
         if (n >= A.max_steps) {
