@@ -506,12 +506,12 @@ struct WalkerTM32 {
             place(M, Xn, Zn, best, bw, nk, ei);
             return 1;
         }
-        const float dtD = Di * (float)A.dt;
+        // 2 d d' / (D_i dt) as c2 d d' (c2 = 2 / (D_i dt) of the strip)
         float best = 0.f;
         int bw = -1;
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
-            const float q = 2.f * d[w] * e[w] / dtD;
+            const float q = c2 * d[w] * e[w];
             if (bw < 0 || q < best) { best = q; bw = w; }
         }
         const float U = bridge_u(wa, wb);
@@ -541,12 +541,12 @@ struct WalkerTM32 {
             float bq = 0.f, bx = 0.f;
             int bs = -1;
             if (i > 0 && M.fdiff[i - 1] != Di) {
-                bq = 2.f * (X - xl) * (Xn - xl) / dtD;
+                bq = c2 * (X - xl) * (Xn - xl);
                 bs = i - 1;
                 bx = xl;
             }
             if (i < M.K - 1 && M.fdiff[i + 1] != Di) {
-                const float q = 2.f * (xr - X) * (xr - Xn) / dtD;
+                const float q = c2 * (xr - X) * (xr - Xn);
                 if (bs < 0 || q < bq) { bq = q; bs = i + 1; bx = xr; }
             }
             const float pg = (bs >= 0 && bq <= 40.f) ? __expf(-bq) : 0.f;
