@@ -21,6 +21,17 @@
  * every evaluation e (a row kappa[e][.] of phase rates, e.g. a frequency),
  * because the TE walk does not depend on kappa.
  *
+ * Around that path the library also provides:
+ *  - TM models: vertical strips whose diffusion coefficient jumps, walked
+ *    with the interface rules of Sec. 3.1 (sdd_model_desc.diffusion);
+ *  - interpolation between Monte Carlo nodes along an interface (Sec. 5):
+ *    sdd_interpolate, sdd_interface_values_interp;
+ *  - apparent resistivity and phase at measurement sites (Sec. 2.1,
+ *    Sec. 4.2): sdd_apparent_resistivity;
+ *  - the RBF-FD sub-domain solve that completes the decomposition
+ *    (Sec. 3.2): sdd_rbffd_weights, sdd_rbffd_solve;
+ *  - batched, graph, allocation-free and served launches of the walk.
+ *
  * Conventions common to all entry points:
  *  - z grows downwards; air is z < 0, earth z >= 0.
  *  - All arrays are dense, row-major, little-endian, in the units stated.
