@@ -169,3 +169,25 @@ def test_interface_interp_rejects_bad_polylines():
         assert e.value.status == sdd.SDD_E_ARG
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_interface_interp_with_16_evaluations(kind):
+    """The block model's 16 evaluations (32 real components per node) along
+    the block's top edge and down its side."""
+    w = I.workload("block")
+    a = np.stack([np.linspace(-0.3, 0.2, 21), np.full(21, 0.15)], axis=1)
+    b = np.stack([np.full(20, 0.25), np.linspace(0.2, 0.6, 20)], axis=1)
+    nodes = np.concatenate([a, b])
+    n, stride = len(nodes), 5
+    ctx = sdd.sdd_create(w["model"])
+    try:
+        m, se, st = sdd.sdd_interface_values_interp(ctx, nodes, stride, 3000, kind, 1e-3, 23)
+        k = OI.knot_indices(n, stride)
+        assert m.shape == (n, 16) and st["walks"] == len(k) * 3000
+        kv = np.stack([m[k].real, m[k].imag], axis=-1)
+        ov, oe = OI.interface_interp(kv, se[k], nodes, stride, kind)
+        np.testing.assert_allclose(np.stack([m.real, m.imag], axis=-1), ov, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(se, oe, rtol=1e-12, atol=1e-15)
+    finally:
+        ctx.close()

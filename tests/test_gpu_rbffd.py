@@ -188,3 +188,31 @@ def test_stochastic_domain_decomposition_of_the_quarter_space():
     se_c = np.sqrt(se[:, 0, 0] ** 2 + se[:, 0, 1] ** 2).max()
     tol = 4 * se_c + 2 * pins.bias_bound(dt) + 2 * disc + ref_err.max()
     assert np.abs(u[inner] - ref[inner]).max() <= tol, (np.abs(u[inner] - ref[inner]).max(), tol)
+
+
+def test_weights_at_the_node_limit():
+    """SDD_RBFFD_MAX_NODES nodes (a jittered 512 x 512 grid): the stencils
+    and weights of 64 sampled nodes against the definition evaluated for
+    those nodes alone (nearest nodes by a full scan, a dense solve)."""
+    n_side = 512
+    assert n_side * n_side == sdd.SDD_RBFFD_MAX_NODES
+    rng = np.random.default_rng(17)
+    nodes, _ = I.rect_grid(0, 1, 0, 1, n_side, n_side)
+    h = 1.0 / (n_side - 1)
+    nodes = nodes + rng.uniform(-0.2 * h, 0.2 * h, nodes.shape)
+    eps = 20.0
+    st_g, w_g = sdd.sdd_rbffd_weights(nodes, 9, eps)
+    idx = np.arange(len(nodes))
+    for i in rng.choice(len(nodes), 64, replace=False):
+        dx = nodes[:, 0] - nodes[i, 0]
+        dz = nodes[:, 1] - nodes[i, 1]
+        want = np.lexsort((idx, dx * dx + dz * dz))[:9]
+        np.testing.assert_array_equal(st_g[i], want)
+        q = nodes[want]
+        r = np.hypot(q[:, None, 0] - q[None, :, 0], q[:, None, 1] - q[None, :, 1])
+        A = R.mq(r, eps)
+        b = R.mq_lap(np.hypot(q[:, 0] - nodes[i, 0], q[:, 1] - nodes[i, 1]), eps)
+        w_o = np.linalg.solve(A, b)
+        scale = np.linalg.norm(A, 2) * np.linalg.norm(w_g[i]) + np.linalg.norm(b)
+        assert np.linalg.norm(A @ w_g[i] - b) <= 1e-12 * scale
+        assert np.linalg.norm(w_g[i] - w_o) <= 1e-14 * np.linalg.cond(A) * np.linalg.norm(w_o)
