@@ -36,7 +36,7 @@ from paper_1603_09311_gb300 import inputs as I  # noqa: E402
 WORKLOAD = "quarterspace"
 METRIC = "walk-steps/s"
 # Algorithmic thread-instructions per Euler step of the single-precision walk
-# on the quarter-space model (derivation in the design doc): half a Philox4x32-10
+# on the quarter-space model: half a Philox4x32-10
 # call with the first round's fixed product precomputed (19.5), two uniforms
 # from bit masks (3), Box-Muller (7), Euler update (2), wall distances and the
 # bridge filter (5), the vertical-contact material test (4), two occupation
