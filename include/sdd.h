@@ -451,6 +451,17 @@ sdd_status sdd_apparent_resistivity(sdd_ctx *ctx, const double *sites_xz, int32_
                                     double *rho_se, double *phase_se, double *u0, double *uz,
                                     sdd_stats *stats);
 
+/* The arithmetic of sdd_apparent_resistivity on given three-point values:
+ *   values, se  host, [n_sites][3][n_eval][2]: estimates (re, im) and their
+ *               standard errors at (x, z0 - h), (x, z0), (x, z0 + h)
+ *   d_site      host, [n_sites] diffusion of each site's strip (TM), or NULL (TE)
+ *   h, kappa_ref, rho, phase, rho_se, phase_se, u0, uz as sdd_apparent_resistivity.
+ * Errors: SDD_E_ARG, SDD_E_CUDA. */
+sdd_status sdd_apparent_from_values(const double *values, const double *se, int32_t n_sites,
+                                    int32_t n_eval, double h, const double *kappa_ref,
+                                    const double *d_site, double *rho, double *phase,
+                                    double *rho_se, double *phase_se, double *u0, double *uz);
+
 /* ------------------------------------------------------------------------
  * RBF-FD sub-domain solve (Sec. 3.2).  Once the interface values are known,
  * a sub-domain of constant rate kappa (TE: Lap u = i kappa u; a TM strip of

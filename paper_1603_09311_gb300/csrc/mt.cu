@@ -120,6 +120,58 @@ struct MtScratch {
     }
 };
 
+// The kernel on host three-point estimates mean, se [3 n][E][2]; dsite
+// [n] (TM) or nullptr (TE).  Adds its time, launch and copies to stats.
+sdd_status mt_post(const double *mean, const double *se, int n_sites, int E, double h, const double *kappa_ref,
+                   const double *dsite, double *rho, double *phase, double *rho_se, double *phase_se, double *u0,
+                   double *uz, sdd_stats *stats) {
+    MtScratch S;
+    const bool tm = dsite != nullptr;
+    double *dm, *ds, *dk, *dd = nullptr, *orho, *oph, *orse = nullptr, *opse = nullptr, *ou0 = nullptr,
+                                                                                       *ouz = nullptr;
+    const size_t nv = (size_t)3 * n_sites * E * 2, no = (size_t)n_sites * E;
+    MT_CUDA(S.alloc(&dm, nv));
+    MT_CUDA(S.alloc(&ds, nv));
+    MT_CUDA(S.alloc(&dk, E));
+    if (tm) MT_CUDA(S.alloc(&dd, n_sites));
+    MT_CUDA(S.alloc(&orho, no));
+    MT_CUDA(S.alloc(&oph, no));
+    if (rho_se) MT_CUDA(S.alloc(&orse, no));
+    if (phase_se) MT_CUDA(S.alloc(&opse, no));
+    if (u0) MT_CUDA(S.alloc(&ou0, 2 * no));
+    if (uz) MT_CUDA(S.alloc(&ouz, 2 * no));
+    MT_CUDA(cudaStreamCreateWithFlags(&S.st, cudaStreamNonBlocking));
+    MT_CUDA(cudaEventCreate(&S.ev[0]));
+    MT_CUDA(cudaEventCreate(&S.ev[1]));
+    cudaStream_t st = S.st;
+    MT_CUDA(cudaMemcpyAsync(dm, mean, nv * sizeof(double), cudaMemcpyHostToDevice, st));
+    MT_CUDA(cudaMemcpyAsync(ds, se, nv * sizeof(double), cudaMemcpyHostToDevice, st));
+    MT_CUDA(cudaMemcpyAsync(dk, kappa_ref, E * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (tm) MT_CUDA(cudaMemcpyAsync(dd, dsite, n_sites * sizeof(double), cudaMemcpyHostToDevice, st));
+    MT_CUDA(cudaEventRecord(S.ev[0], st));
+    mt_kernel<<<(unsigned)((no + 127) / 128), 128, 0, st>>>(dm, ds, n_sites, E, h, dk, dd, orho, oph, orse,
+                                                           opse, ou0, ouz);
+    MT_CUDA(cudaGetLastError());
+    MT_CUDA(cudaEventRecord(S.ev[1], st));
+    MT_CUDA(cudaMemcpyAsync(rho, orho, no * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MT_CUDA(cudaMemcpyAsync(phase, oph, no * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (rho_se) MT_CUDA(cudaMemcpyAsync(rho_se, orse, no * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (phase_se) MT_CUDA(cudaMemcpyAsync(phase_se, opse, no * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (u0) MT_CUDA(cudaMemcpyAsync(u0, ou0, 2 * no * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (uz) MT_CUDA(cudaMemcpyAsync(uz, ouz, 2 * no * sizeof(double), cudaMemcpyDeviceToHost, st));
+    MT_CUDA(cudaStreamSynchronize(st));
+    if (stats) {
+        float ms = 0.f;
+        MT_CUDA(cudaEventElapsedTime(&ms, S.ev[0], S.ev[1]));
+        stats->post_ms = ms;
+        stats->launches += 1;
+        stats->h2d_bytes += 2 * nv * sizeof(double) + E * sizeof(double) + (tm ? n_sites * sizeof(double) : 0);
+        stats->d2h_bytes += no * sizeof(double) * (2 + (rho_se ? 1 : 0) + (phase_se ? 1 : 0) +
+                                                   (u0 ? 2 : 0) + (uz ? 2 : 0));
+    }
+    return SDD_OK;
+}
+
 }  // namespace
 }  // namespace sdd
 
@@ -163,48 +215,28 @@ extern "C" sdd_status sdd_apparent_resistivity(sdd_ctx *ctx, const double *sites
                                                cfg, mean.data(), se.data(), stats);
     if (mc != SDD_OK && mc != SDD_E_TRUNCATED) return mc;
 
-    MtScratch S;
-    double *dm, *ds, *dk, *dd = nullptr, *orho, *oph, *orse = nullptr, *opse = nullptr, *ou0 = nullptr,
-                                                                                       *ouz = nullptr;
-    const size_t nv = (size_t)np * E * 2, no = (size_t)n_sites * E;
-    MT_CUDA(S.alloc(&dm, nv));
-    MT_CUDA(S.alloc(&ds, nv));
-    MT_CUDA(S.alloc(&dk, E));
-    if (tm) MT_CUDA(S.alloc(&dd, n_sites));
-    MT_CUDA(S.alloc(&orho, no));
-    MT_CUDA(S.alloc(&oph, no));
-    if (rho_se) MT_CUDA(S.alloc(&orse, no));
-    if (phase_se) MT_CUDA(S.alloc(&opse, no));
-    if (u0) MT_CUDA(S.alloc(&ou0, 2 * no));
-    if (uz) MT_CUDA(S.alloc(&ouz, 2 * no));
-    MT_CUDA(cudaStreamCreateWithFlags(&S.st, cudaStreamNonBlocking));
-    MT_CUDA(cudaEventCreate(&S.ev[0]));
-    MT_CUDA(cudaEventCreate(&S.ev[1]));
-    cudaStream_t st = S.st;
-    MT_CUDA(cudaMemcpyAsync(dm, mean.data(), nv * sizeof(double), cudaMemcpyHostToDevice, st));
-    MT_CUDA(cudaMemcpyAsync(ds, se.data(), nv * sizeof(double), cudaMemcpyHostToDevice, st));
-    MT_CUDA(cudaMemcpyAsync(dk, kappa_ref, E * sizeof(double), cudaMemcpyHostToDevice, st));
-    if (tm) MT_CUDA(cudaMemcpyAsync(dd, dsite.data(), n_sites * sizeof(double), cudaMemcpyHostToDevice, st));
-    MT_CUDA(cudaEventRecord(S.ev[0], st));
-    mt_kernel<<<(unsigned)((no + 127) / 128), 128, 0, st>>>(dm, ds, n_sites, E, h, dk, dd, orho, oph, orse,
-                                                           opse, ou0, ouz);
-    MT_CUDA(cudaGetLastError());
-    MT_CUDA(cudaEventRecord(S.ev[1], st));
-    MT_CUDA(cudaMemcpyAsync(rho, orho, no * sizeof(double), cudaMemcpyDeviceToHost, st));
-    MT_CUDA(cudaMemcpyAsync(phase, oph, no * sizeof(double), cudaMemcpyDeviceToHost, st));
-    if (rho_se) MT_CUDA(cudaMemcpyAsync(rho_se, orse, no * sizeof(double), cudaMemcpyDeviceToHost, st));
-    if (phase_se) MT_CUDA(cudaMemcpyAsync(phase_se, opse, no * sizeof(double), cudaMemcpyDeviceToHost, st));
-    if (u0) MT_CUDA(cudaMemcpyAsync(u0, ou0, 2 * no * sizeof(double), cudaMemcpyDeviceToHost, st));
-    if (uz) MT_CUDA(cudaMemcpyAsync(uz, ouz, 2 * no * sizeof(double), cudaMemcpyDeviceToHost, st));
-    MT_CUDA(cudaStreamSynchronize(st));
-    if (stats) {
-        float ms = 0.f;
-        MT_CUDA(cudaEventElapsedTime(&ms, S.ev[0], S.ev[1]));
-        stats->post_ms = ms;
-        stats->launches += 1;
-        stats->h2d_bytes += 2 * nv * sizeof(double) + E * sizeof(double) + (tm ? n_sites * sizeof(double) : 0);
-        stats->d2h_bytes += no * sizeof(double) * (2 + (rho_se ? 1 : 0) + (phase_se ? 1 : 0) +
-                                                   (u0 ? 2 : 0) + (uz ? 2 : 0));
-    }
+    const sdd_status r = mt_post(mean.data(), se.data(), n_sites, E, h, kappa_ref, tm ? dsite.data() : nullptr,
+                                 rho, phase, rho_se, phase_se, u0, uz, stats);
+    if (r != SDD_OK) return r;
     return mc;
+}
+
+extern "C" sdd_status sdd_apparent_from_values(const double *values, const double *se, int32_t n_sites,
+                                               int32_t n_eval, double h, const double *kappa_ref,
+                                               const double *d_site, double *rho, double *phase,
+                                               double *rho_se, double *phase_se, double *u0, double *uz) {
+    if (n_sites < 0 || n_sites > SDD_MT_MAX_SITES) return mt_arg_error("n_sites must be in 0 .. SDD_MT_MAX_SITES");
+    if (n_eval < 1 || n_eval > SDD_MAX_EVAL) return mt_arg_error("n_eval must be in 1 .. SDD_MAX_EVAL");
+    if (!(h > 0.0) || !std::isfinite(h)) return mt_arg_error("h must be finite and > 0");
+    if (!kappa_ref) return mt_arg_error("kappa_ref must not be NULL");
+    for (int e = 0; e < n_eval; ++e)
+        if (!(kappa_ref[e] > 0.0) || !std::isfinite(kappa_ref[e]))
+            return mt_arg_error("kappa_ref must be finite and > 0");
+    if (n_sites == 0) return SDD_OK;
+    if (!values || !se || !rho || !phase) return mt_arg_error("values, se, rho and phase must not be NULL");
+    if (d_site)
+        for (int i = 0; i < n_sites; ++i)
+            if (!(d_site[i] > 0.0) || !std::isfinite(d_site[i])) return mt_arg_error("d_site must be finite and > 0");
+    return mt_post(values, se, n_sites, n_eval, h, kappa_ref, d_site, rho, phase, rho_se, phase_se, u0, uz,
+                   nullptr);
 }

@@ -14,6 +14,7 @@ The functions carry the names of the C entry points:
     sdd_interpolate(knots_s, values, se, targets_s, kind)
     sdd_interface_values_interp(ctx, nodes, stride, n_paths, kind, dt, seed, ...)
     sdd_apparent_resistivity(ctx, sites, h, n_paths, kappa_ref, dt, seed, ...)
+    sdd_apparent_from_values(values, se, h, kappa_ref, d_site=None)
     sdd_rbffd_weights(nodes, n_stencil, eps), sdd_rbffd_solve(nodes, dirichlet, values, kappa, ...)
     sdd_status_str(status), sdd_last_error()
 Models are the plain dicts of ``inputs.py``.
@@ -173,6 +174,10 @@ SIGNATURES = [
       P(ctypes.c_double), ctypes.c_double, ctypes.c_uint64, P(sdd_config), P(ctypes.c_double),
       P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
       P(ctypes.c_double), P(sdd_stats)]),
+    ("sdd_apparent_from_values", ctypes.c_int,
+     [P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+      P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double),
+      P(ctypes.c_double), P(ctypes.c_double), P(ctypes.c_double)]),
     ("sdd_rbffd_weights", ctypes.c_int,
      [P(ctypes.c_double), ctypes.c_int32, ctypes.c_int32, ctypes.c_double, P(ctypes.c_int32),
       P(ctypes.c_double)]),
@@ -550,6 +555,29 @@ def sdd_apparent_resistivity(ctx: Context, sites, h: float, n_paths: int, kappa_
     stats = {f: getattr(st_out, f) for f, _ in sdd_stats._fields_}
     stats["status"] = st
     out["stats"] = stats
+    return out
+
+
+def sdd_apparent_from_values(values, se, h: float, kappa_ref, d_site=None):
+    """The resistivity arithmetic on given values (complex [n][3][E]) and
+    standard errors ([n][3][E][2]); d_site [n] for TM, None for TE.  Returns
+    the dict of sdd_apparent_resistivity without stats."""
+    v = np.asarray(values, dtype=np.complex128)
+    n, _, E = v.shape
+    vv = np.ascontiguousarray(np.stack([v.real, v.imag], axis=-1))
+    ee = np.ascontiguousarray(np.asarray(se, dtype=np.float64).reshape(n, 3, E, 2))
+    kr = np.ascontiguousarray(np.broadcast_to(np.asarray(kappa_ref, dtype=np.float64), (E,)))
+    ds = None if d_site is None else np.ascontiguousarray(np.asarray(d_site, dtype=np.float64).reshape(n))
+    out = {k: np.zeros((n, E)) for k in ("rho", "phase", "rho_se", "phase_se")}
+    u0 = np.zeros((n, E, 2))
+    uz = np.zeros((n, E, 2))
+    st = lib().sdd_apparent_from_values(_dp(vv), _dp(ee), n, E, float(h), _dp(kr), None if ds is None else _dp(ds),
+                                        _dp(out["rho"]), _dp(out["phase"]), _dp(out["rho_se"]),
+                                        _dp(out["phase_se"]), _dp(u0), _dp(uz))
+    if st != SDD_OK:
+        raise SddError(st, "sdd_apparent_from_values")
+    out["u0"] = u0[..., 0] + 1j * u0[..., 1]
+    out["uz"] = uz[..., 0] + 1j * uz[..., 1]
     return out
 
 

@@ -4,9 +4,11 @@ through the C ABI, against the FP64 interpolation oracle.
 Both sides compute in FP64 and differ only in rounding order (a Thomas
 sweep per spline column on the GPU, a dense solve in the oracle), so values
 agree to 1e-12 of the largest knot value and standard errors to 1e-12
-relative.  The end-to-end call is checked in two parts: its knots against
-sdd_interface_values on the whole polyline (same node ids), and its other
-nodes against the oracle's interpolation of those knot values.
+relative.  The end-to-end call is checked without handing any GPU result to
+the oracle: its knots against sdd_interface_values on the whole polyline
+(same node ids), its other nodes against sdd_interpolate of those knots,
+and the whole of it against the oracle's own walks and interpolation within
+4 combined standard errors + 1e-4.
 """
 import numpy as np
 import pytest
@@ -80,6 +82,17 @@ def test_interpolate_without_standard_errors():
     _close(gv, OI.interpolate(s, v, np.zeros_like(v), t, OI.SPLINE)[0], np.abs(v).max())
 
 
+def _interp_of_knots(nodes, k, m, se, kind):
+    """sdd_interpolate of the GPU's knot values at every node (arc lengths of
+    the test's polyline)."""
+    s = OI.arc_length(nodes)
+    E = m.shape[1]
+    kv = np.stack([m[k].real, m[k].imag], axis=-1).reshape(len(k), -1)
+    gv, ge = sdd.sdd_interpolate(s[k], kv, se[k].reshape(len(k), -1), s, kind)
+    gv = gv.reshape(len(nodes), E, 2)
+    return gv[..., 0] + 1j * gv[..., 1], ge.reshape(len(nodes), E, 2)
+
+
 def _line(n):
     # a bent interface polyline inside the quarter-space model: down x = 0,
     # then along a slanted segment
@@ -105,13 +118,36 @@ def test_interface_interp_end_to_end(kind, n, stride):
         # summation order of the walks' samples
         np.testing.assert_allclose(m[k], full[k], rtol=0, atol=1e-12)
         np.testing.assert_allclose(se[k], fse[k], rtol=1e-10, atol=1e-15)
-        # other nodes: the oracle's interpolation of the knot values
-        kv = np.stack([m[k].real, m[k].imag], axis=-1)
-        ov, oe = OI.interface_interp(kv, se[k], nodes, stride, kind)
-        np.testing.assert_allclose(np.stack([m.real, m.imag], axis=-1), ov, rtol=0, atol=1e-12)
-        np.testing.assert_allclose(se, oe, rtol=1e-12, atol=1e-15)
+        # other nodes: the standalone interpolation of those knot values
+        gv, ge = _interp_of_knots(nodes, k, m, se, kind)
+        np.testing.assert_allclose(m, gv, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(se, ge, rtol=1e-12, atol=1e-15)
     finally:
         ctx.close()
+
+
+@pytest.mark.parametrize("kind,n,stride", [(sdd.SDD_INTERP_SPLINE, 41, 4), (sdd.SDD_INTERP_LINEAR, 9, 3)])
+def test_interface_interp_against_the_oracle_pipeline(kind, n, stride):
+    """The oracle's walks at the knots (same streams) and its interpolation,
+    against the GPU call, at every node within 4 combined standard errors
+    + 1e-4 (the propagated errors of both)."""
+    w = I.workload("quarterspace")
+    nodes = _line(n)
+    paths, dt, seed = 3000, 1e-3, 24
+    ctx = sdd.sdd_create(w["model"])
+    try:
+        m, se, _ = sdd.sdd_interface_values_interp(ctx, nodes, stride, paths, kind, dt, seed)
+    finally:
+        ctx.close()
+    k = OI.knot_indices(n, stride)
+    refs = [O.interface_values(w["model"], nodes[j], paths, dt, seed, urule=23, node_id0=int(j)) for j in k]
+    kv = np.stack([np.concatenate([r["mean"] for r in refs]).real,
+                   np.concatenate([r["mean"] for r in refs]).imag], axis=-1)
+    kse = np.concatenate([r["se"] for r in refs])
+    ov, oe = OI.interface_interp(kv, kse, nodes, stride, kind)
+    tol = 4 * np.sqrt(se ** 2 + oe ** 2) + 1e-4
+    assert np.all(np.abs(m.real - ov[..., 0]) <= tol[..., 0])
+    assert np.all(np.abs(m.imag - ov[..., 1]) <= tol[..., 1])
 
 
 def test_interface_interp_knots_against_walk_oracle():
@@ -143,16 +179,21 @@ def test_interface_interp_full_size():
     n = len(nodes)
     ctx = sdd.sdd_create(w["model"])
     try:
+        k = OI.knot_indices(n, 4)
         for kind in KINDS:
             m, se, st = sdd.sdd_interface_values_interp(ctx, nodes, 4, 100_000, kind, w["dt"], w["seed"])
-            k = OI.knot_indices(n, 4)
             assert st["walks"] == len(k) * 100_000
-            kv = np.stack([m[k].real, m[k].imag], axis=-1)
-            ov, oe = OI.interface_interp(kv, se[k], nodes, 4, kind)
-            np.testing.assert_allclose(np.stack([m.real, m.imag], axis=-1), ov, rtol=0, atol=1e-12)
-            np.testing.assert_allclose(se, oe, rtol=1e-12, atol=1e-15)
+            gv, ge = _interp_of_knots(nodes, k, m, se, kind)
+            np.testing.assert_allclose(m, gv, rtol=0, atol=1e-12)
+            np.testing.assert_allclose(se, ge, rtol=1e-12, atol=1e-15)
     finally:
         ctx.close()
+    # one knot recomputed by the oracle's walks under its node id
+    j = int(k[len(k) // 2])
+    ref = O.interface_values(w["model"], nodes[j], 100_000, w["dt"], w["seed"], urule=23, node_id0=j)
+    d = m[j] - ref["mean"][0]
+    tol = 4 * np.sqrt(se[j] ** 2 + ref["se"][0] ** 2) + 1e-4
+    assert np.all(np.abs(d.real) <= tol[..., 0]) and np.all(np.abs(d.imag) <= tol[..., 1])
 
 
 def test_interface_interp_rejects_bad_polylines():
@@ -185,9 +226,8 @@ def test_interface_interp_with_16_evaluations(kind):
         m, se, st = sdd.sdd_interface_values_interp(ctx, nodes, stride, 3000, kind, 1e-3, 23)
         k = OI.knot_indices(n, stride)
         assert m.shape == (n, 16) and st["walks"] == len(k) * 3000
-        kv = np.stack([m[k].real, m[k].imag], axis=-1)
-        ov, oe = OI.interface_interp(kv, se[k], nodes, stride, kind)
-        np.testing.assert_allclose(np.stack([m.real, m.imag], axis=-1), ov, rtol=0, atol=1e-12)
-        np.testing.assert_allclose(se, oe, rtol=1e-12, atol=1e-15)
+        gv, ge = _interp_of_knots(nodes, k, m, se, kind)
+        np.testing.assert_allclose(m, gv, rtol=0, atol=1e-12)
+        np.testing.assert_allclose(se, ge, rtol=1e-12, atol=1e-15)
     finally:
         ctx.close()

@@ -1,8 +1,10 @@
 """Apparent resistivity and phase at measurement sites (Sec. 2.1, Sec. 4.2)
 on the GPU, through the C ABI.
 
-- The kernel's arithmetic against the oracle (`oracle/mt.py`) applied to the
-  same three-point estimates: 1e-12 relative (both FP64).
+- The kernel's arithmetic (the standalone entry point) against the oracle
+  (`oracle/mt.py`) on the same test-generated three-point values: 1e-12
+  relative (both FP64); the site call equals the walks followed by that
+  arithmetic.
 - The whole path against closed forms: a TE half-space (the column solution
   is the exact field, so the centred difference of e^{-kz} gives rho and
   phi at any h), and the TM analytic test model (u linear in z, so the
@@ -46,34 +48,56 @@ def _points_values(ctx, sites, h, paths, dt, seed):
 
 
 @pytest.mark.parametrize("which", ["te", "tm"])
-def test_kernel_matches_oracle_formulas(which):
+def test_formulas_match_oracle_on_given_values(which):
+    """The kernel's arithmetic on test-generated three-point values (the
+    standalone entry point) against the oracle's formulas on the same values."""
+    rng = np.random.default_rng(40 + (which == "tm"))
+    n, E, h = 50, 3, 0.05
+    base = rng.normal(size=(n, 1, E)) + 1j * rng.normal(size=(n, 1, E))
+    slope = rng.normal(size=(n, 1, E)) + 1j * rng.normal(size=(n, 1, E))
+    v = base + slope * h * np.array([-1.0, 0.0, 1.0])[None, :, None] \
+        + 0.01 * (rng.normal(size=(n, 3, E)) + 1j * rng.normal(size=(n, 3, E)))
+    se = rng.uniform(1e-4, 1e-2, (n, 3, E, 2))
+    kr = rng.uniform(0.5, 20.0, E)
+    d_site = rng.uniform(0.1, 10.0, n) if which == "tm" else None
+    mode = OM.TE if which == "te" else OM.TM
+    ds = 1.0 if d_site is None else d_site[:, None]
+    r = sdd.sdd_apparent_from_values(v, se, h, kr, d_site)
+    rho, phi, uz = OM.apparent(v[:, 0], v[:, 1], v[:, 2], h, kr, mode, d_site=ds)
+    rse, pse = OM.apparent_se(v[:, 0], v[:, 1], v[:, 2], se[:, 0], se[:, 1], se[:, 2], h, kr, mode, d_site=ds)
+    np.testing.assert_allclose(r["rho"], rho, rtol=1e-12)
+    np.testing.assert_allclose(r["phase"], phi, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(r["rho_se"], rse, rtol=1e-11)
+    np.testing.assert_allclose(r["phase_se"], pse, rtol=1e-11)
+    np.testing.assert_array_equal(r["u0"], v[:, 1])
+    np.testing.assert_allclose(r["uz"], uz, rtol=1e-13)
+
+
+@pytest.mark.parametrize("which", ["te", "tm"])
+def test_sites_equal_the_standalone_arithmetic(which):
+    """sdd_apparent_resistivity is the walks at the three points (the values
+    sdd_interface_values gives them under the same node ids) followed by the
+    standalone arithmetic."""
     if which == "te":
         model, kr = _halfspace3()
         sites = np.array([[-0.5, 0.3], [0.0, 0.02], [0.4, 0.6], [0.9, 0.1]])
-        d_site = 1.0
+        d_site = None
     else:
         model = I.tm_analytic()
         kr = np.array([10.0])
         sites = np.array([[-0.5, 0.2], [0.3, -0.4], [0.6, 0.5], [0.0, 0.1]])
-        d_site = np.array([OM.strip_diffusion(model, x) for x in sites[:, 0]])[:, None]
+        d_site = np.array([OM.strip_diffusion(model, x) for x in sites[:, 0]])
     ctx = sdd.sdd_create(model)
     try:
         h, paths, dt, seed = 0.05, 3000, 1e-3, 31
         r = sdd.sdd_apparent_resistivity(ctx, sites, h, paths, kr, dt, seed)
         assert r["stats"]["walks"] == 3 * len(sites) * paths
         m, se = _points_values(ctx, sites, h, paths, dt, seed)
-        mode = OM.TE if which == "te" else OM.TM
-        rho, phi, uz = OM.apparent(m[:, 0], m[:, 1], m[:, 2], h, kr, mode, d_site=d_site)
-        rse, pse = OM.apparent_se(m[:, 0], m[:, 1], m[:, 2], se[:, 0], se[:, 1], se[:, 2], h, kr, mode,
-                                  d_site=d_site)
-        np.testing.assert_allclose(r["rho"], rho, rtol=1e-10)
-        np.testing.assert_allclose(r["phase"], phi, rtol=0, atol=1e-10)
-        np.testing.assert_allclose(r["rho_se"], rse, rtol=1e-9)
-        np.testing.assert_allclose(r["phase_se"], pse, rtol=1e-9)
-        np.testing.assert_allclose(r["u0"], m[:, 1], rtol=0, atol=1e-12)
-        np.testing.assert_allclose(r["uz"], uz, rtol=1e-10)
     finally:
         ctx.close()
+    q = sdd.sdd_apparent_from_values(m, se, h, kr, d_site)
+    for k in ("rho", "phase", "rho_se", "phase_se", "u0", "uz"):
+        np.testing.assert_allclose(r[k], q[k], rtol=1e-10, atol=1e-12)
 
 
 def _bias(rho, u, uz, h, dt):
@@ -144,6 +168,13 @@ def test_three_points_against_walk_oracle():
     tol = 4 * np.sqrt(se.reshape(3, -1, 2) ** 2 + ref["se"] ** 2) + 1e-4
     assert np.all(np.abs(d.real) <= tol[..., 0]) and np.all(np.abs(d.imag) <= tol[..., 1])
     np.testing.assert_allclose(r["u0"][0], m[0, 1], atol=1e-12)
+    # the oracle's whole path (its walks, then its formulas) against the
+    # GPU's, within 4 combined first-order standard errors
+    om, ose = ref["mean"], ref["se"]
+    rho_o, phi_o, _ = OM.apparent(om[0], om[1], om[2], h, kr, OM.TE)
+    rse_o, pse_o = OM.apparent_se(om[0], om[1], om[2], ose[0], ose[1], ose[2], h, kr, OM.TE)
+    assert np.all(np.abs(r["rho"][0] - rho_o) <= 4 * np.hypot(r["rho_se"][0], rse_o) + 1e-6)
+    assert np.all(np.abs(r["phase"][0] - phi_o) <= 4 * np.hypot(r["phase_se"][0], pse_o) + 1e-6)
 
 
 def test_edge_cases():
