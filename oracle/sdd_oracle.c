@@ -29,7 +29,9 @@
  *      last paragraph before the Remark): t_w = -2 d d'/log U <= dt.
  *   5. Not exited: dt is added to the occupation time of the material in
  *      which beta' lies (Sec. 3.1, no regime change when the diffusion
- *      coefficients agree), beta = beta', n += 1.
+ *      coefficients agree), beta = beta', n += 1.  (Pinned by one- and
+ *      four-step walks beside a material edge: the count lands in the
+ *      material with the Gaussian probability of the step's end point.)
  *   6. On exit at fraction theta of the step: the partial time theta*dt is
  *      charged to the material of beta^n, the exit point is the interpolated
  *      point beta + theta (beta' - beta) placed exactly on the hit wall, and
@@ -79,9 +81,10 @@
  * the strip on the left.
  * Pins (tests/test_oracle_pins.py): the flux-continuous solution int dx/D
  * (kappa = 0), the analytic test model, finite volumes with phase and flux,
- * equal D = the TE walk.  Parity unpinned: the occupation split of step 3
- * moves O(dt) per hit, below the resolution of every pin; it is checked only
- * by conservation of time and by path-by-path GPU equality.
+ * equal D = the TE walk; the occupation split of step 3 by one-step walks
+ * from a known distance of the interface (hit probability 2 Phi(-a/s) by the
+ * reflection principle, mean occupation against its integral over the
+ * Gaussian step and the hitting-time law) and from a start on it.
  * The TM uniforms U_alpha, disc radius and disc angle are words 1, 2, 3 of
  * the Philox call with counter (n, r, node, 2), by the urule.
  *

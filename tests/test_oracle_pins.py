@@ -243,6 +243,73 @@ def test_quarterspace_matches_finite_differences():
         assert abs((mu - ref).imag) <= 4 * se[1] + pins.bias_bound(dt) + err
 
 
+# --------------------------------------------------------- occupation rule
+
+@pytest.mark.parametrize("urule", [32, 23])
+def test_occupation_counts_the_material_at_the_end_of_each_step(urule):
+    # Sec. 3.1 gives a step's dt to the material in which beta^(n+1) lies.
+    # With every wall far away (no walk can exit in a few steps) and a
+    # material B = {x >= b}, step k is counted in B with probability
+    # P(x0 + sqrt(k dt) N >= b) = Phi((x0 - b) / sqrt(k dt)), so the expected
+    # count in B after n steps is that sum over k = 1..n.  Counting the left
+    # endpoint instead would give 0 (x0 < b) or 1 (x0 >= b) for n = 1.
+    dt, b = 1e-2, 0.0
+    m = {"domain": (-5.0, 5.0, -5.0, 5.0), "kappa": [[0.0, 0.0]], "bg": (0, 0),
+         "shapes": [(0, 1, (b, 10.0, -10.0, 10.0, 0.0, 0.0))], "g": ("affine", 1.0, 0.0, 0.0)}
+    N = 40000
+    for x0, n_steps in ((b - 0.05, 1), (b + 0.03, 1), (b - 0.1, 4)):
+        rec = O.walk_records(m, (x0, 0.3), 0, 0, N, dt, 19, urule=urule, max_steps=n_steps)
+        assert np.all(rec["truncated"] == 1) and np.all(rec["steps"] == n_steps)
+        assert np.all(rec["counts"].sum(1) == n_steps)
+        cnt = rec["counts"][:, 1].astype(float)
+        want = sum(stats.norm.cdf((x0 - b) / math.sqrt(k * dt)) for k in range(1, n_steps + 1))
+        se = cnt.std(ddof=1) / math.sqrt(N)
+        assert abs(cnt.mean() - want) <= 4 * se, (x0, n_steps, cnt.mean(), want, se)
+
+
+# ------------------------------------------------ finite-difference brute force
+
+@pytest.mark.slow
+def test_triangle_matches_finite_differences():
+    # The triangle model of the dt sweep (rate 50 inside, host 2) has no
+    # closed form.  Finite differences with the rate averaged over each
+    # node's dual cell (the triangle clipped against the cell, so the slanted
+    # edges need no point-in-triangle test) on h = 1/40, 1/80, 1/160,
+    # Richardson-extrapolated from the two finest; nodes on two edges, inside,
+    # outside and below.  A triangle of the wrong orientation (empty) or the
+    # wrong rate misses by hundreds of standard errors.
+    pts = [(0.0, 0.2), (0.0, 0.4), (0.15, 0.4), (0.5, 0.5), (0.0, 0.7)]
+    kfn = pins.kappa_cell_average(2.0, [(I.TRIANGLE, 50.0)])
+    ref, err, ratio = pins.fd_richardson3(kfn, DOM, 2.0, 2.0, pts)
+    assert np.all((ratio > 3.5) & (ratio < 4.5)), ratio  # second order observed
+    dt = 1e-3
+    r = O.interface_values(I.triangle(), pts, 200000, dt, 13)
+    for mu, se, want, e in zip(r["mean"][:, 0], r["se"][:, 0, :], ref, err):
+        assert abs((mu - want).real) <= 4 * se[0] + pins.bias_bound(dt) + e
+        assert abs((mu - want).imag) <= 4 * se[1] + pins.bias_bound(dt) + e
+
+
+@pytest.mark.slow
+def test_block_matches_finite_differences():
+    # The block of the batched workload at frequency scale 1, both block
+    # rates (20 and 0.2, host 2) as the two rows of one evaluation table:
+    # finite differences as for the triangle, the block clipped against each
+    # dual cell; nodes on the block's top and right edges, at its centre,
+    # outside and below it.
+    pts = [(0.0, 0.2), (0.2, 0.35), (0.0, 0.35), (-0.45, 0.35), (0.0, 0.6)]
+    m = I.block_batched(scales=[1.0])
+    dt = 1e-3
+    r = O.interface_values(m, pts, 150000, dt, 23)
+    verts = I.rect_vertices(I.BLOCK)
+    for e, kb in enumerate((20.0, 0.2)):
+        kfn = pins.kappa_cell_average(2.0, [(verts, kb)])
+        ref, err, ratio = pins.fd_richardson3(kfn, DOM, 2.0, 2.0, pts)
+        assert np.all((ratio > 3.5) & (ratio < 4.5)), ratio
+        for mu, se, want, er in zip(r["mean"][:, e], r["se"][:, e, :], ref, err):
+            assert abs((mu - want).real) <= 4 * se[0] + pins.bias_bound(dt) + er, (e, mu, want, se)
+            assert abs((mu - want).imag) <= 4 * se[1] + pins.bias_bound(dt) + er, (e, mu, want, se)
+
+
 def test_block_model_is_symmetric_in_x():
     m = I.block_batched(scales=[1.0, 10.0])
     pts = [(-0.2, 0.35), (0.15, 0.55)]
@@ -411,3 +478,76 @@ def test_tm_walks_hit_interfaces_and_conserve_time():
     want = rec["steps"] - 1 + disc_exit
     assert np.allclose(rec["occ"][ok].sum(1), want[ok], rtol=0, atol=1e-9)
     assert 0 < disc_exit.sum() < 50
+
+
+# The TM occupation split (Sec. 3.1, read as: staying on side i gives
+# T_i = dt - (1/2)(dt - t_g) p_i, T_j = (1/2)(dt - t_g) p_i; moving to side j
+# gives T_i = t_g + (1/2)(dt - t_g) p_j and T_j the rest of dt).  Averaged over
+# the side drawn with p_i = D_i/(D_i + D_j), a hit at t_g = th dt leaves
+# E[T_i] = (th + (1/2)(1 - th)) dt whatever the diffusions: the time after the
+# hit is shared evenly on average.  Swapping p_i and p_j in the split gives
+# E[T_i] = (1 - p_j (1 - th)) dt instead.
+
+def _tm_one_step_expectation(c):
+    """E[(1 - th) 1{hit}] for one step of standard deviation s from distance
+    a = c s to a straight interface (no wall within reach): crossed steps
+    (w >= c) have th = c / w; the others hit with probability exp(-g),
+    g = 2 c (c - w), at th = g / (g + E), E ~ Exp(1), whose mean of 1 - th is
+    1 - g e^g E1(g)."""
+    from scipy import integrate, special
+    phi = stats.norm.pdf
+    crossed, _ = integrate.quad(lambda w: phi(w) * (1.0 - c / w), c, np.inf, epsabs=1e-12)
+
+    def bridge(w):
+        g = 2.0 * c * (c - w)
+        return phi(w) * (np.exp(-g) - (g * special.exp1(g) if g > 0 else 0.0))
+    bridged, _ = integrate.quad(bridge, -np.inf, c, epsabs=1e-12)
+    return crossed + bridged
+
+
+@pytest.mark.parametrize("start", ["left", "right"])
+def test_tm_occupation_split_after_one_hit(start):
+    # One step from distance a of the interface x = 0 (D = 1 | 10), walls far
+    # away.  The hit probability is the reflection principle's 2 Phi(-a/s)
+    # (s the step's standard deviation); the occupation of the starting
+    # strip has mean 1 - (1/2) E[(1 - th) 1{hit}] (in units of dt).
+    dt = 1e-3
+    D = (1.0, 10.0)
+    m = _tm(D, (0.0,), (0.0, 0.0), domain=(-3.0, 3.0, -3.0, 3.0))
+    i = 0 if start == "left" else 1
+    s = math.sqrt(D[i] * dt)
+    c = 0.6
+    x0 = -c * s if start == "left" else c * s
+    N = 100000
+    rec = O.walk_records(m, (x0, 0.2), 0, 0, N, dt, 29, max_steps=1)
+    assert np.all(rec["steps"] == 1) and np.all(rec["truncated"] == 1)
+    assert np.allclose(rec["occ"].sum(1), 1.0, rtol=0, atol=1e-12)
+    hit = rec["hits"].astype(float)
+    p_hit = 2.0 * stats.norm.cdf(-c)
+    assert abs(hit.mean() - p_hit) <= 4 * math.sqrt(p_hit * (1 - p_hit) / N)
+    Ti = rec["occ"][:, i]
+    want = 1.0 - 0.5 * _tm_one_step_expectation(c)
+    assert abs(Ti.mean() - want) <= 4 * Ti.std(ddof=1) / math.sqrt(N), (Ti.mean(), want)
+    # the swapped split would sit (1/2 - p_j) E[(1 - th) 1{hit}] away
+    pj = D[1 - i] / (D[0] + D[1])
+    assert abs(0.5 - pj) * _tm_one_step_expectation(c) > 40 * Ti.std(ddof=1) / math.sqrt(N)
+
+
+def test_tm_occupation_split_of_a_start_on_the_interface():
+    # A walk that starts on the interface has hit it at t_g = 0 from the left
+    # strip: each strip's mean occupation of the first step is dt/2, and the
+    # walk resumes on the right with the crossing probability D_R/(D_L + D_R)
+    # (the disc is tangent to the interface on the side drawn).
+    dt = 1e-3
+    for D in ((1.0, 10.0), (10.0, 1.0), (4.0, 0.5)):
+        m = _tm(D, (0.0,), (0.0, 0.0), domain=(-3.0, 3.0, -3.0, 3.0))
+        N = 60000
+        rec = O.walk_records(m, (0.0, 0.2), 0, 0, N, dt, 31, max_steps=1)
+        assert np.all(rec["hits"] == 1)
+        occ = rec["occ"]
+        assert np.allclose(occ.sum(1), 1.0, rtol=0, atol=1e-12)
+        for k in (0, 1):
+            assert abs(occ[:, k].mean() - 0.5) <= 4 * occ[:, k].std(ddof=1) / math.sqrt(N)
+        right = (rec["m_last"] == 1).astype(float)
+        pr = D[1] / (D[0] + D[1])
+        assert abs(right.mean() - pr) <= 4 * math.sqrt(pr * (1 - pr) / N)
