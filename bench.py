@@ -12,8 +12,13 @@ earth kappa 2 left / 20 right, air 0), single-precision walk with FP64 sums.
   cpu_baseline  the FP64 oracle on the host cores, on a bounded sample
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-Under torchrun (N > 1) every rank runs the whole workload on its own node ids
-(weak scaling, no collective on the data path); rank 0 prints the line.
+Under torchrun (N > 1) the ranks split one evaluation by (node, path-range)
+units (shard.py): weak scaling (default) evaluates the 64 nodes with N x 1e5
+walks each, strong scaling (--scaling strong) the 1e5 of one GPU's line.
+Each rank walks a cost-balanced contiguous slice of the range list, one
+all-reduce SUM of the zero-padded range-sum tables (NCCL) hands every rank
+every range's sums, and each forms the node means in range order; rank 0
+prints the line.
 """
 from __future__ import annotations
 
@@ -48,6 +53,15 @@ INST_PER_STEP = 45
 # interface product and filter 4) and the occupation update in shared memory
 # (address and add, 2).
 TM_INST_PER_STEP = 47
+# The same count for the other lookup programs of the single-precision walk
+# (the contact test's 4 replaced): one rectangle in the layered half-space
+# (earth test and select 2, four compares and a select 5): 48; one triangle
+# (earth test and select 2, three edge functions of two FMAs and a compare 9,
+# a select 1): 53.
+RECT_INST_PER_STEP = 48
+TRI_INST_PER_STEP = 53
+# Walks per node of the double-precision leg of the triangle sweep.
+FP64_WALKS = 50_000
 
 
 def traffic_per_launch():
@@ -349,6 +363,144 @@ def tm_measure(sdd, torch, dev, peak_tinst, n_steps, cpu=True):
     return out
 
 
+def device_launches(sdd, torch, dev, ctx, w, dt, seeds, flush, precision="fp32"):
+    """Device-buffer launches of a workload, one per seed, L2 flushed before
+    each; CUDA events on the launching stream.  Returns (ms per launch,
+    steps per launch, walks per launch)."""
+    n = len(w["nodes"])
+    d_nodes = torch.tensor(w["nodes"], dtype=torch.float64, device=dev)
+    d_ids = torch.arange(n, dtype=torch.int32, device=dev)
+    d_mean = torch.empty((n, ctx.E, 2), dtype=torch.float64, device=dev)
+    d_se = torch.empty_like(d_mean)
+    d_cnt = torch.zeros((len(seeds), 3), dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    evs = []
+    for k, sd in enumerate(seeds):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sdd.sdd_interface_values_device(ctx, d_nodes.data_ptr(), n, w["n_paths"], dt, sd, d_mean.data_ptr(),
+                                        d_se.data_ptr(), d_node_ids_ptr=d_ids.data_ptr(),
+                                        d_counters_ptr=d_cnt[k].data_ptr(), stream=stream.cuda_stream,
+                                        precision=precision)
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    cnt = d_cnt.cpu().numpy()
+    return [a.elapsed_time(b) for a, b in evs], cnt[:, 0].astype(float), cnt[:, 1].astype(float)
+
+
+def _dev_stats(d):
+    """Largest and rms of |d| (an array of deviations)."""
+    d = np.abs(np.asarray(d, dtype=float)).ravel()
+    return {"max": float(d.max()), "rms": float(np.sqrt((d ** 2).mean()))}
+
+
+def fp32_error(sdd, ctx, w, idx, n_sub, dt, seed, ref_cache=None):
+    """The single-precision walk against the FP64 oracle on the same random
+    streams: nodes idx under their own node ids, the first n_sub walks of
+    each, the oracle with the same 23-bit uniform rule.  Returns |GPU -
+    oracle| (absolute, and in units of the oracle's standard error) over
+    every node, evaluation and component, and the oracle's own timing."""
+    from oracle import oracle as O
+    idx = [int(j) for j in idx]
+    nodes = w["nodes"][idx]
+    m32, s32, st = sdd.sdd_interface_values(ctx, nodes, n_sub, dt, seed,
+                                            node_ids=np.asarray(idx, dtype=np.uint32))
+    t = time.perf_counter()
+    ref, ref_se, steps = [], [], 0
+    for j in idx:
+        r = O.interface_values(w["model"], w["nodes"][j:j + 1], n_sub, dt, seed, urule=23, node_id0=j)
+        ref.append(r["mean"][0])
+        ref_se.append(r["se"][0])
+        steps += r["steps"]
+    sec = time.perf_counter() - t
+    ref, ref_se = np.array(ref), np.array(ref_se)
+    d = m32 - ref
+    d2 = np.stack([d.real, d.imag], axis=-1)
+    out = {"nodes": idx, "walks_per_node": int(n_sub), "dt": dt, "streams": "same (23-bit uniform rule)",
+           "abs": _dev_stats(d2), "in_se": _dev_stats(d2 / ref_se),
+           "se_median": float(np.median(ref_se)),
+           "step_totals": {"gpu": int(st["steps"]), "oracle": int(steps)}}
+    return out, {"value": steps / sec, "unit": METRIC, "cores": O.max_threads(), "kind": "oracle",
+                 "sample": f"nodes {idx} x first {n_sub} walks, dt {dt} ({steps:.3e} steps, {sec:.1f} s)"}
+
+
+def block_measure(sdd, torch, dev, peak_tinst, flush, reps=2, cpu=True):
+    """The batched block workload in full: 256 nodes on the perimeter of the
+    block [-0.2,0.2]x[0.2,0.5] (rates 20 and 0.2 in host 2, x 8 frequency
+    scales = 16 evaluations per walk), walks per node log-uniform in
+    [1e4, 1e6] (5.5e7 walks), dt 1e-4, one launch; walk-steps/s of the
+    device entry point and its issue roofline."""
+    w = I.workload("block")
+    ctx = sdd.sdd_create(w["model"])
+    sdd.sdd_interface_values(ctx, w["nodes"][:4], 2000, w["dt"], 1)  # loads the kernel
+    ms, steps, walks = device_launches(sdd, torch, dev, ctx, w, w["dt"],
+                                       [w["seed"] + k for k in range(reps)], flush)
+    value = float(steps.sum() / (sum(ms) * 1e-3))
+    ach = RECT_INST_PER_STEP * value / 1e12
+    out = {"metric": METRIC, "value": value, "unit": METRIC, "ms_per_launch": statistics.mean(ms),
+           "launches": reps, "steps_per_launch": float(steps.mean()), "walks_per_launch": float(walks.mean()),
+           "workload": "block in half-space: 256 perimeter nodes, 1e4-1e6 walks per node (log-uniform, "
+                       "seed 3), 16 evaluations per walk (rates 20 | 0.2 x 8 scales 0.1-100), dt 1e-4, "
+                       "one launch, FP32 walk, FP64 sums",
+           "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tinst, "unit": "Tinst/s",
+                        "frac": ach / peak_tinst, "inst_per_step": RECT_INST_PER_STEP}}
+    if cpu:
+        # the four nodes with the fewest walks, their first 20000 walks
+        idx = np.argsort(w["n_paths"])[:4]
+        out["fp32_error"], out["cpu_baseline"] = fp32_error(sdd, ctx, w, idx, 20000, w["dt"], w["seed"])
+    ctx.close()
+    return out
+
+
+def triangle_measure(sdd, torch, dev, peak_tinst, flush, cpu=True):
+    """The triangle time-step sweep in full: 128 nodes on the edges of the
+    triangle (-0.3,0.2),(0.3,0.2),(0,0.6) (rate 50 in host 2), 1e6 walks per
+    node, dt in {1e-3, 3e-4, 1e-4, 3e-5}, one FP32 launch per dt; the FP64
+    walk on four of the nodes at each dt (its own 32-bit uniform stream), and
+    the FP32 error against the oracle on the same streams."""
+    w = I.workload("triangle")
+    ctx = sdd.sdd_create(w["model"])
+    sdd.sdd_interface_values(ctx, w["nodes"][:4], 2000, 1e-3, 1)
+    sub = [0, 40, 85, 127]
+    per_dt, tot_steps, tot_ms = [], 0.0, 0.0
+    for dt in (1e-3, 3e-4, 1e-4, 3e-5):
+        ms, steps, walks = device_launches(sdd, torch, dev, ctx, w, dt, [w["seed"]], flush)
+        m32, s32, _ = sdd.sdd_interface_values(ctx, w["nodes"][sub], w["n_paths"][sub], dt, w["seed"],
+                                               node_ids=np.asarray(sub, dtype=np.uint32))
+        t = time.perf_counter()
+        m64, s64, st64 = sdd.sdd_interface_values(ctx, w["nodes"][sub], FP64_WALKS, dt, w["seed"],
+                                                  node_ids=np.asarray(sub, dtype=np.uint32), precision="fp64")
+        t64 = time.perf_counter() - t
+        d = m32 - m64
+        cse = np.sqrt(s32 ** 2 + s64 ** 2)
+        d2 = np.stack([d.real, d.imag], axis=-1)
+        v = float(steps[0] / (ms[0] * 1e-3))
+        ent = {"dt": dt, "value": v, "ms": ms[0], "steps": float(steps[0]), "walks": float(walks[0]),
+               "frac": TRI_INST_PER_STEP * v / 1e12 / peak_tinst,
+               "fp32_vs_gpu_fp64": {"nodes": sub, "walks_fp32": 1_000_000, "walks_fp64": FP64_WALKS,
+                                    "streams": "independent (23- and 32-bit uniform rules)",
+                                    "abs": _dev_stats(d2), "in_combined_se": _dev_stats(d2 / cse),
+                                    "fp64_steps_per_s": st64["steps"] / (st64["kernel_ms"] * 1e-3),
+                                    "fp64_seconds": t64}}
+        if cpu:
+            n_sub = int(min(100_000, max(2000, 6e7 / (0.4 / dt) / 2)))
+            ent["fp32_error"], ent["cpu_baseline"] = fp32_error(sdd, ctx, w, [40, 85], n_sub, dt, w["seed"])
+        per_dt.append(ent)
+        tot_steps += steps[0]
+        tot_ms += ms[0]
+    ctx.close()
+    value = tot_steps / (tot_ms * 1e-3)
+    ach = TRI_INST_PER_STEP * value / 1e12
+    return {"metric": METRIC, "value": value, "unit": METRIC, "ms": tot_ms, "steps": tot_steps,
+            "workload": "triangle in half-space: 128 edge nodes x 1e6 walks, rate 50 in host 2, "
+                        "dt 1e-3, 3e-4, 1e-4, 3e-5 (one launch each), FP32 walk, FP64 sums",
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tinst, "unit": "Tinst/s",
+                         "frac": ach / peak_tinst, "inst_per_step": TRI_INST_PER_STEP},
+            "per_dt": per_dt}
+
+
 def interp_measure(sdd, reps=3, cpu=True):
     """Interpolation along an interface (Sec. 5): the quarter-space line of 64
     nodes at 1e5 walks per walked node, walks at every 4th node and the last
@@ -525,6 +677,103 @@ def rbffd_measure(sdd, reps=2, cpu=True):
     return out
 
 
+def run_sharded(args, torch, rank, world, local):
+    """The quarter-space evaluation split across `world` ranks (one GPU each)
+    by (node, path-range) units; timed per step from the first range launch
+    to the node means, max over ranks."""
+    import torch.distributed as dist
+    from paper_1603_09311_gb300 import sdd
+    from paper_1603_09311_gb300 import shard as S
+    w = I.workload(WORKLOAD)
+    n = len(w["nodes"])
+    per_node = int(w["n_paths"][0]) * (world if args.scaling == "weak" else 1)
+    npth = np.full(n, per_node, dtype=np.int64)
+    P = S.plan(w["nodes"], npth, args.chunk, world, I.DOMAIN)
+    b, e = int(P["bounds"][rank]), int(P["bounds"][rank + 1])
+    node, begin, count = P["node"], P["begin"], P["count"]
+    m = len(node)
+    dev = torch.device("cuda", local)
+    ctx = sdd.sdd_create(w["model"])
+    d_nodes = torch.tensor(w["nodes"][node[b:e]], dtype=torch.float64, device=dev).reshape(-1, 2)
+    d_ids = torch.tensor(node[b:e].astype(np.int32), device=dev)
+    table = torch.zeros((m, ctx.E, 4), dtype=torch.float64, device=dev)
+    nvalid = torch.zeros(m, dtype=torch.int64, device=dev)
+    d_mean = torch.empty((n, ctx.E, 2), dtype=torch.float64, device=dev)
+    d_se = torch.empty_like(d_mean)
+    d_cnt = torch.zeros((max(args.steps, args.warmup), 3), dtype=torch.int64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(seed, k):
+        # rows of the other ranks are zero before the all-reduce
+        table[:b].zero_()
+        table[e:].zero_()
+        nvalid[:b].zero_()
+        nvalid[e:].zero_()
+        if e > b:
+            sdd.sdd_range_sums_device(ctx, d_nodes.data_ptr(), e - b, begin[b:e], count[b:e], w["dt"], seed,
+                                      table[b:e].data_ptr(), nvalid[b:e].data_ptr(),
+                                      d_node_ids_ptr=d_ids.data_ptr(), d_counters_ptr=d_cnt[k].data_ptr(),
+                                      stream=stream.cuda_stream)
+        S.allreduce_table(table, dist)
+        S.allreduce_table(nvalid, dist)
+        sdd.sdd_reduce_sums_device(ctx, n, node, table.data_ptr(), nvalid.data_ptr(), d_mean.data_ptr(),
+                                   d_se.data_ptr(), stream=stream.cuda_stream)
+
+    for i in range(args.warmup):
+        step(w["seed"] + 1000 + i, i)
+    torch.cuda.synchronize()
+    d_cnt.zero_()
+    sampler = ClockSampler(local)
+    sampler.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        step(w["seed"] + k, k)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = sampler.stop()
+    total_ms = barrier_max(sum(a.elapsed_time(b_) for a, b_ in evs), world, torch)
+    steps_local = torch.tensor([float(d_cnt[: args.steps, 0].sum())], dtype=torch.float64, device=dev)
+    dist.all_reduce(steps_local)  # every rank's walk-steps
+    steps_all = float(steps_local.item())
+    walks = int(nvalid.sum())
+    assert walks == n * per_node, "a step did not reach every walk"
+    value = steps_all / (total_ms * 1e-3)
+    peaks, src = load_peaks()
+    clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tinst = world * n_sm * 128 * clk_mhz * 1e6 / 1e12
+    achieved = INST_PER_STEP * value / 1e12
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": args.scaling, "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": (f"quarterspace: {n} nodes on x=0, z in [0,0.9], {per_node} walks/node, "
+                                    "dt 1e-4, kappa 2|20 earth, 0 air (dimensionless)"),
+                       "parallelism": (f"{world} ranks x (node, path-range) slices of {args.chunk}-walk ranges "
+                                       f"({m} ranges, balanced by expected steps), one NCCL all-reduce of the "
+                                       "zero-padded range-sum table per step, node means in range order"),
+                       "walks_per_step": n * per_node, "l2": "flushed between steps (256 MB write)",
+                       "precision": "FP32 walk, FP64 sums"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tinst, "unit": "Tinst/s",
+                         "frac": achieved / peak_tinst, "inst_per_step": INST_PER_STEP,
+                         "peak_source": f"{world} GPUs x {n_sm} SMs x 128 lanes x {clk_mhz:.0f} MHz ({src})"},
+            "clocks": clocks, "gpu_launches": 3 * args.steps,
+            "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0,
+                    "note": "multi-rank steps are device-resident; the host-buffer form is measured at N = 1"},
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    dist.destroy_process_group()
+    return 0
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -573,6 +822,14 @@ def main():
                     help="requests of the serving measurement (0 skips it)")
     ap.add_argument("--small", action="store_true",
                     help="16 nodes x 1e5 walks of the same workload (for profiler captures)")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="N > 1: weak = N x 1e5 walks per node split across the ranks, strong = 1e5")
+    ap.add_argument("--chunk", type=int, default=4096, help="N > 1: walks per (node, path-range) unit")
+    ap.add_argument("--sharded", action="store_true",
+                    help="run the multi-rank form (range sums, all-reduce, reduction) even at N = 1")
+    ap.add_argument("--objects", default="all",
+                    help="comma-separated objects added to the line: serving, tm, interp, mt, rbffd, "
+                         "block, triangle (default all)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -582,9 +839,12 @@ def main():
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU")
     torch.cuda.set_device(local)
-    if world > 1:
+    if world > 1 or args.sharded:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        if not dist.is_initialized():
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            os.environ.setdefault("MASTER_PORT", "29531")
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local), rank=rank, world_size=world)
     from paper_1603_09311_gb300 import build as B
     from paper_1603_09311_gb300 import sdd
     if rank == 0:
@@ -592,12 +852,14 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     B.build()
+    if world > 1 or args.sharded:
+        return run_sharded(args, torch, rank, world, local)
 
     w = I.workload(WORKLOAD)
     if args.small:
         w = I.scaled(w, n_nodes=16)
     n = len(w["nodes"])
-    node_ids = np.arange(n, dtype=np.uint32) + np.uint32(rank * n)
+    node_ids = np.arange(n, dtype=np.uint32)
     ctx = sdd.sdd_create(w["model"])
     dev = torch.device("cuda", local)
     d_nodes = torch.tensor(w["nodes"], dtype=torch.float64, device=dev)
@@ -629,9 +891,6 @@ def main():
     sampler.start()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
-    steps_done = 0
-    if world > 1:
-        torch.distributed.barrier()
     torch.cuda.synchronize()
     for k in range(args.steps):
         flush.zero_()
@@ -639,16 +898,14 @@ def main():
         step(w["seed"] + k, k)
         evs[k][1].record(stream)
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = barrier_max(sum(step_ms), world, torch)
+    total_ms = sum(step_ms)
     cnt = d_cnt[: args.steps].cpu().numpy()
     steps_local = int(cnt[:, 0].sum())
     steps_done_one = steps_local / args.steps
     assert int(cnt[:, 1].min()) == n * int(w["n_paths"][0]), "a step did not run every walk"
-    steps_done = int(round(barrier_max(float(steps_local), world, torch) * world))
+    steps_done = steps_local
     mean = d_mean.cpu().numpy()
     se = d_se.cpu().numpy()
     value = steps_done / (total_ms * 1e-3)
@@ -667,8 +924,7 @@ def main():
         e2e_steps += st["steps"]
         h2d, d2h = st["h2d_bytes"], st["d2h_bytes"]
         kernel_ms_host = st["kernel_ms"]
-    e2e_t = barrier_max(e2e_t, world, torch)
-    e2e_value = e2e_steps * world / e2e_t
+    e2e_value = e2e_steps / e2e_t
 
     # ---- interface-node solves at standard error 1e-3 (adaptive path counts)
     solve_ms, met, walks_t = [], 0, 0
@@ -681,7 +937,7 @@ def main():
         solve_ms.append(1e3 * (time.perf_counter() - t0))
         met = int((np.sqrt((se_t ** 2).sum(-1)).max(-1) <= 1e-3).sum())
         walks_t = int(used.sum())
-    solve_s = barrier_max(statistics.mean(solve_ms) * 1e-3, world, torch)
+    solve_s = statistics.mean(solve_ms) * 1e-3
 
     peaks, src = load_peaks()
     clk_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -705,7 +961,7 @@ def main():
                        "precision": "FP32 walk, FP64 sums",
                        "launch": tuned if tuned else "default shape",
                        "cuda_graph": bool(args.graph)},
-            "node_solves": {"value": met * world / solve_s, "unit": "interface-node solves/s",
+            "node_solves": {"value": met / solve_s, "unit": "interface-node solves/s",
                             "target_se": 1e-3, "nodes_met": f"{met}/{n}", "pilot": 4096,
                             "n_max": 4_000_000, "walks_per_solve_set": walks_t,
                             "ms_per_solve_set": 1e3 * solve_s,
@@ -721,22 +977,33 @@ def main():
             "clocks": clocks,
             "gpu_launches": 2 * args.steps,
         }
-        if args.serve_requests > 0 and world == 1 and not args.small:
+        objs = set(args.objects.split(",")) if args.objects != "all" else \
+            {"serving", "tm", "interp", "mt", "rbffd", "block", "triangle"}
+        full = world == 1 and not args.small
+        cpu = not args.no_cpu_baseline
+        if full and cpu:
+            # the FP32 walk against the oracle on the same streams: four nodes
+            # of the line under their own node ids, their first 20000 walks
+            line["fp32_error"], _ = fp32_error(sdd, ctx, w, [9, 32, 50, 63], 20000, w["dt"], w["seed"])
+        if full and "block" in objs:
+            line["block"] = block_measure(sdd, torch, dev, peak_tinst, flush, cpu=cpu)
+        if full and "triangle" in objs:
+            line["triangle"] = triangle_measure(sdd, torch, dev, peak_tinst, flush, cpu=cpu)
+        if args.serve_requests > 0 and full and "serving" in objs:
             line["serving"] = serving(sdd, args.serve_requests)
-        if world == 1 and not args.small:
-            line["tm"] = tm_measure(sdd, torch, dev, peak_tinst, max(1, min(args.steps, 3)),
-                                    cpu=not args.no_cpu_baseline)
-        if world == 1 and not args.small:
-            line["interp"] = interp_measure(sdd, cpu=not args.no_cpu_baseline)
-            line["mt"] = mt_measure(sdd, cpu=not args.no_cpu_baseline)
-            line["rbffd"] = rbffd_measure(sdd, cpu=not args.no_cpu_baseline)
-        if not args.no_cpu_baseline and world == 1:
+        if full and "tm" in objs:
+            line["tm"] = tm_measure(sdd, torch, dev, peak_tinst, max(1, min(args.steps, 3)), cpu=cpu)
+        if full and "interp" in objs:
+            line["interp"] = interp_measure(sdd, cpu=cpu)
+        if full and "mt" in objs:
+            line["mt"] = mt_measure(sdd, cpu=cpu)
+        if full and "rbffd" in objs:
+            line["rbffd"] = rbffd_measure(sdd, cpu=cpu)
+        if cpu and world == 1:
             cb = cpu_baseline(w)
             cb.pop("seconds", None)
             line["cpu_baseline"] = cb
         print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
     ctx.close()
     return 0
 

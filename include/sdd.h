@@ -30,7 +30,9 @@
  *    Sec. 4.2): sdd_apparent_resistivity;
  *  - the RBF-FD sub-domain solve that completes the decomposition
  *    (Sec. 3.2): sdd_rbffd_weights, sdd_rbffd_solve;
- *  - batched, graph, allocation-free and served launches of the walk.
+ *  - batched, graph, allocation-free and served launches of the walk;
+ *  - raw sums of path ranges and their fixed-order reduction, for an
+ *    evaluation split across processes (sdd_range_sums, sdd_reduce_sums).
  *
  * Conventions common to all entry points:
  *  - z grows downwards; air is z < 0, earth z >= 0.
@@ -331,12 +333,18 @@ sdd_status sdd_walk_occupation(sdd_ctx *ctx, double x0, double z0, uint32_t node
  * deployment variant of the same estimator.
  *   Arguments and outputs as sdd_interface_values_device (ctx from
  *   sdd_create; d_nodes_xz, d_node_ids, d_mean, d_se, d_counters device; n_paths
- *   host; stream a cudaStream_t or NULL).
+ *   host; stream a cudaStream_t or NULL), except that cfg->use_graph must be 0:
+ *   this call launches its kernels directly.  n_paths is also read by an
+ *   asynchronous copy queued on the stream: if it is page-locked memory, keep
+ *   it unchanged until the stream has passed the call.
  *   Errors: SDD_E_ARG for more than SDD_NOALLOC_MAX_NODES nodes, a request whose
  *   work items cannot fit SDD_NOALLOC_MAX_ITEMS, or a context created on another
- *   device than the current one; the checks of sdd_interface_values_device.
+ *   device than the current one; SDD_E_UNSUPPORTED for cfg->use_graph != 0; the
+ *   checks of sdd_interface_values_device.
  * The first call on a device looks up the array's device address (set-up); make
- * that first call before any stream capture.  All calls share the one array,
+ * that first call before any stream capture.  The address is kept for the life
+ * of the process: after cudaDeviceReset on a device, this entry point must not
+ * be called on that device again.  All calls share the one array,
  * which keeps the last call's contents (each call clears what must start at
  * zero): calls that overlap on the GPU -- on two streams or from two host
  * threads -- race and must be ordered by the caller. */
@@ -345,6 +353,60 @@ sdd_status sdd_interface_values_noalloc(sdd_ctx *ctx, const double *d_nodes_xz,
                                         const int64_t *n_paths, double dt, uint64_t seed,
                                         const sdd_config *cfg, double *d_mean, double *d_se,
                                         uint64_t *d_counters, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Path ranges and their reduction: one evaluation split across processes.
+ *
+ * The walks of a node are independent, and so are the nodes (Sec. 5), so an
+ * evaluation can be cut into ranges -- a node and a contiguous range of its
+ * paths -- that different processes (one per GPU) evaluate.  A range's raw
+ * sums are those of the Monte Carlo estimator of Sec. 3.1 over its walks,
+ * which keep the Philox streams (node id, path) they have in a whole-node
+ * call.  The node's mean and standard errors follow from the sums of its
+ * ranges added in range order, so they do not depend on which process
+ * evaluated which range.
+ *
+ * sdd_range_sums: range i is paths [path_begin[i], path_begin[i] +
+ * path_count[i]) of the node at nodes_xz[i] (host, [n_ranges][2]) under RNG
+ * node id node_ids[i] (host, nullable: i).  path_count[i] in 1..2^31-1,
+ * path_begin[i] >= 0 and path_begin[i] + path_count[i] <= 2^32.  Outputs (host):
+ *   sums    [n_ranges][n_eval][4]  sum re, sum im, sum re^2, sum im^2 of the
+ *           samples g(exit) exp(-i (1/2) sum_m kappa_{e,m} T_m) of the walks
+ *           that reached the boundary;
+ *   n_valid [n_ranges]             those walks (truncated ones left out).
+ * Errors: as sdd_interface_values; SDD_E_ARG for a range outside 0..2^32;
+ * SDD_E_UNSUPPORTED for cfg->use_graph != 0.  Synchronous. */
+sdd_status sdd_range_sums(sdd_ctx *ctx, const double *nodes_xz, const uint32_t *node_ids,
+                          int32_t n_ranges, const int64_t *path_begin, const int64_t *path_count,
+                          double dt, uint64_t seed, const sdd_config *cfg, double *sums,
+                          int64_t *n_valid, sdd_stats *stats);
+
+/* The same with device buffers, queued on stream (cudaStream_t or NULL):
+ * d_nodes_xz [n_ranges][2], d_node_ids [n_ranges] (nullable), d_sums
+ * [n_ranges][n_eval][4], d_n_valid [n_ranges], d_counters [3] (nullable:
+ * steps, walks, truncated walks); path_begin and path_count are host arrays. */
+sdd_status sdd_range_sums_device(sdd_ctx *ctx, const double *d_nodes_xz, const uint32_t *d_node_ids,
+                                 int32_t n_ranges, const int64_t *path_begin,
+                                 const int64_t *path_count, double dt, uint64_t seed,
+                                 const sdd_config *cfg, double *d_sums, int64_t *d_n_valid,
+                                 uint64_t *d_counters, void *stream);
+
+/* Mean and standard errors per node and evaluation from range sums:
+ * range_node [n_ranges] (host) is the node 0..n_nodes-1 of each range,
+ * nondecreasing; the sums of a node's ranges are added in range order, then
+ * mean = sum / N and se = sqrt(unbiased variance / N) per component, N the
+ * node's n_valid total (NaN where N = 0, and se NaN where N = 1).  sums and
+ * n_valid are laid out as sdd_range_sums writes them; mean and se are
+ * [n_nodes][n_eval][2].  ctx gives n_eval and the device; host buffers,
+ * synchronous. */
+sdd_status sdd_reduce_sums(sdd_ctx *ctx, int32_t n_nodes, int32_t n_ranges, const int32_t *range_node,
+                           const double *sums, const int64_t *n_valid, double *mean, double *se);
+
+/* The same on device buffers, queued on stream; range_node stays on the host. */
+sdd_status sdd_reduce_sums_device(sdd_ctx *ctx, int32_t n_nodes, int32_t n_ranges,
+                                  const int32_t *range_node, const double *d_sums,
+                                  const int64_t *d_n_valid, double *d_mean, double *d_se,
+                                  void *stream);
 
 /* ------------------------------------------------------------------------
  * Interpolation along an interface (Sec. 5: the stochastic solution is

@@ -112,6 +112,11 @@ def lib():
                                       ctypes.c_int64, ctypes.c_int, P(ctypes.c_double)]
         L.orc_tm_uniforms.restype = None
         L.orc_walk_records.restype = None
+        L.orc_range_sums.argtypes = [
+            P(_Model), P(ctypes.c_double), P(ctypes.c_uint32), ctypes.c_int, P(ctypes.c_int64),
+            P(ctypes.c_int64), ctypes.c_double, ctypes.c_uint64, ctypes.c_int, P(ctypes.c_double),
+            P(ctypes.c_int64), P(ctypes.c_int64)]
+        L.orc_range_sums.restype = None
         L.orc_max_threads.argtypes = []
         L.orc_max_threads.restype = ctypes.c_int
         _lib = L
@@ -282,6 +287,26 @@ def walk_records(model: dict, node_xz, node_id: int, p0: int, count: int, dt: fl
                            _ptr(hits, ctypes.c_int64))
     return {"steps": steps, "counts": counts, "exit": ext, "wall": wall, "m_last": mlast,
             "truncated": trunc, "occ": occ, "hits": hits}
+
+
+def range_sums(model: dict, nodes, node_ids, path_begin, path_count, dt: float, seed: int,
+               urule: int = 32, max_steps: int | None = None, threads: int = 0):
+    """Raw sums of path ranges (range i: paths [path_begin[i], +path_count[i]) of
+    nodes[i] under node id node_ids[i]).  Returns (sums [n][E][4] = sum re, sum im,
+    sum re^2, sum im^2; n_valid [n]; total steps)."""
+    om = OracleModel(model, urule=urule, max_steps=max_steps, dt=dt)
+    nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64).reshape(-1, 2))
+    n = nodes.shape[0]
+    ids = np.ascontiguousarray(np.asarray(node_ids, dtype=np.uint32))
+    b = np.ascontiguousarray(np.asarray(path_begin, dtype=np.int64))
+    c = np.ascontiguousarray(np.asarray(path_count, dtype=np.int64))
+    sums = np.zeros((n, om.E, 4))
+    nv = np.zeros(n, dtype=np.int64)
+    st = np.zeros(1, dtype=np.int64)
+    lib().orc_range_sums(ctypes.byref(om.s), _ptr(nodes, ctypes.c_double), _ptr(ids, ctypes.c_uint32), n,
+                         _ptr(b, ctypes.c_int64), _ptr(c, ctypes.c_int64), dt, seed, threads,
+                         _ptr(sums, ctypes.c_double), _ptr(nv, ctypes.c_int64), _ptr(st, ctypes.c_int64))
+    return sums, nv, int(st[0])
 
 
 def max_threads() -> int:

@@ -739,6 +739,49 @@ int64_t orc_interface_values(const orc_model *m, const double *nodes_xz, int n_n
     return tot_trunc;
 }
 
+/* Raw sums of path ranges: range i is paths [path_begin[i], path_begin[i] +
+ * path_count[i]) of the node at nodes_xz[i] with node id node_ids[i].  Per
+ * range and evaluation: sum re, sum im, sum re^2, sum im^2 over the walks that
+ * reached the boundary, added in path order (one range per thread, so the
+ * sums do not depend on the number of threads); n_valid[i] those walks, and
+ * stats[0] the Euler steps of all walks.  A range is the unit a sharded
+ * evaluation hands to one process: every range's walks are independent of
+ * the others (Sec. 5). */
+void orc_range_sums(const orc_model *m, const double *nodes_xz, const uint32_t *node_ids,
+                    int n_ranges, const int64_t *path_begin, const int64_t *path_count, double dt,
+                    uint64_t seed, int n_threads, double *sums /* [n][E][4] */,
+                    int64_t *n_valid, int64_t *stats)
+{
+    int64_t steps = 0;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#endif
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : steps)
+    for (int i = 0; i < n_ranges; ++i) {
+        double *S = sums + (size_t)i * m->E * 4;
+        for (int k = 0; k < m->E * 4; ++k) S[k] = 0.0;
+        int64_t nv = 0;
+        for (int64_t p = path_begin[i]; p < path_begin[i] + path_count[i]; ++p) {
+            orc_walk_rec rec;
+            (m->tm ? orc_walk_tm : orc_walk)(m, nodes_xz[2 * i], nodes_xz[2 * i + 1], node_ids[i],
+                                             (uint32_t)p, dt, seed, &rec);
+            steps += rec.steps;
+            if (rec.truncated) continue;
+            nv += 1;
+            for (int e = 0; e < m->E; ++e) {
+                double complex v = orc_sample(m, e, &rec, dt);
+                double re = creal(v), im = cimag(v);
+                S[4 * e + 0] += re;
+                S[4 * e + 1] += im;
+                S[4 * e + 2] += re * re;
+                S[4 * e + 3] += im * im;
+            }
+        }
+        n_valid[i] = nv;
+    }
+    if (stats) stats[0] = steps;
+}
+
 /* Per-path records of paths [p0, p0+count) of one node (for per-path
  * comparison of exit steps, counts and exit points). */
 void orc_walk_records(const orc_model *m, double x0, double z0, uint32_t node, uint32_t p0,

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -131,6 +132,8 @@ struct sdd_ctx {
     DevBuf items, slots, trunc, counters, queue, err, nodes, node_ids, mean, se;
     DevBuf rec_steps, rec_counts, rec_occ, rec_hits, rec_exit, rec_wall, rec_mlast;
     DevBuf batch_models;  // model table of batched launches owned by this context
+    DevBuf red_index;     // node -> first range of the range reduction (sdd_reduce_sums)
+    std::vector<int32_t> h_red_index;
     Item *h_items = nullptr;  // pinned staging of the item table
     size_t h_items_cap = 0;
     cudaEvent_t items_done = nullptr;  // last copy out of h_items finished
@@ -777,7 +780,7 @@ void sdd_destroy(sdd_ctx *c) {
                       &c->err, &c->nodes, &c->node_ids, &c->mean, &c->se, &c->rec_steps,
                       &c->rec_counts, &c->rec_occ, &c->rec_hits, &c->rec_exit, &c->rec_wall,
                       &c->rec_mlast,
-                      &c->batch_models};
+                      &c->batch_models, &c->red_index};
     for (DevBuf *b : bufs) b->release();
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->h_items) cudaFreeHost(c->h_items);
@@ -1024,19 +1027,23 @@ static_assert(kNaBytes == SDD_NOALLOC_SCRATCH_BYTES, "scratch size differs from 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
 
 // Device address of g_noalloc_scratch per device, looked up once per device
-// with that device current (the name is only a host-side stand-in).
+// with that device current (the name is only a host-side stand-in).  Host
+// threads may make their first calls at once: the cache is atomic, and two
+// threads that both look the address up store the same value.
 constexpr int kNaMaxDevices = 64;
-unsigned char *g_noalloc_ptr[kNaMaxDevices] = {nullptr};
+std::atomic<unsigned char *> g_noalloc_ptr[kNaMaxDevices];
 
 sdd_status noalloc_scratch(int device, unsigned char **out) {
     if (device < 0 || device >= kNaMaxDevices) return fail(SDD_E_UNSUPPORTED, "device id too large");
-    if (!g_noalloc_ptr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    unsigned char *p = g_noalloc_ptr[device].load(std::memory_order_acquire);
+    if (!p) {
+        void *a = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&a, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
-        g_noalloc_ptr[device] = static_cast<unsigned char *>(p);
+        p = static_cast<unsigned char *>(a);
+        g_noalloc_ptr[device].store(p, std::memory_order_release);
     }
-    *out = g_noalloc_ptr[device];
+    *out = p;
     return SDD_OK;
 }
 
@@ -1080,6 +1087,9 @@ extern "C" sdd_status sdd_interface_values_noalloc(sdd_ctx *ctx, const double *d
     if (st != SDD_OK) return st;
     if (n_nodes == 0) return SDD_OK;
     if (!d_nodes_xz || !d_mean || !d_se) return fail(SDD_E_ARG, "d_nodes_xz, d_mean and d_se must not be NULL");
+    if (cfg && cfg->use_graph)
+        return fail(SDD_E_UNSUPPORTED, "sdd_interface_values_noalloc launches its kernels directly: "
+                                       "cfg->use_graph must be 0");
     if ((size_t)n_nodes > kNaNodes)
         return fail(SDD_E_ARG, "sdd_interface_values_noalloc takes at most SDD_NOALLOC_MAX_NODES (" +
                                    std::to_string(kNaNodes) + ") nodes per call");
@@ -1140,6 +1150,219 @@ extern "C" sdd_status sdd_interface_values_noalloc(sdd_ctx *ctx, const double *d
     if (d_counters)
         SDD_CUDA(cudaMemcpyAsync(d_counters, A.counters, 3 * sizeof(uint64_t),
                                  cudaMemcpyDeviceToDevice, s));
+    return SDD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Path ranges (sdd_range_sums, sdd_range_sums_device) and the fixed-order
+// reduction of their sums (sdd_reduce_sums, sdd_reduce_sums_device).
+//
+// The walks of a node are independent of one another, and so are the nodes
+// (Sec. 5), so one evaluation can be cut into ranges (a node and a contiguous
+// range of its paths) that separate processes evaluate.  A range's raw sums
+// are those of its walks under the node's Philox streams; the node's mean and
+// standard error follow from the sums of its ranges, added in range order.
+
+namespace {
+
+__global__ void range_reduce_kernel(const double *__restrict__ sums, const long long *__restrict__ n_valid,
+                                    const int32_t *__restrict__ node_range0, int n_nodes, int E,
+                                    double *__restrict__ mean, double *__restrict__ se) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_nodes * E) return;
+    const int j = t / E, e = t % E;
+    double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    long long nv = 0;
+    for (int r = node_range0[j]; r < node_range0[j + 1]; ++r) {
+        const double *o = sums + ((size_t)r * E + e) * 4;
+        s0 += o[0]; s1 += o[1]; s2 += o[2]; s3 += o[3];
+        nv += n_valid[r];
+    }
+    const double N = (double)nv;
+    double mr = nan(""), mi = nan(""), vr = nan(""), vi = nan("");
+    if (nv > 0) { mr = s0 / N; mi = s1 / N; }
+    if (nv > 1) {
+        vr = fmax((s2 - s0 * mr) / (N - 1.0), 0.0);
+        vi = fmax((s3 - s1 * mi) / (N - 1.0), 0.0);
+    }
+    mean[2 * t] = mr;
+    mean[2 * t + 1] = mi;
+    se[2 * t] = sqrt(vr / N);
+    se[2 * t + 1] = sqrt(vi / N);
+}
+
+sdd_status check_ranges(sdd_ctx *ctx, int32_t n, const int64_t *begin, const int64_t *count, double dt,
+                        const sdd_config *cfg) {
+    sdd_status st = check_call(ctx, n, count, dt, cfg);
+    if (st != SDD_OK) return st;
+    if (n > 0 && !begin) return fail(SDD_E_ARG, "path_begin is NULL");
+    for (int i = 0; i < n; ++i)
+        if (begin[i] < 0 || begin[i] + count[i] > 0x100000000ll)
+            return fail(SDD_E_ARG, "a path range must lie in 0..2^32");
+    if (cfg && cfg->use_graph)
+        return fail(SDD_E_UNSUPPORTED, "range sums launch their kernels directly: cfg->use_graph must be 0");
+    return SDD_OK;
+}
+
+// Walks of the ranges and their raw sums into d_sums / d_n_valid (device).
+sdd_status range_walks(sdd_ctx *ctx, const double *d_nodes, const uint32_t *d_ids, int32_t n,
+                       const int64_t *begin, const int64_t *count, double dt, uint64_t seed,
+                       const sdd_config *cfg, double *d_sums, long long *d_nv, cudaStream_t s,
+                       bool timed, size_t *n_items) {
+    const Launch L = choose_launch(ctx, cfg, dt);
+    ctx->plan_valid = false;
+    const Plan P = plan_work(n, begin, count, 0, L);
+    WalkArgs A = base_args(ctx, L, dt, seed);
+    A.nodes = d_nodes;
+    A.node_ids = d_ids;
+    sdd_status st = run(ctx, P, L, A, s, timed, false, nullptr, nullptr, n);
+    if (st != SDD_OK) return st;
+    const size_t ni = P.items.size();
+    const Item *d_items = (const Item *)ctx->items.p;
+    const int32_t *d_i0 = (const int32_t *)(reinterpret_cast<unsigned char *>(ctx->items.p) + ni * sizeof(Item));
+    const int nt = n * ctx->E;
+    sums_kernel<<<(nt + 127) / 128, 128, 0, s>>>((const double *)ctx->slots.p, (const int32_t *)ctx->trunc.p,
+                                                d_items, d_i0, n, ctx->E, d_sums, d_nv);
+    SDD_CUDA(cudaGetLastError());
+    if (n_items) *n_items = ni;
+    return SDD_OK;
+}
+
+// node -> first range (CSR) of a nondecreasing range -> node map.
+sdd_status range_index(sdd_ctx *ctx, int32_t n_nodes, int32_t n_ranges, const int32_t *range_node) {
+    if (n_nodes < 0 || n_ranges < 0) return fail(SDD_E_ARG, "n_nodes and n_ranges must be >= 0");
+    if (n_ranges > 0 && !range_node) return fail(SDD_E_ARG, "range_node is NULL");
+    std::vector<int32_t> &ix = ctx->h_red_index;
+    ix.assign((size_t)n_nodes + 1, 0);
+    for (int r = 0; r < n_ranges; ++r) {
+        if (range_node[r] < 0 || range_node[r] >= n_nodes || (r > 0 && range_node[r] < range_node[r - 1]))
+            return fail(SDD_E_ARG, "range_node must be nondecreasing node indices in 0..n_nodes-1");
+        ix[(size_t)range_node[r] + 1] += 1;
+    }
+    for (int j = 0; j < n_nodes; ++j) ix[(size_t)j + 1] += ix[j];
+    return SDD_OK;
+}
+
+}  // namespace
+
+extern "C" sdd_status sdd_range_sums(sdd_ctx *ctx, const double *nodes_xz, const uint32_t *node_ids,
+                                     int32_t n_ranges, const int64_t *path_begin,
+                                     const int64_t *path_count, double dt, uint64_t seed,
+                                     const sdd_config *cfg, double *sums, int64_t *n_valid,
+                                     sdd_stats *stats) {
+    sdd_status st = check_ranges(ctx, n_ranges, path_begin, path_count, dt, cfg);
+    if (st != SDD_OK) return st;
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (n_ranges == 0) return SDD_OK;
+    if (!nodes_xz || !sums || !n_valid) return fail(SDD_E_ARG, "nodes_xz, sums and n_valid must not be NULL");
+    st = check_nodes(ctx, nodes_xz, n_ranges);
+    if (st != SDD_OK) return st;
+    cudaStream_t s = ctx->stream;
+    const size_t sb = (size_t)n_ranges * ctx->E * 4 * sizeof(double);
+    SDD_CUDA(ctx->nodes.ensure((size_t)n_ranges * 2 * sizeof(double)));
+    SDD_CUDA(ctx->mean.ensure(sb));
+    SDD_CUDA(ctx->se.ensure((size_t)n_ranges * sizeof(long long)));
+    SDD_CUDA(cudaMemcpyAsync(ctx->nodes.p, nodes_xz, (size_t)n_ranges * 2 * sizeof(double),
+                             cudaMemcpyHostToDevice, s));
+    const uint32_t *d_ids = nullptr;
+    if (node_ids) {
+        SDD_CUDA(ctx->node_ids.ensure((size_t)n_ranges * sizeof(uint32_t)));
+        SDD_CUDA(cudaMemcpyAsync(ctx->node_ids.p, node_ids, (size_t)n_ranges * sizeof(uint32_t),
+                                 cudaMemcpyHostToDevice, s));
+        d_ids = (const uint32_t *)ctx->node_ids.p;
+    }
+    size_t ni = 0;
+    st = range_walks(ctx, (const double *)ctx->nodes.p, d_ids, n_ranges, path_begin, path_count, dt, seed,
+                     cfg, (double *)ctx->mean.p, (long long *)ctx->se.p, s, true, &ni);
+    if (st != SDD_OK) return st;
+    unsigned long long cnt[3] = {0, 0, 0};
+    SDD_CUDA(cudaMemcpyAsync(sums, ctx->mean.p, sb, cudaMemcpyDeviceToHost, s));
+    SDD_CUDA(cudaMemcpyAsync(n_valid, ctx->se.p, (size_t)n_ranges * sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    SDD_CUDA(cudaMemcpyAsync(cnt, ctx->counters.p, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    SDD_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    SDD_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    if (stats) {
+        stats->steps = cnt[0];
+        stats->walks = cnt[1];
+        stats->truncated = cnt[2];
+        stats->kernel_ms = ms;
+        stats->launches = 2;
+        stats->items = (int32_t)ni;
+        stats->h2d_bytes = ctx->last_h2d + (uint64_t)n_ranges * 2 * sizeof(double) +
+                           (node_ids ? (uint64_t)n_ranges * sizeof(uint32_t) : 0);
+        stats->d2h_bytes = sb + (uint64_t)n_ranges * sizeof(int64_t) + sizeof(cnt);
+    }
+    return cnt[2] ? SDD_E_TRUNCATED : SDD_OK;
+}
+
+extern "C" sdd_status sdd_range_sums_device(sdd_ctx *ctx, const double *d_nodes_xz, const uint32_t *d_node_ids,
+                                            int32_t n_ranges, const int64_t *path_begin,
+                                            const int64_t *path_count, double dt, uint64_t seed,
+                                            const sdd_config *cfg, double *d_sums, int64_t *d_n_valid,
+                                            uint64_t *d_counters, void *stream) {
+    sdd_status st = check_ranges(ctx, n_ranges, path_begin, path_count, dt, cfg);
+    if (st != SDD_OK) return st;
+    if (n_ranges == 0) return SDD_OK;
+    if (!d_nodes_xz || !d_sums || !d_n_valid) return fail(SDD_E_ARG, "d_nodes_xz, d_sums and d_n_valid must not be NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    st = range_walks(ctx, d_nodes_xz, d_node_ids, n_ranges, path_begin, path_count, dt, seed, cfg, d_sums,
+                     reinterpret_cast<long long *>(d_n_valid), s, false, nullptr);
+    if (st != SDD_OK) return st;
+    if (d_counters)
+        SDD_CUDA(cudaMemcpyAsync(d_counters, ctx->counters.p, 3 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+    return SDD_OK;
+}
+
+extern "C" sdd_status sdd_reduce_sums_device(sdd_ctx *ctx, int32_t n_nodes, int32_t n_ranges,
+                                             const int32_t *range_node, const double *d_sums,
+                                             const int64_t *d_n_valid, double *d_mean, double *d_se,
+                                             void *stream) {
+    if (!ctx) return fail(SDD_E_ARG, "ctx is NULL");
+    sdd_status st = range_index(ctx, n_nodes, n_ranges, range_node);
+    if (st != SDD_OK) return st;
+    if (n_nodes == 0) return SDD_OK;
+    if (!d_mean || !d_se || (n_ranges > 0 && (!d_sums || !d_n_valid)))
+        return fail(SDD_E_ARG, "d_sums, d_n_valid, d_mean and d_se must not be NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    SDD_CUDA(ctx->red_index.ensure(ctx->h_red_index.size() * sizeof(int32_t)));
+    SDD_CUDA(cudaMemcpyAsync(ctx->red_index.p, ctx->h_red_index.data(), ctx->h_red_index.size() * sizeof(int32_t),
+                             cudaMemcpyHostToDevice, s));
+    const int nt = n_nodes * ctx->E;
+    range_reduce_kernel<<<(nt + 127) / 128, 128, 0, s>>>(d_sums, reinterpret_cast<const long long *>(d_n_valid),
+                                                        (const int32_t *)ctx->red_index.p, n_nodes, ctx->E,
+                                                        d_mean, d_se);
+    SDD_CUDA(cudaGetLastError());
+    return SDD_OK;
+}
+
+extern "C" sdd_status sdd_reduce_sums(sdd_ctx *ctx, int32_t n_nodes, int32_t n_ranges, const int32_t *range_node,
+                                      const double *sums, const int64_t *n_valid, double *mean, double *se) {
+    if (!ctx) return fail(SDD_E_ARG, "ctx is NULL");
+    if (n_nodes > 0 && (!mean || !se || (n_ranges > 0 && (!sums || !n_valid))))
+        return fail(SDD_E_ARG, "sums, n_valid, mean and se must not be NULL");
+    if (n_ranges < 0 || n_nodes <= 0) return sdd_reduce_sums_device(ctx, n_nodes, n_ranges, range_node, nullptr,
+                                                                     nullptr, nullptr, nullptr, ctx->stream);
+    cudaStream_t s = ctx->stream;
+    const size_t sb = (size_t)n_ranges * ctx->E * 4 * sizeof(double);
+    const size_t ob = (size_t)n_nodes * ctx->E * 2 * sizeof(double);
+    // the walk scratch is free between calls: sums in slots, counts in trunc,
+    // outputs in mean / se
+    SDD_CUDA(ctx->slots.ensure(std::max<size_t>(sb, 8)));
+    SDD_CUDA(ctx->trunc.ensure(std::max<size_t>((size_t)n_ranges * sizeof(int64_t), 8)));
+    SDD_CUDA(ctx->mean.ensure(ob));
+    SDD_CUDA(ctx->se.ensure(ob));
+    if (n_ranges > 0) {
+        SDD_CUDA(cudaMemcpyAsync(ctx->slots.p, sums, sb, cudaMemcpyHostToDevice, s));
+        SDD_CUDA(cudaMemcpyAsync(ctx->trunc.p, n_valid, (size_t)n_ranges * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    }
+    sdd_status st = sdd_reduce_sums_device(ctx, n_nodes, n_ranges, range_node, (const double *)ctx->slots.p,
+                                           (const int64_t *)ctx->trunc.p, (double *)ctx->mean.p,
+                                           (double *)ctx->se.p, s);
+    if (st != SDD_OK) return st;
+    SDD_CUDA(cudaMemcpyAsync(mean, ctx->mean.p, ob, cudaMemcpyDeviceToHost, s));
+    SDD_CUDA(cudaMemcpyAsync(se, ctx->se.p, ob, cudaMemcpyDeviceToHost, s));
+    SDD_CUDA(cudaStreamSynchronize(s));
     return SDD_OK;
 }
 

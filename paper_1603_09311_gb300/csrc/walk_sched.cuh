@@ -68,10 +68,15 @@ __device__ __forceinline__ uint4 philox4x32_10_pre(uint32_t c0, uint32_t c3, uin
 
 // 32 x 32 -> 64-bit product as one wide multiply.
 __device__ __forceinline__ void mul_wide(uint32_t a, uint32_t b, uint32_t &lo, uint32_t &hi) {
+#ifdef SDD_MUL_HILO
+    lo = a * b;
+    hi = __umulhi(a, b);
+#else
     uint64_t p;
     asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(b));
     lo = (uint32_t)p;
     hi = (uint32_t)(p >> 32);
+#endif
 }
 
 // Philox4x32-10 with the ten round keys given (rk0[r] = k0 + r 0x9E3779B9,
@@ -189,9 +194,12 @@ struct ExitInfo {
 // leaves up to 85 registers a thread.  24 resident warps whose iterations
 // carry four independent Philox chains keep the issue slots fuller than 32
 // warps squeezed into 64 registers.
+#ifndef SDD_MIN_CTAS
+#define SDD_MIN_CTAS 3
+#endif
 template <class W>
-__global__ void __launch_bounds__(256, 3) walk_kernel(const __grid_constant__ ModelDev M,
-                                                   const WalkArgs A) {
+__global__ void __launch_bounds__(256, SDD_MIN_CTAS) walk_kernel(const __grid_constant__ ModelDev M,
+                                                              const WalkArgs A) {
     using Real = typename W::Real;
     constexpr int KMAX = W::KMAX;
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -151,6 +151,20 @@ SIGNATURES = [
      [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_int64),
       ctypes.c_double, ctypes.c_uint64, P(sdd_config), ctypes.c_void_p, ctypes.c_void_p,
       ctypes.c_void_p, ctypes.c_void_p]),
+    ("sdd_range_sums", ctypes.c_int,
+     [ctypes.c_void_p, P(ctypes.c_double), P(ctypes.c_uint32), ctypes.c_int32, P(ctypes.c_int64),
+      P(ctypes.c_int64), ctypes.c_double, ctypes.c_uint64, P(sdd_config), P(ctypes.c_double),
+      P(ctypes.c_int64), P(sdd_stats)]),
+    ("sdd_range_sums_device", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, P(ctypes.c_int64),
+      P(ctypes.c_int64), ctypes.c_double, ctypes.c_uint64, P(sdd_config), ctypes.c_void_p,
+      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("sdd_reduce_sums", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_double),
+      P(ctypes.c_int64), P(ctypes.c_double), P(ctypes.c_double)]),
+    ("sdd_reduce_sums_device", ctypes.c_int,
+     [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32), ctypes.c_void_p,
+      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("sdd_batch_values", ctypes.c_int,
      [P(sdd_batch_entry), ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, P(sdd_config),
       P(sdd_stats)]),
@@ -412,6 +426,74 @@ def sdd_interface_values_noalloc(ctx: Context, d_nodes_ptr: int, n_nodes: int, n
         ctypes.c_void_p(d_counters_ptr or None), ctypes.c_void_p(stream or None))
     if st != SDD_OK:
         raise SddError(st, "sdd_interface_values_noalloc")
+    return st
+
+
+def sdd_range_sums(ctx: Context, nodes, path_begin, path_count, dt: float, seed: int, node_ids=None,
+                   config: sdd_config | None = None, **cfg):
+    """Raw sums of path ranges (range i: paths [path_begin[i], +path_count[i]) of
+    nodes[i]).  Returns (sums [n][E][4], n_valid [n], stats dict)."""
+    nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64).reshape(-1, 2))
+    n = nodes.shape[0]
+    b = np.ascontiguousarray(np.asarray(path_begin, dtype=np.int64).reshape(n))
+    c = np.ascontiguousarray(np.asarray(path_count, dtype=np.int64).reshape(n))
+    ids = None if node_ids is None else np.ascontiguousarray(np.asarray(node_ids, dtype=np.uint32))
+    sums = np.zeros((n, ctx.E, 4))
+    nv = np.zeros(n, dtype=np.int64)
+    st_out = sdd_stats()
+    c_ = config if config is not None else make_config(**cfg)
+    st = lib().sdd_range_sums(ctx.handle, _dp(nodes), None if ids is None else ids.ctypes.data_as(P(ctypes.c_uint32)),
+                              n, b.ctypes.data_as(P(ctypes.c_int64)), c.ctypes.data_as(P(ctypes.c_int64)),
+                              float(dt), int(seed) & (2 ** 64 - 1), ctypes.byref(c_), _dp(sums),
+                              nv.ctypes.data_as(P(ctypes.c_int64)), ctypes.byref(st_out))
+    if st not in (SDD_OK, SDD_E_TRUNCATED):
+        raise SddError(st, "sdd_range_sums")
+    stats = {f: getattr(st_out, f) for f, _ in sdd_stats._fields_}
+    stats["status"] = st
+    return sums, nv, stats
+
+
+def sdd_range_sums_device(ctx: Context, d_nodes_ptr: int, n_ranges: int, path_begin, path_count, dt: float,
+                          seed: int, d_sums_ptr: int, d_n_valid_ptr: int, d_node_ids_ptr: int = 0,
+                          d_counters_ptr: int = 0, stream: int = 0, config: sdd_config | None = None, **cfg) -> int:
+    """Device-buffer range sums queued on `stream` (raw pointers)."""
+    b = np.ascontiguousarray(np.asarray(path_begin, dtype=np.int64).reshape(n_ranges))
+    c = np.ascontiguousarray(np.asarray(path_count, dtype=np.int64).reshape(n_ranges))
+    c_ = config if config is not None else make_config(**cfg)
+    st = lib().sdd_range_sums_device(
+        ctx.handle, ctypes.c_void_p(d_nodes_ptr), ctypes.c_void_p(d_node_ids_ptr or None), n_ranges,
+        b.ctypes.data_as(P(ctypes.c_int64)), c.ctypes.data_as(P(ctypes.c_int64)), float(dt),
+        int(seed) & (2 ** 64 - 1), ctypes.byref(c_), ctypes.c_void_p(d_sums_ptr), ctypes.c_void_p(d_n_valid_ptr),
+        ctypes.c_void_p(d_counters_ptr or None), ctypes.c_void_p(stream or None))
+    if st != SDD_OK:
+        raise SddError(st, "sdd_range_sums_device")
+    return st
+
+
+def sdd_reduce_sums(ctx: Context, n_nodes: int, range_node, sums, n_valid):
+    """Per-node mean (complex [n_nodes][E]) and se ([n_nodes][E][2]) from range sums,
+    a node's ranges added in range order."""
+    rn = np.ascontiguousarray(np.asarray(range_node, dtype=np.int32))
+    sums = np.ascontiguousarray(np.asarray(sums, dtype=np.float64))
+    nv = np.ascontiguousarray(np.asarray(n_valid, dtype=np.int64))
+    mean = np.zeros((n_nodes, ctx.E, 2))
+    se = np.zeros((n_nodes, ctx.E, 2))
+    st = lib().sdd_reduce_sums(ctx.handle, int(n_nodes), len(rn), rn.ctypes.data_as(P(ctypes.c_int32)), _dp(sums),
+                               nv.ctypes.data_as(P(ctypes.c_int64)), _dp(mean), _dp(se))
+    if st != SDD_OK:
+        raise SddError(st, "sdd_reduce_sums")
+    return mean[..., 0] + 1j * mean[..., 1], se
+
+
+def sdd_reduce_sums_device(ctx: Context, n_nodes: int, range_node, d_sums_ptr: int, d_n_valid_ptr: int,
+                           d_mean_ptr: int, d_se_ptr: int, stream: int = 0) -> int:
+    rn = np.ascontiguousarray(np.asarray(range_node, dtype=np.int32))
+    st = lib().sdd_reduce_sums_device(ctx.handle, int(n_nodes), len(rn), rn.ctypes.data_as(P(ctypes.c_int32)),
+                                      ctypes.c_void_p(d_sums_ptr), ctypes.c_void_p(d_n_valid_ptr),
+                                      ctypes.c_void_p(d_mean_ptr), ctypes.c_void_p(d_se_ptr),
+                                      ctypes.c_void_p(stream or None))
+    if st != SDD_OK:
+        raise SddError(st, "sdd_reduce_sums_device")
     return st
 
 

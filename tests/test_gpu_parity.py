@@ -9,7 +9,13 @@ between the two math libraries are the only source of difference).
 
 FP32 mode (same streams, uniform rule (w mod 2^23 + 1/2) 2^-23, FP32
 positions): node means within 4 combined standard errors + 1e-4 of the
-oracle's on the same streams.
+oracle's on the same streams.  On the same streams the FP32 walks take the
+oracle's decisions (measured: every walk's step count and wall equal at dt
+1e-3 and 1e-4), so the actual difference is far below that bound: it is
+asserted below FP32_SAME_NSE standard errors.  A few walks (0.1-0.3 %) count
+one step in a neighbouring material: a position within FP32 rounding (about
+1e-6 after hundreds of steps) of a material edge.  With independent seeds
+the two estimates agree within 4 combined standard errors.
 """
 import numpy as np
 import pytest
@@ -23,6 +29,10 @@ pytestmark = pytest.mark.gpu
 
 FP64_REL = 1e-10        # relative to max |g| on the boundary
 FP32_NSE, FP32_ABS = 4.0, 1e-4
+# Same streams: the walks agree step for step, so the means differ by the
+# rounding of exit points and samples (about 1e-5 of |g|), a small fraction
+# of a standard error.
+FP32_SAME_NSE = 0.1
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -112,19 +122,42 @@ def test_fp32_node_values_match_oracle(name):
     d = mean - ref["mean"]
     assert np.all(np.abs(d.real) <= tol[..., 0])
     assert np.all(np.abs(d.imag) <= tol[..., 1])
+    # what the same streams actually give: a small fraction of a standard error
+    assert np.all(np.abs(d.real) <= FP32_SAME_NSE * ref["se"][..., 0] + 1e-6), np.abs(d.real) / ref["se"][..., 0]
+    assert np.all(np.abs(d.imag) <= FP32_SAME_NSE * ref["se"][..., 1] + 1e-6), np.abs(d.imag) / ref["se"][..., 1]
     assert st["walks"] == n_paths.sum() and st["truncated"] == 0
-    # same streams: the step totals agree to a fraction of a percent
-    assert abs(st["steps"] - ref["steps"]) <= 0.01 * ref["steps"]
+    # same streams: the step totals agree to a small fraction of a percent
+    assert abs(st["steps"] - ref["steps"]) <= 1e-3 * ref["steps"]
 
 
-def test_fp32_walks_follow_the_oracle_streams():
+@pytest.mark.parametrize("name", sorted(MODELS))
+def test_fp32_independent_seeds_agree_with_oracle(name):
+    # the FP32 walk and the FP64 oracle on unrelated streams (other seed,
+    # other uniform rule): both estimate the same expectation, so they agree
+    # within 4 combined standard errors
+    model, _ = MODELS[name]
+    nodes = np.array([[0.0, 0.25], [-0.55, 0.6], [0.35, -0.2]])
+    dt = 1e-3
+    ctx = sdd.sdd_create(model)
+    mean, se, _ = sdd.sdd_interface_values(ctx, nodes, 20000, dt, 5150)
+    ref = O.interface_values(model, nodes, 20000, dt, 8088, urule=32)
+    assert _fp32_close(mean, se, ref["mean"], ref["se"])
+
+
+@pytest.mark.parametrize("dt", [1e-3, 1e-4])
+def test_fp32_walks_follow_the_oracle_streams(dt):
     model, (x0, z0) = MODELS["quarterspace"]
     ctx = sdd.sdd_create(model)
-    g = sdd.sdd_walk_records(ctx, x0, z0, 3, 0, 4000, 1e-3, 77)
-    o = O.walk_records(model, (x0, z0), 3, 0, 4000, 1e-3, 77, urule=23)
-    same = np.mean(g["steps"] == o["steps"])
-    assert same >= 0.9, same
+    n = 4000 if dt == 1e-3 else 1000
+    g = sdd.sdd_walk_records(ctx, x0, z0, 3, 0, n, dt, 77)
+    o = O.walk_records(model, (x0, z0), 3, 0, n, dt, 77, urule=23)
+    same = g["steps"] == o["steps"]
+    assert same.mean() >= 0.99, same.mean()
+    assert np.array_equal(g["wall"][same], o["wall"][same])
+    assert np.abs(g["exit"][same, :2] - o["exit"][same, :2]).max() <= 1e-3
     assert np.array_equal(g["counts"].sum(1), g["steps"] - 1)
+    eq = np.all(g["counts"][same] == o["counts"][same], axis=1)
+    assert eq.mean() >= 0.99
 
 
 @pytest.mark.parametrize("name", ["quarterspace", "triangle_raster", "eight_materials"])
@@ -216,14 +249,33 @@ def test_device_api_matches_host_api():
     assert int(d_cnt[1]) == 8 * 5000
 
 
+def _kappa_quarter(X, Z):
+    # the quarter-space rates at grid nodes, averaged over a node's dual cell
+    # on the contact x = 0 and on the surface z = 0
+    k = np.where(X < 0, 2.0, 20.0)
+    k = np.where(np.abs(X) < 1e-12, 11.0, k)
+    k = np.where(Z < 0, 0.0, k)
+    return np.where(np.abs(Z) < 1e-12, k / 2, k)
+
+
 @pytest.mark.slow
 def test_full_size_quarterspace_sampled_nodes():
     # the benchmarked launch: 64 nodes x 1e5 paths, dt = 1e-4, default launch;
-    # two nodes recomputed by the oracle in full
+    # two nodes recomputed by the oracle in full, and every node against
+    # finite differences (h = 1/70 and 1/140 put the nodes z = 0.9 k/63 = k/70
+    # on both grids; Richardson-extrapolated)
+    import pins
     w = I.workload("quarterspace")
     ctx = sdd.sdd_create(w["model"])
     mean, se, st = sdd.sdd_interface_values(ctx, w["nodes"], w["n_paths"], w["dt"], w["seed"])
     assert st["walks"] == 6_400_000 and st["truncated"] == 0
+    a = pins.fd_value(_kappa_quarter, I.DOMAIN, 1 / 70, 2.0, 20.0, w["nodes"])
+    b = pins.fd_value(_kappa_quarter, I.DOMAIN, 1 / 140, 2.0, 20.0, w["nodes"])
+    fd, fd_err = (4 * b - a) / 3, np.abs(b - a) / 3
+    d = mean[:, 0] - fd
+    tb = pins.bias_bound(w["dt"])
+    assert np.all(np.abs(d.real) <= 4 * se[:, 0, 0] + tb + fd_err), np.abs(d.real) / se[:, 0, 0]
+    assert np.all(np.abs(d.imag) <= 4 * se[:, 0, 1] + tb + fd_err), np.abs(d.imag) / se[:, 0, 1]
     # each sampled node keeps its own node id (its index in the full call)
     for j in (9, 50):
         r = O.interface_values(w["model"], w["nodes"][j:j + 1], w["n_paths"][j:j + 1], w["dt"],
@@ -372,9 +424,13 @@ def test_fp32_raster_walks_count_materials_like_the_oracle():
         g = sdd.sdd_walk_records(ctx, x0, z0, 9, 0, 3000, 1e-3, 31)
         o = O.walk_records(r["model"], (x0, z0), 9, 0, 3000, 1e-3, 31, urule=23)
         same = g["steps"] == o["steps"]
-        assert same.mean() >= 0.9
+        assert same.mean() >= 0.99
         eq = np.all(g["counts"][same] == o["counts"][same], axis=1)
-        assert eq.mean() >= 0.95, eq.mean()
+        assert eq.mean() >= 0.99, eq.mean()
+        # a differing walk has one step counted in a neighbouring material: a
+        # position within FP32 rounding of a cell edge
+        moved = np.abs(g["counts"][same][~eq] - o["counts"][same][~eq]).sum(1)
+        assert np.all(moved == 2), moved
 
 
 def test_graph_mode_equals_direct_launches():

@@ -40,7 +40,7 @@ def _buffers(torch, w, E):
 def _run(fn, ctx, w, b, mean, se, cnt, stream):
     fn(ctx, b["nodes"].data_ptr(), len(w["nodes"]), w["n_paths"], w["dt"], w["seed"],
        b[mean].data_ptr(), b[se].data_ptr(), d_counters_ptr=b[cnt].data_ptr(),
-       stream=stream.cuda_stream)
+       stream=stream.cuda_stream, **w.get("cfg", {}))
 
 
 def test_no_alloc_entry_point_matches_the_allocating_one():
@@ -52,8 +52,14 @@ def test_no_alloc_entry_point_matches_the_allocating_one():
     first["seed"] = 11
     second = I.scaled(I.workload("block"), n_nodes=40, paths_per_node=2000, dt=1e-3)
     second["seed"] = 12
+    # 64 nodes x 5003 walks in chunks of 32 would need 10048 work items, more
+    # than SDD_NOALLOC_MAX_ITEMS: the call widens its chunks to 40 walks (8064
+    # items, the last of each node 3 walks)
+    third = I.scaled(I.workload("quarterspace"), n_nodes=64, paths_per_node=5003, dt=1e-3)
+    third["seed"] = 13
+    third["cfg"] = {"chunk_paths": 32}
     cases = []
-    for w in (first, second):
+    for w in (first, second, third):
         ctx = sdd.sdd_create(w["model"])
         b = _buffers(torch, w, ctx.E)
         # reference: the allocating device entry point
@@ -79,6 +85,10 @@ def test_no_alloc_entry_point_matches_the_allocating_one():
 
     # more nodes than the fixed scratch holds: a clear argument error, no work
     ctx, w, b = cases[0]
+    with pytest.raises(sdd.SddError) as err:
+        sdd.sdd_interface_values_noalloc(ctx, b["nodes"].data_ptr(), len(w["nodes"]), w["n_paths"], w["dt"], 1,
+                                         b["mean2"].data_ptr(), b["se2"].data_ptr(), use_graph=1)
+    assert err.value.status == sdd.SDD_E_UNSUPPORTED
     many = sdd.lib().sdd_interface_values_noalloc
     n_big = 4097
     npth = np.ones(n_big, dtype=np.int64)
