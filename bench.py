@@ -175,11 +175,16 @@ def cpu_baseline(w, seconds_target: float = 15.0):
             "seconds": el}
 
 
-def serving(sdd, n_requests: int, seed: int = 5):
-    """Serving run: a Poisson stream of random raster requests (16-1024 nodes,
-    target complex SE 1e-3, pilot 4096, cap 1e6 walks per node, dt 1e-3).
-    Closed loop for capacity, open loop at 0.7 x capacity for p50/p99
-    latency, and the same arrivals served one request per launch, in order."""
+def serving(sdd, n_requests: int, seed: int = 5, prefix: int = 200):
+    """Serving run on the C5 request stream: random raster requests (16-1024
+    nodes, target complex SE 1e-3, pilot 4096, cap 1e6 walks per node, dt 1e-3).
+      - capacity: the server in closed loop (every request of the first
+        `prefix` submitted at t = 0) against one request per launch on the
+        same requests (the sum of their service times);
+      - latency: all n_requests on Poisson arrivals at 0.7 x the capacity of
+        one request per launch, served by the server (open loop), and the
+        same arrivals served one request per launch in order (FIFO over the
+        measured service times of every request)."""
     rng = np.random.default_rng(seed)
     reqs = [I.random_request(rng, i) for i in range(n_requests)]
     for r in reqs:
@@ -215,22 +220,10 @@ def serving(sdd, n_requests: int, seed: int = 5):
             out.append(free_at - a)
         return np.array(out)
 
-    srv = make_server()
-    # closed loop: every request at t = 0
-    lat_c, span_c = open_loop(srv, np.zeros(len(reqs)))
-    cap = len(reqs) / span_c
-    st0 = srv.stats()
-    # open loop at 0.7 x capacity
-    arr = np.cumsum(np.random.default_rng(seed + 1).exponential(1.0 / (0.7 * cap), len(reqs)))
-    arr -= arr[0]
-    lat, span = open_loop(srv, arr)
-    st1 = srv.stats()
-    srv.close()
-    steps = st1["steps"] - st0["steps"]
-    # baseline: one request per launch, served in arrival order on the same arrivals
-    # (a request brings its model: its upload is part of the service, as it is
-    # part of a served request's latency)
-    service = []
+    # one request per launch: every request's service time (a request brings
+    # its model: its upload is part of the service, as it is part of a served
+    # request's latency)
+    service, t_kernel = [], 0.0
     for r in reqs:
         t = time.perf_counter()
         ctx = sdd.sdd_create(r["model"])
@@ -238,6 +231,21 @@ def serving(sdd, n_requests: int, seed: int = 5):
                                         1e-3, seed, node_ids=r["node_ids"])
         ctx.close()
         service.append(time.perf_counter() - t)
+    cap_base = len(reqs) / sum(service)
+    # server capacity: closed loop over the prefix
+    pre = reqs[:prefix]
+    srv = make_server()
+    st0 = srv.stats()
+    _, span_c = open_loop(srv, np.zeros(len(pre)), pre)
+    st1 = srv.stats()
+    cap = len(pre) / span_c
+    steps_c = st1["steps"] - st0["steps"]
+    # latency: Poisson arrivals at 0.7 x the capacity of one request per launch
+    arr = np.cumsum(np.random.default_rng(seed + 1).exponential(1.0 / (0.7 * cap_base), len(reqs)))
+    arr -= arr[0]
+    lat, span = open_loop(srv, arr)
+    st2 = srv.stats()
+    srv.close()
     base_lat = fifo(arr, service)
     # the plain form: one node per launch (pilot + top-up per node), on the
     # first requests only (it is far slower)
@@ -291,13 +299,19 @@ def serving(sdd, n_requests: int, seed: int = 5):
             "capacity_req_per_s": cap_base_s,
             "p50_ms": 1e3 * float(np.percentile(base_s, 50)),
             "p99_ms": 1e3 * float(np.percentile(base_s, 99))}}
-    return {"requests": len(reqs), "arrivals": "Poisson at 0.7 x closed-loop capacity",
-            "capacity_req_per_s": cap, "p50_ms": 1e3 * float(np.percentile(lat, 50)),
-            "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-            "steps_per_s": steps / span, "launches": int(st1["launches"] - st0["launches"]),
+    return {"requests": len(reqs),
+            "capacity_req_per_s": cap, "capacity_requests": len(pre),
+            "capacity_steps_per_s": steps_c / span_c,
+            "baseline_capacity_same_requests": len(pre) / sum(service[:len(pre)]),
+            "capacity_gain": cap / (len(pre) / sum(service[:len(pre)])),
+            "arrivals": "Poisson at 0.7 x the capacity of one request per launch (all requests)",
+            "arrival_rate_req_per_s": 0.7 * cap_base,
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "steps_per_s": (st2["steps"] - st1["steps"]) / span,
+            "launches": int(st2["launches"] - st0["launches"]),
             "node_solves_per_s": total_nodes / span,
             "baseline_one_request_per_launch": {
-                "capacity_req_per_s": len(reqs) / sum(service),
+                "capacity_req_per_s": cap_base,
                 "p50_ms": 1e3 * float(np.percentile(base_lat, 50)),
                 "p99_ms": 1e3 * float(np.percentile(base_lat, 99))},
             "baseline_one_node_per_launch": {
@@ -818,7 +832,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--graph", action="store_true", help="run each step as a CUDA graph")
-    ap.add_argument("--serve-requests", type=int, default=24,
+    ap.add_argument("--serve-requests", type=int, default=400,
                     help="requests of the serving measurement (0 skips it)")
     ap.add_argument("--small", action="store_true",
                     help="16 nodes x 1e5 walks of the same workload (for profiler captures)")

@@ -46,7 +46,9 @@
  *    SDD_OK and SDD_E_TRUNCATED the outputs are undefined.  SDD_E_TRUNCATED
  *    means some walks reached max_steps: they are left out of the averages,
  *    the outputs are valid and stats->truncated counts them.
- *  - A context may be used from one host thread at a time.
+ *  - A context may be used from one host thread at a time, except that
+ *    asynchronous requests (sdd_interface_values_async) may be submitted to
+ *    one context from several threads.
  */
 #ifndef SDD_H
 #define SDD_H
@@ -75,6 +77,7 @@ typedef enum {
 #define SDD_MAX_SHAPES 16
 
 typedef struct sdd_ctx sdd_ctx;
+typedef struct sdd_request sdd_request;
 
 /* Rectangular domain Omega = [x_min, x_max] x [z_min, z_max]. */
 typedef struct {
@@ -353,6 +356,43 @@ sdd_status sdd_interface_values_noalloc(sdd_ctx *ctx, const double *d_nodes_xz,
                                         const int64_t *n_paths, double dt, uint64_t seed,
                                         const sdd_config *cfg, double *d_mean, double *d_se,
                                         uint64_t *d_counters, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Asynchronous requests: the evaluation of sdd_interface_values (the Monte
+ * Carlo estimator of Sec. 3.1 at every node), queued without waiting.
+ *
+ * sdd_interface_values_async copies its inputs (nodes_xz, node_ids nullable,
+ * n_paths; host arrays, free to reuse on return), queues the walks, the
+ * reduction and the download of the results on `stream` (a cudaStream_t; NULL
+ * gives the request a stream of its own) and returns a request in *out.  The
+ * request owns its device and page-locked host scratch, so a context may have
+ * several requests in flight, submitted from several host threads.  Results
+ * equal those of sdd_interface_values on the same inputs (the same plan and
+ * walks), up to the FP64 summation order within a work item.
+ *   sdd_poll      SDD_E_BUSY while running; then the request's status:
+ *                 SDD_OK, SDD_E_TRUNCATED, SDD_E_CANCELLED or an error.
+ *   sdd_wait      waits up to timeout_ms (< 0: no limit); SDD_E_TIMEOUT if
+ *                 the request is still running then, else as sdd_poll.
+ *   sdd_cancel    stops handing out walks: the walks already started end,
+ *                 the rest are skipped, and the request ends with
+ *                 SDD_E_CANCELLED (outputs undefined).  A cancel that reaches
+ *                 the GPU before the walks start leaves them to run, and the
+ *                 request still ends cancelled.  Returns at once.
+ *   sdd_request_result  copies mean [n_nodes][n_eval][2] and se (as
+ *                 sdd_interface_values) and stats (nullable) once the request
+ *                 has ended with SDD_OK or SDD_E_TRUNCATED; otherwise returns
+ *                 its status (SDD_E_BUSY while running).
+ *   sdd_request_free  waits for the request's GPU work, then frees it.
+ * Errors at submission: those of sdd_interface_values; SDD_E_UNSUPPORTED for
+ * cfg->use_graph != 0; SDD_E_ARG for a context of another device. */
+sdd_status sdd_interface_values_async(sdd_ctx *ctx, const double *nodes_xz, const uint32_t *node_ids,
+                                      int32_t n_nodes, const int64_t *n_paths, double dt, uint64_t seed,
+                                      const sdd_config *cfg, void *stream, sdd_request **out);
+sdd_status sdd_poll(sdd_request *req);
+sdd_status sdd_wait(sdd_request *req, int64_t timeout_ms);
+sdd_status sdd_cancel(sdd_request *req);
+sdd_status sdd_request_result(sdd_request *req, double *mean, double *se, sdd_stats *stats);
+void sdd_request_free(sdd_request *req);
 
 /* ------------------------------------------------------------------------
  * Path ranges and their reduction: one evaluation split across processes.

@@ -103,6 +103,8 @@ struct Plan {
     std::vector<Item> items;
     std::vector<int32_t> node_item0;  // [n_nodes + 1]
     std::vector<int32_t> order;
+    std::vector<int32_t> qbase;       // grouped launches: [queues + 1] offsets into order
+    std::vector<float> home_cut;      // grouped launches: [queues + 1] CTA shares
     long long total_paths = 0;
     bool cached = false;     // identical to the table already on the device
 };
@@ -149,6 +151,7 @@ struct sdd_ctx {
     uint64_t graph_updates = 0, graph_instantiations = 0;
     int tune_block = 0, tune_k = 0;        // autotuned threads per CTA, guided factor (0: none)
     bool tune_file_read = false;
+    std::mutex submit_mu;                  // asynchronous requests may be submitted from several threads
 };
 
 namespace {
@@ -480,6 +483,70 @@ Launch choose_launch(const sdd_ctx *ctx, const sdd_config *cfg, double dt,
     return L;
 }
 
+// Guided cuts of the paths of `nodes` (count[j] each): the sequence (node, k
+// = the node's item index, size) in the order the queue hands the items out,
+// sizes shrinking from about R / WF toward cmin (R the paths not yet cut, WF
+// the warps x the guided factor).  In rounds, every node with paths left gets
+// one item of the round's size.  When a round would take every node whole
+// (many nodes, each with fewer paths than the round's size), the size is
+// recomputed after every cut instead, nodes in turn, so that the last part of
+// the queue still shrinks toward one walk per lane.
+struct Cut {
+    int32_t node, k, count;
+};
+
+void guided_cuts(const std::vector<int32_t> &nodes, const int64_t *count, long long WF, long long cmin,
+                 std::vector<int32_t> &per_node, std::vector<Cut> &seq) {
+    std::vector<int32_t> live;
+    long long R = 0, cmax = 0;
+    for (int32_t j : nodes)
+        if (count[j] > 0) {
+            live.push_back(j);
+            R += count[j];
+            cmax = std::max<long long>(cmax, count[j]);
+        }
+    auto size = [&](long long rem) {
+        long long c = (rem + WF - 1) / WF;
+        c = std::max(cmin, (c + 31) / 32 * 32);
+        return std::min<long long>(c, 1 << 24);
+    };
+    std::vector<int64_t> left(live.size());
+    for (size_t i = 0; i < live.size(); ++i) left[i] = count[live[i]];
+    if (size(R) >= cmax && live.size() > 1) {
+        // one cut at a time, nodes in turn
+        size_t at = 0, n_live = live.size();
+        while (n_live > 0) {
+            while (left[at] == 0) at = at + 1 == live.size() ? 0 : at + 1;
+            const int64_t take = std::min<int64_t>(size(R), left[at]);
+            const int32_t j = live[at];
+            seq.push_back({j, per_node[j]++, (int32_t)take});
+            left[at] -= take;
+            R -= take;
+            if (left[at] == 0) --n_live;
+            at = at + 1 == live.size() ? 0 : at + 1;
+        }
+        return;
+    }
+    while (!live.empty()) {
+        const long long c = size(R);
+        size_t keep = 0;
+        for (size_t i = 0; i < live.size(); ++i) {
+            const int32_t j = live[i];
+            const int64_t take = std::min<int64_t>(c, left[i]);
+            seq.push_back({j, per_node[j]++, (int32_t)take});
+            left[i] -= take;
+            R -= take;
+            if (left[i] > 0) {
+                live[keep] = j;
+                left[keep] = left[i];
+                ++keep;
+            }
+        }
+        live.resize(keep);
+        left.resize(keep);
+    }
+}
+
 // Items for paths [offset + begin[j], offset + begin[j] + count[j]) of every
 // node j (begin == nullptr: from 0), for the launch L.
 //   Fixed (L.chunk > 0): items of L.chunk paths, node by node.
@@ -513,29 +580,11 @@ Plan plan_work(int32_t n_nodes, const int64_t *begin, const int64_t *count, uint
     }
     const long long W = std::max<long long>(1, (long long)L.grid * (L.block / 32) * std::max(L.factor, 1));
     const long long cmin = std::max<long long>(32, (P.total_paths / (1 << 20) + 31) / 32 * 32);
-    struct Cut {
-        int32_t node, k, count;
-    };
     std::vector<Cut> seq;
-    std::vector<int32_t> live, per_node((size_t)n_nodes, 0);
+    std::vector<int32_t> all((size_t)n_nodes), per_node((size_t)n_nodes, 0);
     std::vector<int64_t> done((size_t)n_nodes, 0);
-    for (int j = 0; j < n_nodes; ++j)
-        if (count[j] > 0) live.push_back(j);
-    long long R = P.total_paths;
-    while (!live.empty()) {
-        long long c = (R + W - 1) / W;
-        c = std::max(cmin, (c + 31) / 32 * 32);
-        c = std::min<long long>(c, 1 << 24);
-        size_t keep = 0;
-        for (int32_t j : live) {
-            const int64_t take = std::min<int64_t>(c, count[j] - done[j]);
-            seq.push_back({j, per_node[j]++, (int32_t)take});
-            done[j] += take;
-            R -= take;
-            if (done[j] < count[j]) live[keep++] = j;
-        }
-        live.resize(keep);
-    }
+    for (int j = 0; j < n_nodes; ++j) all[j] = j;
+    guided_cuts(all, count, W, cmin, per_node, seq);
     for (int j = 0; j < n_nodes; ++j) P.node_item0[j + 1] = P.node_item0[j] + per_node[j];
     P.items.resize(seq.size());
     P.order.resize(seq.size());
@@ -551,6 +600,64 @@ Plan plan_work(int32_t n_nodes, const int64_t *begin, const int64_t *count, uint
         done[x.node] += x.count;
         P.order[q] = idx;
     }
+    return P;
+}
+
+// Items of a launch over several models, one queue per model (the models of
+// a batched or served launch each have their own tile map; keeping an SM on
+// few models keeps their tile maps in its L1).  Model m's nodes are cut with
+// the guided sizes of plan_work for the warps of its share of the grid (its
+// share of the walks), the queue of model m hands its items out in cut
+// order, and CTAs are homed on the queues in proportion to the shares.  The
+// item table stays node by node (the per-node sums add items in path order).
+Plan plan_grouped(int32_t n_nodes, const int64_t *begin, const int64_t *count, const int32_t *node_model,
+                  int32_t n_models, const Launch &L) {
+    Plan P;
+    P.node_item0.assign((size_t)n_nodes + 1, 0);
+    std::vector<long long> walks((size_t)n_models, 0);
+    for (int j = 0; j < n_nodes; ++j) {
+        P.total_paths += count[j];
+        walks[node_model[j]] += count[j];
+    }
+    auto first = [&](int j) -> int64_t { return begin ? begin[j] : 0; };
+    const long long Wall = std::max<long long>(1, (long long)L.grid * (L.block / 32));
+    const long long F = std::max(L.factor, 1);
+    const long long cmin = std::max<long long>(32, (P.total_paths / (1 << 20) + 31) / 32 * 32);
+    std::vector<std::vector<int32_t>> nodes_of((size_t)n_models);
+    for (int j = 0; j < n_nodes; ++j) nodes_of[node_model[j]].push_back(j);
+    std::vector<std::vector<Cut>> seq((size_t)n_models);
+    std::vector<int32_t> per_node((size_t)n_nodes, 0);
+    std::vector<int64_t> done((size_t)n_nodes, 0);
+    P.home_cut.assign((size_t)n_models + 1, 0.f);
+    long long acc = 0;
+    for (int m = 0; m < n_models; ++m) {
+        P.home_cut[m] = P.total_paths ? (float)((double)acc / (double)P.total_paths) : 0.f;
+        acc += walks[m];
+        const long long W = std::max<long long>(1, (long long)std::llround((double)Wall * walks[m] /
+                                                                          std::max<double>(1.0, (double)P.total_paths))) * F;
+        guided_cuts(nodes_of[m], count, W, cmin, per_node, seq[m]);
+    }
+    P.home_cut[n_models] = 1.f;
+    for (int j = 0; j < n_nodes; ++j) P.node_item0[j + 1] = P.node_item0[j] + per_node[j];
+    const size_t ni = (size_t)P.node_item0[n_nodes];
+    P.items.resize(ni);
+    P.order.reserve(ni);
+    P.qbase.assign((size_t)n_models + 1, 0);
+    std::fill(done.begin(), done.end(), 0);
+    for (int m = 0; m < n_models; ++m) {
+        P.qbase[m] = (int32_t)P.order.size();
+        for (const Cut &x : seq[m]) {
+            const int32_t idx = P.node_item0[x.node] + x.k;
+            Item &I = P.items[idx];
+            I.node = x.node;
+            I.path0 = (uint32_t)(first(x.node) + done[x.node]);
+            I.count = x.count;
+            I.model = m;
+            done[x.node] += x.count;
+            P.order.push_back(idx);
+        }
+    }
+    P.qbase[n_models] = (int32_t)P.order.size();
     return P;
 }
 
@@ -601,7 +708,36 @@ WalkArgs base_args(sdd_ctx *ctx, const Launch &L, double dt, uint64_t seed) {
 // holds this plan.
 size_t table_bytes(const Plan &P, int n_nodes) {
     return P.items.size() * sizeof(Item) + ((size_t)n_nodes + 1) * sizeof(int32_t) +
-           P.order.size() * sizeof(int32_t);
+           P.order.size() * sizeof(int32_t) + P.qbase.size() * sizeof(int32_t) +
+           P.home_cut.size() * sizeof(float);
+}
+
+// The item table as uploaded: items, node_item0, order, then (grouped
+// launches) qbase and home_cut.
+void pack_table(const Plan &P, int n_nodes, unsigned char *h) {
+    const size_t ni = P.items.size();
+    std::memcpy(h, P.items.data(), ni * sizeof(Item));
+    h += ni * sizeof(Item);
+    std::memcpy(h, P.node_item0.data(), ((size_t)n_nodes + 1) * sizeof(int32_t));
+    h += ((size_t)n_nodes + 1) * sizeof(int32_t);
+    if (!P.order.empty()) std::memcpy(h, P.order.data(), P.order.size() * sizeof(int32_t));
+    h += P.order.size() * sizeof(int32_t);
+    if (!P.qbase.empty()) std::memcpy(h, P.qbase.data(), P.qbase.size() * sizeof(int32_t));
+    h += P.qbase.size() * sizeof(int32_t);
+    if (!P.home_cut.empty()) std::memcpy(h, P.home_cut.data(), P.home_cut.size() * sizeof(float));
+}
+
+// Device pointers of a packed table at d: order, qbase, home_cut and the
+// number of queues.
+void table_args(const Plan &P, int n_nodes, const unsigned char *d, WalkArgs &A) {
+    const size_t ni = P.items.size();
+    const unsigned char *o = d + ni * sizeof(Item) + ((size_t)n_nodes + 1) * sizeof(int32_t);
+    A.order = P.order.empty() ? nullptr : reinterpret_cast<const int32_t *>(o);
+    o += P.order.size() * sizeof(int32_t);
+    A.qbase = P.qbase.empty() ? nullptr : reinterpret_cast<const int32_t *>(o);
+    o += P.qbase.size() * sizeof(int32_t);
+    A.home_cut = P.home_cut.empty() ? nullptr : reinterpret_cast<const float *>(o);
+    A.n_queues = P.qbase.empty() ? 1 : (int32_t)P.qbase.size() - 1;
 }
 
 sdd_status prepare(sdd_ctx *ctx, const Plan &P, int n_nodes, cudaStream_t s) {
@@ -612,7 +748,7 @@ sdd_status prepare(sdd_ctx *ctx, const Plan &P, int n_nodes, cudaStream_t s) {
     SDD_CUDA(ctx->slots.ensure(ni * (size_t)ctx->E * 4 * sizeof(double)));
     SDD_CUDA(ctx->trunc.ensure(ni * sizeof(int32_t)));
     SDD_CUDA(ctx->counters.ensure(3 * sizeof(unsigned long long)));
-    SDD_CUDA(ctx->queue.ensure(sizeof(int32_t)));
+    SDD_CUDA(ctx->queue.ensure(std::max<size_t>(P.qbase.size(), 1) * sizeof(int32_t)));
     SDD_CUDA(ctx->err.ensure(sizeof(int32_t)));
     ctx->last_h2d = 0;
     const bool own = &P == &ctx->plan;
@@ -625,12 +761,7 @@ sdd_status prepare(sdd_ctx *ctx, const Plan &P, int n_nodes, cudaStream_t s) {
             SDD_CUDA(cudaMallocHost((void **)&ctx->h_items, hbytes + hbytes / 4 + 256));
             ctx->h_items_cap = hbytes + hbytes / 4 + 256;
         }
-        unsigned char *h = reinterpret_cast<unsigned char *>(ctx->h_items);
-        std::memcpy(h, P.items.data(), ni * sizeof(Item));
-        h += ni * sizeof(Item);
-        std::memcpy(h, P.node_item0.data(), ((size_t)n_nodes + 1) * sizeof(int32_t));
-        h += ((size_t)n_nodes + 1) * sizeof(int32_t);
-        if (!P.order.empty()) std::memcpy(h, P.order.data(), P.order.size() * sizeof(int32_t));
+        pack_table(P, n_nodes, reinterpret_cast<unsigned char *>(ctx->h_items));
         SDD_CUDA(cudaMemcpyAsync(ctx->items.p, ctx->h_items, hbytes, cudaMemcpyHostToDevice, s));
         SDD_CUDA(cudaEventRecord(ctx->items_done, s));
         ctx->last_h2d = hbytes;
@@ -646,13 +777,11 @@ sdd_status enqueue(sdd_ctx *ctx, const Plan &P, const Launch &L, WalkArgs A, cud
     const ModelDev &MD = model ? *model : ctx->M;
     const size_t ni = P.items.size();
     if (ni == 0) return SDD_OK;
-    SDD_CUDA(cudaMemsetAsync(ctx->queue.p, 0, sizeof(int32_t), s));
+    SDD_CUDA(cudaMemsetAsync(ctx->queue.p, 0, std::max<size_t>(P.qbase.size(), 1) * sizeof(int32_t), s));
     SDD_CUDA(cudaMemsetAsync(ctx->counters.p, 0, 3 * sizeof(unsigned long long), s));
     A.items = (const Item *)ctx->items.p;
     A.n_items = (int32_t)ni;
-    A.order = P.order.empty() ? nullptr
-                              : reinterpret_cast<const int32_t *>(reinterpret_cast<unsigned char *>(ctx->items.p) +
-                                                                  ni * sizeof(Item) + ((size_t)n_nodes + 1) * sizeof(int32_t));
+    table_args(P, n_nodes, reinterpret_cast<const unsigned char *>(ctx->items.p), A);
     A.slots = (double *)ctx->slots.p;
     A.item_trunc = (int32_t *)ctx->trunc.p;
     A.counters = (unsigned long long *)ctx->counters.p;
@@ -1367,6 +1496,248 @@ extern "C" sdd_status sdd_reduce_sums(sdd_ctx *ctx, int32_t n_nodes, int32_t n_r
 }
 
 // ---------------------------------------------------------------------------
+// Asynchronous requests (sdd_interface_values_async, sdd_poll, sdd_wait,
+// sdd_cancel, sdd_request_result, sdd_request_free).
+//
+// A request owns its scratch -- one device block (nodes, node ids, item
+// table, per-item sums, counters, work queue, outputs) and one page-locked
+// host block (the staged inputs and the outputs) -- so several requests of
+// one context can be in flight at once, on one stream or several.  Its
+// walks are those of sdd_interface_values: the same plan, launch and fixed-
+// order reduction, queued on the request's stream.  Cancelling sets the
+// request's cancel flag from a side stream: a warp that finds it set when it
+// next refills its lanes hands out no more paths, so the launch ends once
+// the walks in flight are done.
+
+struct sdd_request {
+    sdd_ctx *ctx = nullptr;
+    int32_t n_nodes = 0, E = 0;
+    size_t n_items = 0;
+    cudaStream_t stream = nullptr;  // the caller's, or own_stream
+    cudaStream_t own_stream = nullptr, cancel_stream = nullptr;
+    cudaEvent_t done = nullptr, ev0 = nullptr, ev1 = nullptr;
+    unsigned char *dev = nullptr, *host = nullptr;
+    size_t off_mean = 0, off_se = 0, off_cnt = 0, off_flag = 0, off_cancel = 0;
+    Launch L{};
+    uint64_t h2d = 0;
+    std::atomic<int> cancelled{0};
+    bool finished = false;
+    sdd_status status = SDD_OK;
+    std::mutex mu;
+};
+
+namespace {
+
+size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+void request_release(sdd_request *r) {
+    if (r->done) cudaEventSynchronize(r->done);
+    if (r->cancel_stream) cudaStreamSynchronize(r->cancel_stream);
+    if (r->dev) cudaFree(r->dev);
+    if (r->host) cudaFreeHost(r->host);
+    if (r->done) cudaEventDestroy(r->done);
+    if (r->ev0) cudaEventDestroy(r->ev0);
+    if (r->ev1) cudaEventDestroy(r->ev1);
+    if (r->own_stream) cudaStreamDestroy(r->own_stream);
+    if (r->cancel_stream) cudaStreamDestroy(r->cancel_stream);
+    delete r;
+}
+
+// Completion of a request whose done event has fired (caller holds r->mu).
+void request_finish(sdd_request *r) {
+    if (r->finished) return;
+    r->finished = true;
+    const unsigned long long *cnt = reinterpret_cast<const unsigned long long *>(r->host + r->off_cnt);
+    if (r->cancelled.load()) r->status = SDD_E_CANCELLED;
+    else r->status = cnt[2] ? SDD_E_TRUNCATED : SDD_OK;
+}
+
+}  // namespace
+
+extern "C" sdd_status sdd_interface_values_async(sdd_ctx *ctx, const double *nodes_xz, const uint32_t *node_ids,
+                                                 int32_t n_nodes, const int64_t *n_paths, double dt,
+                                                 uint64_t seed, const sdd_config *cfg, void *stream,
+                                                 sdd_request **out) {
+    if (!out) return fail(SDD_E_ARG, "out is NULL");
+    *out = nullptr;
+    sdd_status st = check_call(ctx, n_nodes, n_paths, dt, cfg);
+    if (st != SDD_OK) return st;
+    if (n_nodes > 0 && !nodes_xz) return fail(SDD_E_ARG, "nodes_xz is NULL");
+    if (cfg && cfg->use_graph) return fail(SDD_E_UNSUPPORTED, "asynchronous requests launch their kernels directly");
+    st = check_nodes(ctx, nodes_xz, n_nodes);
+    if (st != SDD_OK) return st;
+    int device = -1;
+    SDD_CUDA(cudaGetDevice(&device));
+    if (device != ctx->device) return fail(SDD_E_ARG, "the context's device is not the current device");
+    Launch L;
+    {
+        std::lock_guard<std::mutex> lk(ctx->submit_mu);
+        L = choose_launch(ctx, cfg, dt);
+    }
+    const Plan P = plan_work(n_nodes, nullptr, n_paths, 0, L);
+    sdd_request *r = new (std::nothrow) sdd_request();
+    if (!r) return fail(SDD_E_OOM, "host allocation failed");
+    r->ctx = ctx;
+    r->n_nodes = n_nodes;
+    r->E = ctx->E;
+    r->n_items = P.items.size();
+    r->L = L;
+    const size_t ni = P.items.size(), nn = (size_t)n_nodes, E = (size_t)ctx->E;
+    // one layout for both blocks: inputs (staged on the host, copied once),
+    // then device-only scratch, then the outputs (copied back)
+    const size_t o_nodes = 0, o_ids = al256(o_nodes + nn * 16), o_items = al256(o_ids + nn * 4);
+    const size_t o_i0 = al256(o_items + ni * sizeof(Item)), o_order = al256(o_i0 + (nn + 1) * 4);
+    const size_t in_bytes = al256(o_order + P.order.size() * 4);
+    const size_t o_slots = in_bytes, o_trunc = al256(o_slots + std::max<size_t>(ni, 1) * E * 32);
+    const size_t o_queue = al256(o_trunc + ni * 4), o_err = o_queue + 16, o_flag = o_queue + 24;
+    const size_t o_mean = al256(o_err + 16), o_se = al256(o_mean + nn * E * 16), o_cnt = al256(o_se + nn * E * 16);
+    const size_t total = al256(o_cnt + 32), o_cancel = total;
+    r->off_mean = o_mean; r->off_se = o_se; r->off_cnt = o_cnt; r->off_flag = o_flag; r->off_cancel = o_cancel;
+    cudaError_t e = cudaMalloc((void **)&r->dev, total);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&r->host, total + 256);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&r->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&r->ev1);
+    if (e == cudaSuccess && !stream) e = cudaStreamCreateWithFlags(&r->own_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        request_release(r);
+        return e == cudaErrorMemoryAllocation ? fail(SDD_E_OOM, "request allocation") : cuda_fail(e, "request setup");
+    }
+    r->stream = stream ? (cudaStream_t)stream : r->own_stream;
+    unsigned char *h = r->host;
+    if (nn) std::memcpy(h + o_nodes, nodes_xz, nn * 16);
+    if (node_ids) std::memcpy(h + o_ids, node_ids, nn * 4);
+    if (ni) std::memcpy(h + o_items, P.items.data(), ni * sizeof(Item));
+    std::memcpy(h + o_i0, P.node_item0.data(), (nn + 1) * 4);
+    if (!P.order.empty()) std::memcpy(h + o_order, P.order.data(), P.order.size() * 4);
+    *reinterpret_cast<int32_t *>(h + o_cancel) = 1;
+    std::memset(h + o_cnt, 0, 32);
+    cudaStream_t s = r->stream;
+    r->h2d = in_bytes;
+    sdd_status res = SDD_OK;
+    auto q = [&](cudaError_t err, const char *what) {
+        if (err != cudaSuccess && res == SDD_OK) res = cuda_fail(err, what);
+    };
+    q(cudaMemcpyAsync(r->dev, r->host, in_bytes, cudaMemcpyHostToDevice, s), "request upload");
+    if (ni > 0) {
+        q(cudaMemsetAsync(r->dev + o_queue, 0, 32, s), "request queue");
+        q(cudaMemsetAsync(r->dev + o_cnt, 0, 32, s), "request counters");
+        WalkArgs A = base_args(ctx, L, dt, seed);
+        A.nodes = reinterpret_cast<const double *>(r->dev + o_nodes);
+        A.node_ids = node_ids ? reinterpret_cast<const uint32_t *>(r->dev + o_ids) : nullptr;
+        A.items = reinterpret_cast<const Item *>(r->dev + o_items);
+        A.n_items = (int32_t)ni;
+        A.order = P.order.empty() ? nullptr : reinterpret_cast<const int32_t *>(r->dev + o_order);
+        A.slots = reinterpret_cast<double *>(r->dev + o_slots);
+        A.item_trunc = reinterpret_cast<int32_t *>(r->dev + o_trunc);
+        A.counters = reinterpret_cast<unsigned long long *>(r->dev + o_cnt);
+        A.queue = reinterpret_cast<int32_t *>(r->dev + o_queue);
+        A.error = reinterpret_cast<int32_t *>(r->dev + o_err);
+        A.cancel = reinterpret_cast<const int32_t *>(r->dev + o_flag);
+        const int wpc = L.block / 32;
+        int grid = L.grid;
+        const int need = (int)((ni + wpc - 1) / wpc);
+        if (grid > need) grid = need;
+        q(cudaEventRecord(r->ev0, s), "event");
+        if (res == SDD_OK) {
+            cudaError_t le = L.f64 ? launch_walk_f64(L.kmax, ctx->geo, ctx->M, A, grid, L.block, s)
+                                   : launch_walk_f32(L.kmax, ctx->geo, ctx->M, A, grid, L.block, s);
+            q(le, "walk kernel launch");
+        }
+        q(cudaEventRecord(r->ev1, s), "event");
+        if (res == SDD_OK) {
+            const int nt = n_nodes * ctx->E;
+            reduce_kernel<<<(nt + 127) / 128, 128, 0, s>>>(
+                A.slots, A.item_trunc, A.items, reinterpret_cast<const int32_t *>(r->dev + o_i0), n_nodes, ctx->E,
+                reinterpret_cast<double *>(r->dev + o_mean), reinterpret_cast<double *>(r->dev + o_se));
+            q(cudaGetLastError(), "reduce kernel launch");
+        }
+        q(cudaMemcpyAsync(r->host + o_mean, r->dev + o_mean, total - o_mean, cudaMemcpyDeviceToHost, s),
+          "request download");
+    }
+    q(cudaEventRecord(r->done, s), "event");
+    if (res != SDD_OK) {
+        request_release(r);
+        return res;
+    }
+    *out = r;
+    return SDD_OK;
+}
+
+extern "C" sdd_status sdd_poll(sdd_request *r) {
+    if (!r) return fail(SDD_E_ARG, "request is NULL");
+    std::lock_guard<std::mutex> lk(r->mu);
+    if (r->finished) return r->status;
+    const cudaError_t e = cudaEventQuery(r->done);
+    if (e == cudaErrorNotReady) return SDD_E_BUSY;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventQuery");
+    request_finish(r);
+    return r->status;
+}
+
+extern "C" sdd_status sdd_wait(sdd_request *r, int64_t timeout_ms) {
+    if (!r) return fail(SDD_E_ARG, "request is NULL");
+    if (timeout_ms < 0) {
+        const cudaError_t e = cudaEventSynchronize(r->done);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        return sdd_poll(r);
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const sdd_status st = sdd_poll(r);
+        if (st != SDD_E_BUSY) return st;
+        if (std::chrono::steady_clock::now() - t0 >= std::chrono::milliseconds(timeout_ms))
+            return SDD_E_TIMEOUT;
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
+}
+
+extern "C" sdd_status sdd_cancel(sdd_request *r) {
+    if (!r) return fail(SDD_E_ARG, "request is NULL");
+    std::lock_guard<std::mutex> lk(r->mu);
+    if (r->finished || r->cancelled.exchange(1)) return SDD_OK;
+    if (r->n_items == 0) return SDD_OK;
+    cudaError_t e = cudaSuccess;
+    if (!r->cancel_stream) e = cudaStreamCreateWithFlags(&r->cancel_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(r->dev + r->off_flag, r->host + r->off_cancel, sizeof(int32_t), cudaMemcpyHostToDevice,
+                            r->cancel_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cancel");
+    return SDD_OK;
+}
+
+extern "C" sdd_status sdd_request_result(sdd_request *r, double *mean, double *se, sdd_stats *stats) {
+    const sdd_status st = sdd_poll(r);
+    if (st != SDD_OK && st != SDD_E_TRUNCATED) return st;
+    const size_t ob = (size_t)r->n_nodes * r->E * 16;
+    if (r->n_nodes > 0 && (!mean || !se)) return fail(SDD_E_ARG, "mean and se must not be NULL");
+    if (ob) {
+        std::memcpy(mean, r->host + r->off_mean, ob);
+        std::memcpy(se, r->host + r->off_se, ob);
+    }
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        const unsigned long long *cnt = reinterpret_cast<const unsigned long long *>(r->host + r->off_cnt);
+        stats->steps = cnt[0];
+        stats->walks = cnt[1];
+        stats->truncated = cnt[2];
+        float ms = 0.f;
+        if (r->n_items && cudaEventElapsedTime(&ms, r->ev0, r->ev1) == cudaSuccess) stats->kernel_ms = ms;
+        stats->launches = r->n_items ? 2 : 0;
+        stats->items = (int32_t)r->n_items;
+        stats->grid = r->L.grid;
+        stats->block = r->L.block;
+        stats->h2d_bytes = r->h2d;
+        stats->d2h_bytes = r->n_items ? r->off_cancel - r->off_mean : 0;
+    }
+    return st;
+}
+
+extern "C" void sdd_request_free(sdd_request *r) {
+    if (r) request_release(r);
+}
+
+// ---------------------------------------------------------------------------
 // Adaptive path counts (sdd_interface_values_target).
 
 namespace {
@@ -1571,7 +1942,8 @@ extern "C" sdd_status sdd_batch_values(const sdd_batch_entry *entries, int32_t n
     first[n_entries] = n_nodes;
     if (n_nodes == 0) return SDD_OK;
     const Launch L = choose_launch(own, cfg, dt, kmax_for(Kmax), GC_RASTER_MULTI);
-    Plan P = plan_work(n_nodes, nullptr, paths.data(), 0, L);
+    Plan P = L.chunk > 0 ? plan_work(n_nodes, nullptr, paths.data(), 0, L)
+                         : plan_grouped(n_nodes, nullptr, paths.data(), node_model.data(), n_entries, L);
     for (Item &I : P.items) I.model = node_model[I.node];
     own->plan_valid = false;
 
@@ -1672,6 +2044,7 @@ struct SrvRequest {
     int launches = 0;
     Clock::time_point t_submit, t_first, t_done;
     bool started = false;
+    double deadline = 0.0;         // queue key of the current phase (seconds, virtual)
 };
 
 // Nodes [a, b) of a request's current phase, launched together.
@@ -1722,6 +2095,7 @@ struct sdd_server {
     int64_t bytes_in_use = 0;
     sdd_server_stats st{};
     std::string worker_error;
+    Clock::time_point t_start = Clock::now();  // origin of the virtual deadlines
 };
 
 namespace {
@@ -1732,16 +2106,27 @@ int64_t request_bytes(const sdd_server *srv, int32_t n_nodes) {
            (int64_t)sizeof(BatchModel);
 }
 
+// Walks a launch gets through per second, for the virtual deadlines below
+// (a scale only: the order of the queue depends on it, not the results).
+constexpr double kDeadlineWalksPerS = 5.0e8;
+
 // Cut a request's current phase into pieces of at most batch_walks walks
-// (whole nodes; nodes with no walks left out) and queue them in submission
-// order of their requests: a top-up phase goes ahead of the pilot phases of
-// requests submitted after it, so launches serve the oldest request first and
-// fill up with younger ones.
-void srv_queue_phase(sdd_server *srv, SrvRequest *r) {
+// (whole nodes; nodes with no walks left out) and queue them by the phase's
+// virtual deadline: the request's submission time plus the time its phase's
+// walks would take alone.  A small request (or a pilot phase) then goes ahead
+// of a large top-up submitted a little earlier, while a request submitted
+// long before keeps its place; every deadline grows with the submission
+// time, so no request waits forever.  Launches serve the earliest deadline
+// and fill up with the next ones.
+void srv_queue_phase(sdd_server *srv, SrvRequest *r, Clock::time_point t0) {
     const int32_t n = (int32_t)r->ids.size();
     int pieces = 0;
-    auto at = std::upper_bound(srv->runnable.begin(), srv->runnable.end(), r->id,
-                               [](uint64_t id, const SrvPiece &pc) { return id < pc.r->id; });
+    long long phase_walks = 0;
+    for (int32_t j = 0; j < n; ++j) phase_walks += r->count[j];
+    r->deadline = std::chrono::duration<double>(r->t_submit - t0).count() +
+                  (double)phase_walks / kDeadlineWalksPerS;
+    auto at = std::upper_bound(srv->runnable.begin(), srv->runnable.end(), r->deadline,
+                               [](double d, const SrvPiece &pc) { return d < pc.r->deadline; });
     std::vector<SrvPiece> add;
     int32_t a = 0;
     while (a < n) {
@@ -1803,7 +2188,9 @@ sdd_status srv_launch(sdd_server *srv, SrvLane &L, std::vector<SrvPiece> &batch)
     L.walks = (uint64_t)total;
     const Launch La = choose_launch(srv->tmpl, &srv->cfg.launch, srv->cfg.dt, kmax_for(Kmax),
                                     GC_RASTER_MULTI);
-    Plan P = plan_work(n_nodes, begin.data(), count.data(), 0, La);
+    Plan P = La.chunk > 0 ? plan_work(n_nodes, begin.data(), count.data(), 0, La)
+                          : plan_grouped(n_nodes, begin.data(), count.data(), node_model.data(),
+                                         (int32_t)table.size(), La);
     for (Item &I : P.items) I.model = node_model[I.node];
     const size_t ni = P.items.size();
     cudaStream_t s = L.s;
@@ -1812,7 +2199,7 @@ sdd_status srv_launch(sdd_server *srv, SrvLane &L, std::vector<SrvPiece> &batch)
     SDD_CUDA(L.slots.ensure(std::max<size_t>(ni, 1) * (size_t)E * 4 * sizeof(double)));
     SDD_CUDA(L.trunc.ensure(std::max<size_t>(ni, 1) * sizeof(int32_t)));
     SDD_CUDA(L.counters.ensure(3 * sizeof(unsigned long long)));
-    SDD_CUDA(L.queue.ensure(sizeof(int32_t)));
+    SDD_CUDA(L.queue.ensure(std::max<size_t>(P.qbase.size(), 1) * sizeof(int32_t)));
     SDD_CUDA(L.err.ensure(sizeof(int32_t)));
     SDD_CUDA(L.nodes.ensure(nodes.size() * sizeof(double)));
     SDD_CUDA(L.ids.ensure(ids.size() * sizeof(uint32_t)));
@@ -1830,23 +2217,17 @@ sdd_status srv_launch(sdd_server *srv, SrvLane &L, std::vector<SrvPiece> &batch)
         L.h_cap_nodes = n_nodes;
     }
     std::vector<unsigned char> hi(tb);
-    std::memcpy(hi.data(), P.items.data(), ni * sizeof(Item));
-    std::memcpy(hi.data() + ni * sizeof(Item), P.node_item0.data(), (n_nodes + 1) * sizeof(int32_t));
-    if (!P.order.empty())
-        std::memcpy(hi.data() + ni * sizeof(Item) + (n_nodes + 1) * sizeof(int32_t), P.order.data(),
-                    P.order.size() * sizeof(int32_t));
+    pack_table(P, n_nodes, hi.data());
     SDD_CUDA(cudaMemcpyAsync(L.items.p, hi.data(), hi.size(), cudaMemcpyHostToDevice, s));
     SDD_CUDA(cudaMemcpyAsync(L.nodes.p, nodes.data(), nodes.size() * sizeof(double), cudaMemcpyHostToDevice, s));
     SDD_CUDA(cudaMemcpyAsync(L.ids.p, ids.data(), ids.size() * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
     SDD_CUDA(cudaMemcpyAsync(L.models.p, table.data(), table.size() * sizeof(BatchModel), cudaMemcpyHostToDevice, s));
-    SDD_CUDA(cudaMemsetAsync(L.queue.p, 0, sizeof(int32_t), s));
+    SDD_CUDA(cudaMemsetAsync(L.queue.p, 0, std::max<size_t>(P.qbase.size(), 1) * sizeof(int32_t), s));
     SDD_CUDA(cudaMemsetAsync(L.counters.p, 0, 3 * sizeof(unsigned long long), s));
     WalkArgs A = base_args(srv->tmpl, La, srv->cfg.dt, srv->cfg.seed);
     A.items = (const Item *)L.items.p;
     A.n_items = (int32_t)ni;
-    if (!P.order.empty())
-        A.order = reinterpret_cast<const int32_t *>(reinterpret_cast<unsigned char *>(L.items.p) +
-                                                    ni * sizeof(Item) + (n_nodes + 1) * sizeof(int32_t));
+    table_args(P, n_nodes, reinterpret_cast<const unsigned char *>(L.items.p), A);
     A.nodes = (const double *)L.nodes.p;
     A.node_ids = (const uint32_t *)L.ids.p;
     A.slots = (double *)L.slots.p;
@@ -1919,7 +2300,7 @@ void srv_phase_done(sdd_server *srv, SrvRequest *r) {
         }
         if (extra_total > 0) {
             r->phase = 2;
-            srv_queue_phase(srv, r);
+            srv_queue_phase(srv, r, srv->t_start);
             return;
         }
     }
@@ -1974,22 +2355,35 @@ void srv_worker(sdd_server *srv) {
         }
         for (SrvLane &L : srv->lanes) {
             if (L.busy || srv->runnable.empty() || srv->stop) continue;
+            // The launch serves the oldest runnable piece and fills up with the
+            // pieces, in queue order, whose models need the same material bound
+            // (kmax_for(K): 2, 3, 4 or 8): a batch runs the kernel of its class,
+            // so requests with few materials keep the faster per-step counters
+            // instead of the shared-memory histogram that one 8-material model
+            // would impose on the whole launch.
             std::vector<SrvPiece> batch;
             std::map<SrvRequest *, int> models;
             int64_t walks = 0;
-            while (!srv->runnable.empty()) {
-                const SrvPiece pc = srv->runnable.front();
+            int cls = 0;
+            for (auto it = srv->runnable.begin(); it != srv->runnable.end();) {
+                const SrvPiece pc = *it;
                 if (pc.r->cancelled) {
-                    srv->runnable.pop_front();
+                    it = srv->runnable.erase(it);
                     if (--pc.r->pieces_left == 0) srv_finish(srv, pc.r);
                     progress = true;
+                    continue;
+                }
+                const int c = kmax_for(pc.r->K);
+                if (batch.empty()) cls = c;
+                if (c != cls) {
+                    ++it;
                     continue;
                 }
                 const bool new_model = models.find(pc.r) == models.end();
                 if (!batch.empty() && (walks + pc.walks > srv->batch_walks ||
                                        (new_model && (int)models.size() >= srv->cfg.max_batch_models)))
                     break;
-                srv->runnable.pop_front();
+                it = srv->runnable.erase(it);
                 models[pc.r] = 1;
                 walks += pc.walks;
                 if (!pc.r->started) {
@@ -2207,7 +2601,7 @@ extern "C" sdd_status sdd_server_submit(sdd_server *srv, const sdd_request_desc 
     r->t_submit = Clock::now();
     srv->reqs[r->id] = r;
     r->phase = 0;
-    srv_queue_phase(srv, r);
+    srv_queue_phase(srv, r, srv->t_start);
     *id = r->id;
     lk.unlock();
     srv->cv.notify_all();

@@ -144,8 +144,15 @@ struct WalkArgs {
                                // (cleared by the warp that opens the item)
     int32_t *item_trunc;       // [n_items] truncated walks (cleared likewise)
     unsigned long long *counters;  // steps, walks, truncated
-    int32_t *queue;            // next item (zero before launch)
+    int32_t *queue;            // next item (zero before launch); one counter per queue
+    // grouped launches (several models): queue m hands out order[qbase[m] ..
+    // qbase[m+1]); a CTA starts on queue m when (blockIdx + 1/2) / gridDim
+    // falls in [home_cut[m], home_cut[m+1]) and moves on when it is empty
+    const int32_t *qbase;      // [n_queues + 1] (nullptr: one queue over order)
+    const float *home_cut;     // [n_queues + 1]
+    int32_t n_queues;
     int32_t *error;            // nonzero if a device-side check failed
+    const int32_t *cancel;     // nullable; nonzero: hand out no more paths (asynchronous requests)
     // per-path dump (sdd_walk_records); when rec_steps != nullptr the walk
     // records are written here instead of being summed
     int64_t *rec_steps;

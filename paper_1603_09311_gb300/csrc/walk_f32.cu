@@ -116,6 +116,7 @@ struct WalkerF32 {
     using HistT = uint32_t;
     static constexpr int kStored = KMAX - 1;
     static constexpr int kHist = KMAX == 8 ? 8 : 1;
+    static constexpr bool kGrouped = GC == GC_RASTER_MULTI;
 
     float X, Z, dmin;  // centred position, distance to the nearest wall
     uint32_t n;        // Euler steps accepted (even at the start of iterate)
@@ -346,60 +347,6 @@ struct WalkerF32 {
             if (j < cnt) occ.add(m[j]);
     }
 
-    // Steps g .. g + kGroup - 1 of an iteration with one near-wall branch:
-    // the positions of the group are formed first (they do not depend on the
-    // wall tests unless the walk exits), and only when some step of the
-    // group came within reach of a wall are its steps tested one by one in
-    // order, exactly as advance() does; otherwise each step's material is
-    // counted.  Walk decisions are those of advance() step by step.
-#ifndef SDD_STEP_GROUP
-#define SDD_STEP_GROUP 1
-#endif
-    static constexpr int kGroup = SDD_STEP_GROUP;
-    template <int NQ>
-    __device__ __forceinline__ bool group(const ModelDev &M, const WalkArgs &A, const uint4 (&w)[NQ], int g,
-                                          ExitInfo<float> &ei) {
-        float xs[kGroup + 1], zs[kGroup + 1], ds[kGroup + 1], ps[kGroup];
-        uint32_t wa[kGroup], wb[kGroup];
-        xs[0] = X;
-        zs[0] = Z;
-        ds[0] = dmin;
-        float pmin = 3.0e38f;
-#pragma unroll
-        for (int k = 0; k < kGroup; ++k) {
-            const int st = g + k;
-            wa[k] = (st & 1) ? w[st >> 1].z : w[st >> 1].x;
-            wb[k] = (st & 1) ? w[st >> 1].w : w[st >> 1].y;
-            const Incr d = increment(A, wa[k], wb[k]);
-            xs[k + 1] = fmaf(-d.r, d.cs, xs[k]);
-            zs[k + 1] = fmaf(-d.r, d.sn, zs[k]);
-            ds[k + 1] = fminf(M.fhw - fabsf(xs[k + 1]), M.fhh - fabsf(zs[k + 1]));
-            ps[k] = ds[k] * ds[k + 1];
-            pmin = fminf(pmin, ps[k]);
-        }
-        if (pmin <= A.f_bthr) {
-#pragma unroll
-            for (int k = 0; k < kGroup; ++k) {
-                X = xs[k];
-                Z = zs[k];
-                dmin = ds[k];
-                if (ps[k] <= A.f_bthr &&
-                    near_wall(M, A, xs[k + 1], zs[k + 1], ds[k + 1], ps[k], wa[k], wb[k], ei)) {
-                    ei.nocc = n + (uint32_t)(g + k);
-                    return true;
-                }
-                occ.add(material(M, xs[k + 1], zs[k + 1]));
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < kGroup; ++k) occ.add(material(M, xs[k + 1], zs[k + 1]));
-        }
-        X = xs[kGroup];
-        Z = zs[kGroup];
-        dmin = ds[kGroup];
-        return false;
-    }
-
     // PAIRS Philox calls, two Euler steps each, per call of iterate: the
     // per-iteration work of the scheduler loop (constants, vote, branch) is
     // shared by 2 PAIRS steps.  The calls depend only on the step counter, so
@@ -429,10 +376,6 @@ struct WalkerF32 {
             }
             add_cells(M, ci, off, done);
             if (done < NS) return 1;
-        } else if constexpr (kGroup > 1) {
-#pragma unroll
-            for (int g = 0; g < 2 * PAIRS; g += kGroup)
-                if (group(M, A, w, g, ei)) return 1;
         } else {
 #pragma unroll
             for (int q = 0; q < PAIRS; ++q) {

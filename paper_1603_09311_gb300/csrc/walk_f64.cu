@@ -26,6 +26,7 @@ struct WalkerF64 {
     using Real = double;
     static constexpr int KMAX = KMAX_;
     static constexpr bool kCoop = false;  // no cooperative tail: the parity walk stays plain
+    static constexpr bool kGrouped = false;  // one queue (a grouped plan's order is one queue too)
     using Occ = uint32_t;
     using HistT = uint32_t;
     static constexpr int kStored = KMAX - 1;

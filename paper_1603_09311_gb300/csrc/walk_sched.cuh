@@ -68,15 +68,10 @@ __device__ __forceinline__ uint4 philox4x32_10_pre(uint32_t c0, uint32_t c3, uin
 
 // 32 x 32 -> 64-bit product as one wide multiply.
 __device__ __forceinline__ void mul_wide(uint32_t a, uint32_t b, uint32_t &lo, uint32_t &hi) {
-#ifdef SDD_MUL_HILO
-    lo = a * b;
-    hi = __umulhi(a, b);
-#else
     uint64_t p;
     asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(b));
     lo = (uint32_t)p;
     hi = (uint32_t)(p >> 32);
-#endif
 }
 
 // Philox4x32-10 with the ten round keys given (rk0[r] = k0 + r 0x9E3779B9,
@@ -140,6 +135,7 @@ struct WarpState {
     uint32_t disp_next, nid;
     uint32_t head, tail;
     int32_t queue_empty;
+    int32_t home;  // grouped launches: the queue this warp takes items from
 };
 
 // The model's rates [E][K] and boundary constants [E], staged in shared
@@ -190,16 +186,14 @@ struct ExitInfo {
 //   bind(a): shared-memory address of the lane's occupancy histogram
 //   static sample(M, T, A, model, e, x, z, th, wall, mlast, counts) -> double2
 //   static to_abs(M, x, z, ax, az)
+//   kGrouped: takes items from per-model queues (multi-model launches)
 // Launch bounds: at most 256 threads, and at least 3 such CTAs per SM, which
 // leaves up to 85 registers a thread.  24 resident warps whose iterations
 // carry four independent Philox chains keep the issue slots fuller than 32
 // warps squeezed into 64 registers.
-#ifndef SDD_MIN_CTAS
-#define SDD_MIN_CTAS 3
-#endif
 template <class W>
-__global__ void __launch_bounds__(256, SDD_MIN_CTAS) walk_kernel(const __grid_constant__ ModelDev M,
-                                                              const WalkArgs A) {
+__global__ void __launch_bounds__(256, 3) walk_kernel(const __grid_constant__ ModelDev M,
+                                                   const WalkArgs A) {
     using Real = typename W::Real;
     constexpr int KMAX = W::KMAX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -224,6 +218,13 @@ __global__ void __launch_bounds__(256, SDD_MIN_CTAS) walk_kernel(const __grid_co
         S.head = S.tail = 0;
         S.queue_empty = 0;
         S.nx0 = S.nz0 = 0.0;
+        S.home = 0;
+        if (W::kGrouped && A.qbase) {
+            const float x = ((float)blockIdx.x + 0.5f) / (float)gridDim.x;
+            int m = 0;
+            while (m + 1 < A.n_queues && A.home_cut[m + 1] <= x) ++m;
+            S.home = m;
+        }
     }
     __syncthreads();
 
@@ -323,18 +324,47 @@ __global__ void __launch_bounds__(256, SDD_MIN_CTAS) walk_kernel(const __grid_co
     // current one is fully handed out.
     auto refill = [&]() {
         unsigned need = __ballot_sync(kFull, !active);
+        if (A.cancel && need) {
+            // a cancelled request: no more paths; the walks in flight end
+            int c = 0;
+            if (lane == 0) c = *reinterpret_cast<const volatile int32_t *>(A.cancel);
+            if (__shfl_sync(kFull, c, 0)) {
+                if (lane == 0) {
+                    S.queue_empty = 1;
+                    S.disp_rem = 0;
+                }
+                __syncwarp();
+                return;
+            }
+        }
         while (need) {
             if (S.disp_rem == 0) {
                 if (S.queue_empty) break;
-                int q = 0;
-                if (lane == 0) q = atomicAdd(A.queue, 1);
-                q = __shfl_sync(kFull, q, 0);
-                if (q >= A.n_items) {
+                int it = -1;
+                if (lane == 0) {
+                    if (W::kGrouped && A.qbase) {
+                        // the home queue first, then the next ones in turn
+                        int m = S.home;
+                        for (int t = 0; t < A.n_queues; ++t) {
+                            const int q = atomicAdd(A.queue + m, 1);
+                            if (q < A.qbase[m + 1] - A.qbase[m]) {
+                                it = A.order[A.qbase[m] + q];
+                                break;
+                            }
+                            m = m + 1 == A.n_queues ? 0 : m + 1;
+                        }
+                        S.home = m;
+                    } else {
+                        const int q = atomicAdd(A.queue, 1);
+                        if (q < A.n_items) it = A.order ? A.order[q] : q;
+                    }
+                }
+                it = __shfl_sync(kFull, it, 0);
+                if (it < 0) {
                     if (lane == 0) S.queue_empty = 1;
                     __syncwarp();
                     break;
                 }
-                const int it = A.order ? A.order[q] : q;
                 const Item I = A.items[it];
                 if (!dump) {
                     if (lane < M.E) {

@@ -42,6 +42,7 @@ struct WalkerTM {
     static constexpr int KMAX = KMAX_;
     static constexpr bool kF64 = sizeof(Real) == 8;
     static constexpr bool kCoop = false;
+    static constexpr bool kGrouped = false;
     using Occ = Real;  // occupation time of every strip
     using HistT = Real;
     static constexpr int kStored = KMAX;
@@ -379,6 +380,7 @@ struct WalkerTM32 {
     using Real = float;
     static constexpr int KMAX = KMAX_;
     static constexpr bool kCoop = false;
+    static constexpr bool kGrouped = false;
     using Occ = float;
     using HistT = float;
     static constexpr int kStored = KMAX;

@@ -165,6 +165,14 @@ SIGNATURES = [
     ("sdd_reduce_sums_device", ctypes.c_int,
      [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32), ctypes.c_void_p,
       ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("sdd_interface_values_async", ctypes.c_int,
+     [ctypes.c_void_p, P(ctypes.c_double), P(ctypes.c_uint32), ctypes.c_int32, P(ctypes.c_int64),
+      ctypes.c_double, ctypes.c_uint64, P(sdd_config), ctypes.c_void_p, P(ctypes.c_void_p)]),
+    ("sdd_poll", ctypes.c_int, [ctypes.c_void_p]),
+    ("sdd_wait", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    ("sdd_cancel", ctypes.c_int, [ctypes.c_void_p]),
+    ("sdd_request_result", ctypes.c_int, [ctypes.c_void_p, P(ctypes.c_double), P(ctypes.c_double), P(sdd_stats)]),
+    ("sdd_request_free", None, [ctypes.c_void_p]),
     ("sdd_batch_values", ctypes.c_int,
      [P(sdd_batch_entry), ctypes.c_int32, ctypes.c_double, ctypes.c_uint64, P(sdd_config),
       P(sdd_stats)]),
@@ -427,6 +435,64 @@ def sdd_interface_values_noalloc(ctx: Context, d_nodes_ptr: int, n_nodes: int, n
     if st != SDD_OK:
         raise SddError(st, "sdd_interface_values_noalloc")
     return st
+
+
+class Request:
+    """An sdd_request: poll(), wait(timeout_ms), cancel(), result(), free()."""
+
+    def __init__(self, handle, n_nodes, E):
+        self.handle, self.n, self.E = handle, n_nodes, E
+
+    def poll(self) -> int:
+        return lib().sdd_poll(self.handle)
+
+    def wait(self, timeout_ms: int = -1) -> int:
+        return lib().sdd_wait(self.handle, int(timeout_ms))
+
+    def cancel(self) -> int:
+        return lib().sdd_cancel(self.handle)
+
+    def result(self):
+        """(mean complex [n][E], se [n][E][2], stats dict); raises SddError unless
+        the request ended with SDD_OK or SDD_E_TRUNCATED."""
+        mean = np.zeros((self.n, self.E, 2))
+        se = np.zeros((self.n, self.E, 2))
+        st_out = sdd_stats()
+        st = lib().sdd_request_result(self.handle, _dp(mean), _dp(se), ctypes.byref(st_out))
+        if st not in (SDD_OK, SDD_E_TRUNCATED):
+            raise SddError(st, "sdd_request_result")
+        stats = {f: getattr(st_out, f) for f, _ in sdd_stats._fields_}
+        stats["status"] = st
+        return mean[..., 0] + 1j * mean[..., 1], se, stats
+
+    def free(self):
+        if self.handle:
+            lib().sdd_request_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sdd_interface_values_async(ctx: Context, nodes, n_paths, dt: float, seed: int, node_ids=None, stream: int = 0,
+                               config: sdd_config | None = None, **cfg) -> Request:
+    """Queue an evaluation (inputs copied at once); returns a Request."""
+    nodes = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64).reshape(-1, 2))
+    n = nodes.shape[0]
+    npth = _paths(n_paths, n)
+    ids = None if node_ids is None else np.ascontiguousarray(np.asarray(node_ids, dtype=np.uint32))
+    c = config if config is not None else make_config(**cfg)
+    h = ctypes.c_void_p()
+    st = lib().sdd_interface_values_async(
+        ctx.handle, _dp(nodes), None if ids is None else ids.ctypes.data_as(P(ctypes.c_uint32)), n,
+        npth.ctypes.data_as(P(ctypes.c_int64)), float(dt), int(seed) & (2 ** 64 - 1), ctypes.byref(c),
+        ctypes.c_void_p(stream or None), ctypes.byref(h))
+    if st != SDD_OK:
+        raise SddError(st, "sdd_interface_values_async")
+    return Request(h, n, ctx.E)
 
 
 def sdd_range_sums(ctx: Context, nodes, path_begin, path_count, dt: float, seed: int, node_ids=None,

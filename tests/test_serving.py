@@ -141,3 +141,28 @@ def test_cancel_wait_timeout_and_unknown_ids():
     with pytest.raises(sdd.SddError):
         srv.poll(987654)
     srv.close()
+
+
+def test_a_small_request_overtakes_a_large_one_submitted_just_before():
+    # one stream, launches of at most 2^20 walks: a large request (64 nodes x
+    # 1e5 walks, 7 launches) and then a small one (16 nodes x 2000 walks).
+    # Work is queued by virtual deadline (submission time + the phase's own
+    # walk time), so the small request runs right after the large one's first
+    # launch and ends first; queued by submission alone it would end last.
+    rng = np.random.default_rng(21)
+    big, small = I.random_request(rng, 0), I.random_request(rng, 1)
+    big["nodes"] = np.resize(big["nodes"], (64, 2))
+    small["nodes"] = small["nodes"][:16]
+    srv = _server(n_streams=1, max_batch_models=1, max_batch_walks=1 << 20)
+    rb = srv.submit(big["model"], big["nodes"], node_ids=np.arange(64), n_paths=100_000)
+    rs = srv.submit(small["model"], small["nodes"], node_ids=np.arange(16) + 100, n_paths=2000)
+    done = []
+    t0 = time.perf_counter()
+    while len(done) < 2 and time.perf_counter() - t0 < 120:
+        for rid in (rb, rs):
+            if rid not in done and srv.poll(rid):
+                done.append(rid)
+        time.sleep(0.0002)
+    assert done == [rs, rb]
+    assert srv.result(rs)[0] == sdd.SDD_OK and srv.result(rb)[0] == sdd.SDD_OK
+    srv.close()
