@@ -2107,13 +2107,16 @@ int64_t request_bytes(const sdd_server *srv, int32_t n_nodes) {
 }
 
 // Walks a launch gets through per second, for the virtual deadlines below
-// (a scale only: the order of the queue depends on it, not the results).
+// (a scale only: the order of the queue depends on it, not the results), and
+// the most a phase's own walk time adds to its deadline: a large request can
+// only be overtaken by requests submitted less than that after it.
 constexpr double kDeadlineWalksPerS = 5.0e8;
+constexpr double kDeadlineCapS = 1.0;
 
 // Cut a request's current phase into pieces of at most batch_walks walks
 // (whole nodes; nodes with no walks left out) and queue them by the phase's
 // virtual deadline: the request's submission time plus the time its phase's
-// walks would take alone.  A small request (or a pilot phase) then goes ahead
+// walks would take alone, at most kDeadlineCapS.  A small request (or a pilot phase) then goes ahead
 // of a large top-up submitted a little earlier, while a request submitted
 // long before keeps its place; every deadline grows with the submission
 // time, so no request waits forever.  Launches serve the earliest deadline
@@ -2124,7 +2127,7 @@ void srv_queue_phase(sdd_server *srv, SrvRequest *r, Clock::time_point t0) {
     long long phase_walks = 0;
     for (int32_t j = 0; j < n; ++j) phase_walks += r->count[j];
     r->deadline = std::chrono::duration<double>(r->t_submit - t0).count() +
-                  (double)phase_walks / kDeadlineWalksPerS;
+                  std::min((double)phase_walks / kDeadlineWalksPerS, kDeadlineCapS);
     auto at = std::upper_bound(srv->runnable.begin(), srv->runnable.end(), r->deadline,
                                [](double d, const SrvPiece &pc) { return d < pc.r->deadline; });
     std::vector<SrvPiece> add;
