@@ -424,7 +424,10 @@ sdd_status sdd_range_sums(sdd_ctx *ctx, const double *nodes_xz, const uint32_t *
 /* The same with device buffers, queued on stream (cudaStream_t or NULL):
  * d_nodes_xz [n_ranges][2], d_node_ids [n_ranges] (nullable), d_sums
  * [n_ranges][n_eval][4], d_n_valid [n_ranges], d_counters [3] (nullable:
- * steps, walks, truncated walks); path_begin and path_count are host arrays. */
+ * steps, walks, truncated walks); path_begin and path_count are host arrays.
+ * Like sdd_interface_values_device it uses the context's scratch buffers, as
+ * do sdd_reduce_sums and sdd_reduce_sums_device: calls on one context must be
+ * ordered on one stream. */
 sdd_status sdd_range_sums_device(sdd_ctx *ctx, const double *d_nodes_xz, const uint32_t *d_node_ids,
                                  int32_t n_ranges, const int64_t *path_begin,
                                  const int64_t *path_count, double dt, uint64_t seed,
