@@ -515,6 +515,32 @@ def triangle_measure(sdd, torch, dev, peak_tinst, flush, cpu=True):
             "per_dt": per_dt}
 
 
+def small_cases(sdd, objs):
+    """Two launches of a small case of the block and/or triangle workloads
+    through the host-buffer entry point: walk-steps/s of the second."""
+    out = {}
+    if "block" in objs:
+        w = I.workload("block")
+        idx = np.arange(0, 256, 4)
+        ctx = sdd.sdd_create(w["model"])
+        npth = np.maximum(w["n_paths"][idx] // 8, 1000)
+        for k in range(2):
+            _, _, st = sdd.sdd_interface_values(ctx, w["nodes"][idx], npth, w["dt"], w["seed"] + k,
+                                                node_ids=idx.astype(np.uint32))
+        out["block"] = {"steps": st["steps"], "value": st["steps"] / (st["kernel_ms"] * 1e-3),
+                        "workload": "64 of the block workload's nodes (every 4th), 1/8 of their walks"}
+        ctx.close()
+    if "triangle" in objs:
+        t = I.scaled(I.workload("triangle"), n_nodes=16, paths_per_node=100_000)
+        ctx = sdd.sdd_create(t["model"])
+        for k in range(2):
+            _, _, st = sdd.sdd_interface_values(ctx, t["nodes"], t["n_paths"], t["dt"], t["seed"] + k)
+        out["triangle"] = {"steps": st["steps"], "value": st["steps"] / (st["kernel_ms"] * 1e-3),
+                           "workload": "16 of the triangle workload's nodes x 1e5 walks, dt 1e-4"}
+        ctx.close()
+    return out
+
+
 def interp_measure(sdd, reps=3, cpu=True):
     """Interpolation along an interface (Sec. 5): the quarter-space line of 64
     nodes at 1e5 walks per walked node, walks at every 4th node and the last
@@ -1003,6 +1029,11 @@ def main():
             line["block"] = block_measure(sdd, torch, dev, peak_tinst, flush, cpu=cpu)
         if full and "triangle" in objs:
             line["triangle"] = triangle_measure(sdd, torch, dev, peak_tinst, flush, cpu=cpu)
+        if args.small and world == 1 and args.objects != "all":
+            # small cases of the block and triangle programs (for profiler
+            # captures): 64 of the block's nodes with 1/8 of their walks; 16 of
+            # the triangle's nodes x 1e5 walks at dt 1e-4; two launches each
+            line["small_cases"] = small_cases(sdd, objs)
         if args.serve_requests > 0 and full and "serving" in objs:
             line["serving"] = serving(sdd, args.serve_requests)
         if full and "tm" in objs:

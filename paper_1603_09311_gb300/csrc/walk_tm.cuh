@@ -396,6 +396,7 @@ struct WalkerTM32 {
     uint32_t n, hits, run;
     uint32_t nid, path_, pre_x, pre_y;
     float s, wthr, c2, xl, xr, Di;
+    float lc;  // -2 ln(2) D_i dt: squared step length = lc log2(u0)
     bool start_on_if;
     float *h;
 
@@ -412,6 +413,7 @@ struct WalkerTM32 {
         Di = M.fdiff[k];
         const float dtD = Di * (float)A.dt;
         s = sqrtf(dtD);
+        lc = -1.38629436112f * dtD;
         // bands: out of both, p_w and p_g are below 2^-20 each, so no uniform
         // (>= 2^-19) can hit either: 2 d d' / (D dt) > 20 ln 2 (with a margin)
         wthr = 6.94f * 1.001f * dtD;
@@ -632,11 +634,18 @@ struct WalkerTM32 {
 
     // One step: the short path, or 3 when the long one is needed (the step
     // is recorded and left for the end of the iteration).
+    // (w mod 2^23 + 1/2) 2^-23 as the low 23 bits of w in the mantissa of a
+    // float in [1, 2), minus 1 - 2^-24 (exact): the value of uni(w)
+    __device__ __forceinline__ static float uni_m(uint32_t w) {
+        return __uint_as_float((w & 0x007fffffu) | 0x3f800000u) - 0.99999994039535522f;
+    }
     __device__ __forceinline__ int substep(const ModelDev &M, const WalkArgs &A, uint32_t wa, uint32_t wb,
                                            uint32_t k, ExitInfo<float> &ei) {
         float sn, cs;
-        const float r = s * sqrtf(-2.f * __logf(uni(wa)));
-        __sincosf(6.28318530718f * uni(wb), &sn, &cs);
+        // r = sqrt(-2 ln(u0) D_i dt) as sqrt(lc log2(u0)); |.| only guards the
+        // last-ulp sign of lg2 near u0 = 1
+        const float r = sqrtf(fabsf(lc * __log2f(uni_m(wa))));
+        __sincosf(6.28318530718f * uni_m(wb), &sn, &cs);
         const float Xn = fmaf(r, cs, X);
         const float Zn = fmaf(r, sn, Z);
         const float dn = fminf(M.fhw - fabsf(Xn), M.fhh - fabsf(Zn));
