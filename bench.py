@@ -357,7 +357,6 @@ def tm_measure(sdd, torch, dev, peak_tinst, n_steps, cpu=True):
         ms.append(a.elapsed_time(b))
     steps = d_cnt[:n_steps, 0].cpu().numpy().astype(float)
     value = float(steps.sum() / (sum(ms) * 1e-3))
-    ctx.close()
     out = {"metric": METRIC, "value": value, "unit": METRIC, "ms_per_launch": statistics.mean(ms),
            "launches": n_steps, "steps_per_launch": float(steps.mean()),
            "workload": "TM analytic test model: [-1,1]^2, D 1|10 across x=0, kappa -10 (lambda 10i), "
@@ -366,14 +365,12 @@ def tm_measure(sdd, torch, dev, peak_tinst, n_steps, cpu=True):
                         "unit": "Tinst/s", "frac": TM_INST_PER_STEP * value / 1e12 / peak_tinst,
                         "inst_per_step": TM_INST_PER_STEP}}
     if cpu:
-        from oracle import oracle as O
-        idx = np.arange(0, n, 6)
-        t = time.perf_counter()
-        r = O.interface_values(w["model"], w["nodes"][idx], 1000, w["dt"], w["seed"], urule=23)
-        sec = time.perf_counter() - t
-        out["cpu_baseline"] = {"value": r["steps"] / sec, "unit": METRIC, "cores": O.max_threads(),
-                               "kind": "oracle", "sample": f"{len(idx)} of the nodes x 1000 walks "
-                                                           f"({r['steps']:.3e} steps, {sec:.1f} s)"}
+        # the FP32 TM walk against the oracle on the same streams: every 100th
+        # node (25 nodes across the grid) under its own node id, first 2000
+        # walks; the oracle's timing of that sample is the baseline
+        out["fp32_error"], out["cpu_baseline"] = fp32_error(sdd, ctx, w, np.arange(0, n, 100), 2000,
+                                                            w["dt"], w["seed"])
+    ctx.close()
     return out
 
 
@@ -588,6 +585,7 @@ def interp_measure(sdd, reps=3, cpu=True):
                      "interp_launches": int(st["launches"]) - 2,
                      "max_dev_in_se": float(z.max()), "rms_dev_in_se": float(np.sqrt((z ** 2).mean()))}
     out["value"] = out["spline"]["value"]
+    out["fp32_error"] = "the walks at the knots are the main line's kernel and model: its fp32_error"
     out["roofline"] = {"bound": "latency",
                        "note": "the interpolation kernels move a few KB in a few launches of microseconds; "
                                "the walks at the knots are the time, bounded as the main line's kernel"}
@@ -640,6 +638,7 @@ def mt_measure(sdd, reps=3, cpu=True):
            "rel_rho_se_median": float(np.median(r["rho_se"] / r["rho"])),
            "phase_se_median_deg": float(np.degrees(np.median(r["phase_se"]))),
            "rho_site0": [round(float(v), 4) for v in r["rho"][0, :8]],
+           "fp32_error": "the walks at the three points are the block object's kernel and model: its fp32_error",
            "roofline": {"bound": "alu", "note": "the walks of the 15 points (the main line's kernel) are the "
                                                 "time; the resistivity kernel is one launch of microseconds"}}
     if cpu:
@@ -699,6 +698,8 @@ def rbffd_measure(sdd, reps=2, cpu=True):
            "rbffd_ms": 1e3 * t_rb, "knn_kernel_ms": rs["knn_ms"], "weights_kernel_ms": rs["weights_ms"],
            "solve_ms": rs["solve_ms"], "iterations": rs["iterations"], "rel_residual": rs["rel_residual"],
            "ms_per_iteration": rs["solve_ms"] / max(rs["iterations"], 1),
+           "fp32_error": "the boundary walks are the main line's kernel and model: its fp32_error; "
+                         "the RBF-FD stage is FP64",
            "roofline": {"bound": "latency",
                         "note": "a BiCGStab iteration is 5 launches (replayed 8 iterations at a time as a "
                                 "CUDA graph) over vectors of 32k complex values (a few MB, L2-resident); the "
