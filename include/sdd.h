@@ -30,7 +30,8 @@
  *    Sec. 4.2): sdd_apparent_resistivity;
  *  - the RBF-FD sub-domain solve that completes the decomposition
  *    (Sec. 3.2): sdd_rbffd_weights, sdd_rbffd_solve;
- *  - batched, graph, allocation-free and served launches of the walk;
+ *  - batched, graph, allocation-free, asynchronous and served launches of
+ *    the walk;
  *  - raw sums of path ranges and their fixed-order reduction, for an
  *    evaluation split across processes (sdd_range_sums, sdd_reduce_sums).
  *
