@@ -376,9 +376,11 @@ sdd_status sdd_interface_values_noalloc(sdd_ctx *ctx, const double *d_nodes_xz,
  *                 the request is still running then, else as sdd_poll.
  *   sdd_cancel    stops handing out walks: the walks already started end,
  *                 the rest are skipped, and the request ends with
- *                 SDD_E_CANCELLED (outputs undefined).  A cancel that reaches
- *                 the GPU before the walks start leaves them to run, and the
- *                 request still ends cancelled.  Returns at once.
+ *                 SDD_E_CANCELLED (outputs undefined).  A request cancelled
+ *                 while it still waits behind earlier work on its stream
+ *                 keeps the cancel: it ends once the walks its warps take
+ *                 before the flag arrives (one per lane at most) have ended.
+ *                 Returns at once.
  *   sdd_request_result  copies mean [n_nodes][n_eval][2] and se (as
  *                 sdd_interface_values) and stats (nullable) once the request
  *                 has ended with SDD_OK or SDD_E_TRUNCATED; otherwise returns

@@ -1516,6 +1516,7 @@ struct sdd_request {
     cudaStream_t stream = nullptr;  // the caller's, or own_stream
     cudaStream_t own_stream = nullptr, cancel_stream = nullptr;
     cudaEvent_t done = nullptr, ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t armed = nullptr;  // after the memset that clears the cancel flag
     unsigned char *dev = nullptr, *host = nullptr;
     size_t off_mean = 0, off_se = 0, off_cnt = 0, off_flag = 0, off_cancel = 0;
     Launch L{};
@@ -1538,6 +1539,7 @@ void request_release(sdd_request *r) {
     if (r->done) cudaEventDestroy(r->done);
     if (r->ev0) cudaEventDestroy(r->ev0);
     if (r->ev1) cudaEventDestroy(r->ev1);
+    if (r->armed) cudaEventDestroy(r->armed);
     if (r->own_stream) cudaStreamDestroy(r->own_stream);
     if (r->cancel_stream) cudaStreamDestroy(r->cancel_stream);
     delete r;
@@ -1598,6 +1600,7 @@ extern "C" sdd_status sdd_interface_values_async(sdd_ctx *ctx, const double *nod
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev1);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->armed, cudaEventDisableTiming);
     if (e == cudaSuccess && !stream) e = cudaStreamCreateWithFlags(&r->own_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         request_release(r);
@@ -1622,6 +1625,8 @@ extern "C" sdd_status sdd_interface_values_async(sdd_ctx *ctx, const double *nod
     if (ni > 0) {
         q(cudaMemsetAsync(r->dev + o_queue, 0, 32, s), "request queue");
         q(cudaMemsetAsync(r->dev + o_cnt, 0, 32, s), "request counters");
+        // a cancel copy waits for this point, so the memset cannot clear it
+        q(cudaEventRecord(r->armed, s), "event");
         WalkArgs A = base_args(ctx, L, dt, seed);
         A.nodes = reinterpret_cast<const double *>(r->dev + o_nodes);
         A.node_ids = node_ids ? reinterpret_cast<const uint32_t *>(r->dev + o_ids) : nullptr;
@@ -1699,6 +1704,9 @@ extern "C" sdd_status sdd_cancel(sdd_request *r) {
     if (r->n_items == 0) return SDD_OK;
     cudaError_t e = cudaSuccess;
     if (!r->cancel_stream) e = cudaStreamCreateWithFlags(&r->cancel_stream, cudaStreamNonBlocking);
+    // after the request's queue memset (which also clears the flag), even
+    // while the request still waits behind earlier work on its stream
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(r->cancel_stream, r->armed, 0);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(r->dev + r->off_flag, r->host + r->off_cancel, sizeof(int32_t), cudaMemcpyHostToDevice,
                             r->cancel_stream);

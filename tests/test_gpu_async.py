@@ -121,6 +121,31 @@ def test_poll_timeout_and_cancel():
     assert t_cancel < 0.5 * t_full, (t_cancel, t_full)
 
 
+def test_a_cancel_made_while_queued_behind_another_request_is_kept():
+    # request b waits on the stream behind a (64 nodes x 2e6 walks, about a
+    # second); b is cancelled before its queue memset has run, then a.  The
+    # cancel of b must survive that memset: b's warps take at most one walk
+    # per lane before the flag arrives, so b ends right after a instead of
+    # running its own second of walks
+    torch = pytest.importorskip("torch")
+    w = I.workload("quarterspace")
+    npth = np.full(64, 2_000_000, dtype=np.int64)
+    ctx = sdd.sdd_create(w["model"])
+    s = torch.cuda.Stream()
+    a = sdd.sdd_interface_values_async(ctx, w["nodes"], npth, w["dt"], 3, stream=s.cuda_stream)
+    b = sdd.sdd_interface_values_async(ctx, w["nodes"], npth, w["dt"], 4, stream=s.cuda_stream)
+    assert b.cancel() == sdd.SDD_OK
+    time.sleep(0.05)
+    assert a.cancel() == sdd.SDD_OK
+    assert a.wait() == sdd.SDD_E_CANCELLED
+    t0 = time.perf_counter()
+    assert b.wait() == sdd.SDD_E_CANCELLED
+    t_b = time.perf_counter() - t0
+    a.free()
+    b.free()
+    assert t_b < 0.1, t_b
+
+
 def test_async_arguments():
     w = I.scaled(I.workload("quarterspace"), n_nodes=2, paths_per_node=100, dt=1e-3)
     ctx = sdd.sdd_create(w["model"])
