@@ -370,11 +370,11 @@ struct WalkerTM {
 // A step takes the short path unless its wall product d d' or its product
 // of distances to the strip's bounds comes within reach of a hit (or the
 // step crossed a bound); the long path decides exactly as WalkerTM does.  A
-// lane whose step needs the long path stops for the rest of the iteration;
-// the long path and the interface randomisation then run once for all such
-// lanes of the warp.  Whole steps in the current strip are counted in a
-// register and added to the lane's occupation times when the strip changes
-// or the walk ends.
+// lane whose step needs the long path records that step; the steps it still
+// runs in the iteration are discarded.  The long path and the interface
+// randomisation then run once for all such lanes of the warp.  Whole steps in
+// the current strip are counted in a register and added to the lane's
+// occupation times when the strip changes or the walk ends.
 template <int KMAX_>
 struct WalkerTM32 {
     using Real = float;
@@ -385,10 +385,11 @@ struct WalkerTM32 {
     using HistT = float;
     static constexpr int kStored = KMAX;
     static constexpr int kHist = KMAX;
-    // four Philox calls (8 steps) per iteration: the per-step code is the
-    // short path only (the long path and the events run once per iteration),
-    // so the iteration fits the instruction cache (measured: 1, 2, 4 calls ->
-    // 1.26e11, 1.50e11, 1.64e11 walk-steps/s on the analytic test model)
+    // four Philox calls (8 steps) per round of an iteration: the per-step
+    // code is the short path only (the long path and the events run once per
+    // iteration), so the loop fits the instruction cache (measured with one
+    // round: 1, 2, 4 calls -> 1.26e11, 1.50e11, 1.64e11 walk-steps/s on the
+    // analytic test model)
     static constexpr int PAIRS = 4;
 
     float X, Z, dmin, dI;
@@ -473,11 +474,11 @@ struct WalkerTM32 {
         ei.aux = hits;
     }
 
-    // A step that needs the long path (its proposed point and Philox words),
-    // and a step that hit an interface (hit fraction, interface, side beyond
-    // it).  Both wait until the end of the iteration, where every lane of the
+    // A step that needs the long path (the position before it, its proposed
+    // point and Philox words), and a step that hit an interface (hit
+    // fraction, interface, side beyond it).  Both wait until the end of the iteration, where every lane of the
     // warp that has one runs it together: the per-step code stays short.
-    float pXn, pZn, pth, pxg;
+    float pX, pZ, pXn, pZn, pth, pxg;
     uint32_t pwa, pwb;
     int pside;
 
@@ -521,7 +522,7 @@ struct WalkerTM32 {
         const float U = bridge_u(wa, wb);
         const float pw = best <= 40.f ? __expf(-best) : 0.f;
         if (U <= pw) {
-            place(M, Xn, Zn, best / -logf(U), bw, nk, ei);
+            place(M, Xn, Zn, best / -__logf(U), bw, nk, ei);
             return 1;
         }
         const int j = strip(M, Xn);
@@ -558,7 +559,7 @@ struct WalkerTM32 {
                 flush();
                 pXn = Xn;
                 pZn = Zn;
-                pth = bq / -logf((U - pw) / (1.f - pw));
+                pth = bq / -__logf((U - pw) / (1.f - pw));
                 pside = bs;
                 pxg = bx;
                 return 2;
@@ -576,7 +577,9 @@ struct WalkerTM32 {
     // disc point, time split).  Returns true when the resampled point left
     // the domain (the walk ends on the nearest wall).
     __device__ __forceinline__ bool event(const ModelDev &M, const WalkArgs &A, uint32_t nk, ExitInfo<float> &ei) {
-        const uint4 v = philox_rk(make_uint4(nk, path_, nid, 2u), A.rk0, A.rk1);
+        // counter (nk, path, node id, 2): words 1 and 2 are the walk's, so the
+        // first round's product of word 2 is the precomputed one of the steps
+        const uint4 v = philox_rk_pre(nk, 2u, pre_x, pre_y, A.rk0, A.rk1);
         const float Dj = M.fdiff[pside];
         const float pi_ = Di / (Di + Dj), pj = Dj / (Di + Dj);
         const float zg = Z + pth * (pZn - Z);
@@ -632,15 +635,22 @@ struct WalkerTM32 {
         exit_at(M, ei, ex, ez, th, w, nk);
     }
 
-    // One step: the short path, or 3 when the long one is needed (the step
-    // is recorded and left for the end of the iteration).
     // (w mod 2^23 + 1/2) 2^-23 as the low 23 bits of w in the mantissa of a
     // float in [1, 2), minus 1 - 2^-24 (exact): the value of uni(w)
     __device__ __forceinline__ static float uni_m(uint32_t w) {
         return __uint_as_float((w & 0x007fffffu) | 0x3f800000u) - 0.99999994039535522f;
     }
-    __device__ __forceinline__ int substep(const ModelDev &M, const WalkArgs &A, uint32_t wa, uint32_t wb,
-                                           uint32_t k, ExitInfo<float> &ei) {
+    // One step of the short path, taken by every lane of the warp together
+    // and always committed: the position moves to beta' whatever the lane's
+    // state, so the unrolled steps need no branch around them and no copies
+    // of the state.  The lane's first step that needs the long path (stop < 0
+    // so far; not a skipped step, live false) records itself: its index k,
+    // the position before it, its proposed point and its Philox words.  The
+    // steps after it only move a position that iterate() then replaces by
+    // the recorded one.  first: the walk's step 0 from a start on an
+    // interface (a hit at t = 0).
+    __device__ __forceinline__ void step(const ModelDev &M, const WalkArgs &A, uint32_t wa, uint32_t wb, int k,
+                                         bool live, bool first, int &stop) {
         float sn, cs;
         // r = sqrt(-2 ln(u0) D_i dt) as sqrt(lc log2(u0)); |.| only guards the
         // last-ulp sign of lg2 near u0 = 1
@@ -651,51 +661,83 @@ struct WalkerTM32 {
         const float dn = fminf(M.fhw - fabsf(Xn), M.fhh - fabsf(Zn));
         const float dIn = fminf(Xn - xl, xr - Xn);
         const float pn = dmin * dn, pI = dI * dIn;
-        const bool first = n + k == 0 && start_on_if;
         if (pn <= wthr || pI <= wthr || first) {
             // exact reject: every wall product is >= pn and every bound's
             // product >= pI, so p_w + p_g <= exp(-c2 pn) + exp(-c2 pI)
-            if (first || bridge_u(wa, wb) <= __expf(-c2 * pn) + __expf(-c2 * pI)) {
+            if (stop < 0 && live && (first || bridge_u(wa, wb) <= __expf(-c2 * pn) + __expf(-c2 * pI))) {
+                stop = k;
+                pX = X;
+                pZ = Z;
                 pXn = Xn;
                 pZn = Zn;
                 pwa = wa;
                 pwb = wb;
-                return 3;
             }
         }
-        run += 1;
-        X = Xn;
-        Z = Zn;
-        dmin = dn;
-        dI = dIn;
-        return 0;
+        X = live ? Xn : X;
+        Z = live ? Zn : Z;
+        dmin = live ? dn : dmin;
+        dI = live ? dIn : dI;
     }
 
-    // The steps of PAIRS Philox calls (fewer at max_steps), a lane stopping at
-    // its first step that needs the long path; then the long path and the
-    // interface events of the warp's lanes, once.  0 running, 1 exited,
-    // 2 truncated.
+    // The steps of ROUNDS x PAIRS Philox calls, up to the lane's first step
+    // that needs the long path; then the long path and the interface events
+    // of the warp's lanes, once.  The rounds share the code of one (a loop,
+    // not unrolled); more steps per long-path pass let more of the warp's
+    // lanes have an event to resolve in it (measured on the analytic test
+    // model with committed steps: 2, 4, 8 rounds -> 2.10, 2.25, 2.18e11
+    // walk-steps/s; with the earlier layout, whose steps were each guarded
+    // by the lane's state, 1, 2, 4 rounds -> 1.67, 1.79, 1.86e11).  A walk
+    // within one iteration of max_steps takes its steps one at a time.
+    // 0 running, 1 exited, 2 truncated.
+    static constexpr int ROUNDS = 4;
     __device__ __forceinline__ int iterate(const ModelDev &M, const WalkArgs &A, uint32_t, ExitInfo<float> &ei) {
-        uint4 w[PAIRS];
-#pragma unroll
-        for (int q = 0; q < PAIRS; ++q) w[q] = philox_rk_pre((n >> 1) + q, 0u, pre_x, pre_y, A.rk0, A.rk1);
         const uint32_t odd = n & 1u;
-        const uint32_t lim = min((uint32_t)(2 * PAIRS) - odd, A.max_steps - n);
-        int st = 0;
-        uint32_t done = 0;
+        const uint32_t full = 2u * PAIRS * ROUNDS - odd;
+        const bool first0 = n == 0 && start_on_if;
+        int stop = -1;
+        uint32_t done;
+        if (A.max_steps - n >= full) {
+#pragma unroll 1
+            for (int r = 0; r < ROUNDS; ++r) {
+                uint4 w[PAIRS];
 #pragma unroll
-        for (int q = 0; q < PAIRS; ++q) {
+                for (int q = 0; q < PAIRS; ++q)
+                    w[q] = philox_rk_pre((n >> 1) + PAIRS * r + q, 0u, pre_x, pre_y, A.rk0, A.rk1);
+                // k = steps of this walk since n; for an odd n the first word
+                // pair of round 0 belongs to step n - 1 and is skipped
+                const int kb = 2 * PAIRS * r - (int)odd;
 #pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-                if (q == 0 && hh == 0 && odd) continue;
-                const uint32_t k = 2u * q + hh - odd;
-                if (st == 0 && k < lim) {
-                    st = substep(M, A, hh ? w[q].z : w[q].x, hh ? w[q].w : w[q].y, k, ei);
-                    done = k + 1;
+                for (int q = 0; q < PAIRS; ++q) {
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const bool lead = q == 0 && hh == 0;
+                        step(M, A, hh ? w[q].z : w[q].x, hh ? w[q].w : w[q].y, kb + 2 * q + hh,
+                             lead ? (r != 0 || odd == 0u) : true, lead && r == 0 && first0, stop);
+                    }
                 }
             }
+            done = stop >= 0 ? (uint32_t)stop + 1u : full;
+        } else {
+            const uint32_t lim = A.max_steps - n;
+            for (uint32_t k = 0; k < lim && stop < 0; ++k) {
+                const uint32_t sk = n + k;
+                const uint4 w = philox_rk_pre(sk >> 1, 0u, pre_x, pre_y, A.rk0, A.rk1);
+                step(M, A, (sk & 1u) ? w.z : w.x, (sk & 1u) ? w.w : w.y, (int)k, true, k == 0 && first0, stop);
+            }
+            done = stop >= 0 ? (uint32_t)stop + 1u : lim;
         }
-        if (st == 3) st = rare(M, A, pXn, pZn, pwa, pwb, done - 1, ei);
+        int st = 0;
+        if (stop >= 0) {
+            // back to the position before the recorded step; the steps before
+            // it were spent in the current strip
+            X = pX;
+            Z = pZ;
+            run += (uint32_t)stop;
+            st = rare(M, A, pXn, pZn, pwa, pwb, (uint32_t)stop, ei);
+        } else {
+            run += done;
+        }
         if (st == 1) return 1;
         if (st == 2 && event(M, A, n + done - 1, ei)) return 1;
         n += done;
