@@ -44,21 +44,22 @@ METRIC = "walk-steps/s"
 # on the quarter-space model: half a Philox4x32-10
 # call with the first round's fixed product precomputed (19.5), two uniforms
 # from bit masks (3), Box-Muller (7), Euler update (2), wall distances and the
-# bridge filter (5), the vertical-contact material test (4), two occupation
-# power sums (2), step bookkeeping (2.5).
-INST_PER_STEP = 45
+# bridge filter (5), the vertical-contact test as two compares (earth side,
+# right of the contact) and one predicated add to each region counter (4),
+# step bookkeeping (2.5).
+INST_PER_STEP = 43
 # The same count for a step of the TM walk (strips of their own diffusion):
-# the TE step without the material test and the occupation power sums
-# (45 - 4 - 2), plus the interface tests (crossing compares 2, nearer
-# interface product and filter 4) and the occupation update in shared memory
-# (address and add, 2).
+# the TE step without its material test and counters (43 - 4), plus the
+# interface tests (crossing compares 2, nearer interface product and filter
+# 4) and the occupation update in shared memory (address and add, 2).
 TM_INST_PER_STEP = 47
 # The same count for the other lookup programs of the single-precision walk
-# (the contact test's 4 replaced): one rectangle in the layered half-space
-# (earth test and select 2, four compares and a select 5): 48; one triangle
-# (earth test and select 2, three edge functions of two FMAs and a compare 9,
-# a select 1): 53.
-RECT_INST_PER_STEP = 48
+# (the contact test's 4 replaced): one rectangle on one side of the surface
+# (earth compare 1, four compares 4, two predicated region adds 2): 46; one
+# triangle, counted by material (earth test and select 2, three edge
+# functions of two FMAs and a compare 9, a select 1, two occupation power
+# sums 2): 53.
+RECT_INST_PER_STEP = 46
 TRI_INST_PER_STEP = 53
 # Walks per node of the double-precision leg of the triangle sweep.
 FP64_WALKS = 50_000

@@ -300,12 +300,21 @@ void build_model(const sdd_model_desc *m, ModelDev &M) {
         else if (m->n_shapes == 1) M.gcode = m->shapes[0].kind == SDD_SHAPE_RECT ? GC_RECT1 : GC_TRI1;
         else if (m->n_shapes <= 4) M.gcode = GC_SHAPES4;
         else M.gcode = GC_SHAPES16;
+        M.shape_air = 0;
         if (M.gcode == GC_RECT1) {
             // a vertical contact: the rectangle is the whole earth right of x0
             const sdd_shape &S = m->shapes[0];
             if (S.v[1] >= d.x_max && S.v[2] == 0.0 && S.v[3] >= d.z_max &&
-                (float)(S.v[1] - M.xc) >= M.fhw && (float)(S.v[3] - M.zc) >= M.fhh)
+                (float)(S.v[1] - M.xc) >= M.fhw && (float)(S.v[3] - M.zc) >= M.fhh) {
                 M.gcode = GC_CONTACT;
+            } else if (M.shapes[0].f[2] >= M.fzs) {
+                // every point the single-precision test puts inside has
+                // Z >= f[2] >= fzs: the rectangle is in the earth
+            } else if (M.shapes[0].f[3] <= M.fzs) {
+                M.shape_air = 1;  // Z < f[3] <= fzs: in the air
+            } else {
+                M.gcode = GC_SHAPES4;  // straddles the surface
+            }
         }
     } else {
         M.gcode = GC_RASTER;

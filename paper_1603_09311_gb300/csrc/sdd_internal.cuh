@@ -28,6 +28,10 @@ enum Geo : int { GEO_SHAPES = 0, GEO_RASTER = 1, GEO_TM = 2 };
 // GC_CONTACT is one rectangle [x0, >= x_max) x [0, >= z_max): the earth split
 // by a vertical contact at x0 (the quarter-space model), tested with two
 // compares; it takes the same decisions as GC_RECT1 on every inside point.
+// GC_RECT1 is one rectangle wholly on one side of the surface z = 0.  These
+// two programs count steps by region (earth side, inside the shape) rather
+// than by material, and turn the region counts into material counts at the
+// walk's exit.
 // GC_RASTER_MULTI serves a batch of raster models sharing the domain and the
 // raster size: each lane reads the raster of its walk's model.  GC_TM is the
 // TM walk over vertical strips (its own walker).
@@ -118,6 +122,10 @@ struct ModelDev {
     float fsx, fsz;  // raster cells per unit length
     float fox, foz;  // hw * sx - 1/2 + kTile, hh * sz - 1/2 + kTile: round(X sx + ox) is the
                      // cell index plus kTile (the tile map's margin)
+    // GC_RECT1 / GC_CONTACT: 1 when the one shape lies wholly in the air
+    // (z < 0), 0 when wholly in the earth; a shape that straddles the
+    // surface is served by GC_SHAPES4 instead
+    int32_t shape_air;
     // TM mode: material m is the vertical strip [xif[m-1], xif[m]) with
     // diffusion diff[m]
     int32_t tm;

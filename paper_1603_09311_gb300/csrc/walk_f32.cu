@@ -18,6 +18,8 @@
 // distance to the nearer wall of each pair is h - |X|.  Two steps share one
 // Philox call (words 0,1 for the even step, 2,3 for the odd one), and one
 // call of iterate() runs 8 steps (4 with 8 materials).
+#include <type_traits>
+
 #include "walk_sched.cuh"
 #include "walk_tm.cuh"
 
@@ -105,6 +107,16 @@ struct Occupancy<8> {
     }
 };
 
+// Region counters of the one-shape programs (GC_CONTACT, GC_RECT1): ce steps
+// on the earth side of the surface, cs steps inside the shape.  The shape
+// lies wholly on one side of the surface, so these two give every
+// material's count at the exit (WalkerF32::counts).
+struct Regions {
+    uint32_t ce, cs;
+    __device__ __forceinline__ void bind(uint32_t) {}
+    __device__ __forceinline__ void clear() { ce = 0u; cs = 0u; }
+};
+
 // GC: the material-lookup program (GeoCode).  Shape parameters are read
 // with compile-time indices, so every one is an immediate constant operand.
 template <int KMAX_, int GC>
@@ -118,9 +130,13 @@ struct WalkerF32 {
     static constexpr int kHist = KMAX == 8 ? 8 : 1;
     static constexpr bool kGrouped = GC == GC_RASTER_MULTI;
 
+    // one-shape programs count regions (two predicated adds per step in
+    // place of the material selects and the power sums)
+    static constexpr bool kRegions = GC == GC_CONTACT || GC == GC_RECT1;
+
     float X, Z, dmin;  // centred position, distance to the nearest wall
     uint32_t n;        // Euler steps accepted (even at the start of iterate)
-    Occupancy<KMAX> occ;
+    typename std::conditional<kRegions, Regions, Occupancy<KMAX>>::type occ;
     uint32_t nid, pre_x, pre_y;
     const uint32_t *tco;  // GC_RASTER_MULTI: the tile map of this walk's model
 
@@ -169,7 +185,50 @@ struct WalkerF32 {
         return r;
     }
 
-    __device__ __forceinline__ void counts(uint32_t *c) const { occ.counts(c); }
+    // The step at (X, Z) into the region counters: the earth test and the
+    // shape test of material() as predicates, each adding one to its counter
+    // (compares with .ftz, as the unit's float compares).
+    __device__ __forceinline__ void count_regions(const ModelDev &M, float X, float Z) {
+        if (GC == GC_CONTACT) {
+            asm("{\n\t.reg .pred pe, ps;\n\t"
+                "setp.ge.ftz.f32 pe, %3, %4;\n\t"
+                "setp.ge.and.ftz.f32 ps, %2, %5, pe;\n\t"
+                "@pe add.u32 %0, %0, 1;\n\t"
+                "@ps add.u32 %1, %1, 1;\n\t}"
+                : "+r"(occ.ce), "+r"(occ.cs)
+                : "f"(X), "f"(Z), "f"(M.fzs), "f"(M.shapes[0].f[0]));
+        } else {
+            asm("{\n\t.reg .pred pe, ps;\n\t"
+                "setp.ge.ftz.f32 pe, %3, %4;\n\t"
+                "setp.ge.ftz.f32 ps, %2, %5;\n\t"
+                "setp.lt.and.ftz.f32 ps, %2, %6, ps;\n\t"
+                "setp.ge.and.ftz.f32 ps, %3, %7, ps;\n\t"
+                "setp.lt.and.ftz.f32 ps, %3, %8, ps;\n\t"
+                "@pe add.u32 %0, %0, 1;\n\t"
+                "@ps add.u32 %1, %1, 1;\n\t}"
+                : "+r"(occ.ce), "+r"(occ.cs)
+                : "f"(X), "f"(Z), "f"(M.fzs), "f"(M.shapes[0].f[0]), "f"(M.shapes[0].f[1]),
+                  "f"(M.shapes[0].f[2]), "f"(M.shapes[0].f[3]));
+        }
+    }
+
+    // Counts of materials 1 .. KMAX-1 after nocc counted steps.  Region
+    // counters: the shape has cs; with the shape in the earth the earth
+    // background has ce - cs and the air nocc - ce, with the shape in the air
+    // the earth has ce and the air nocc - ce - cs.
+    __device__ __forceinline__ void counts(const ModelDev &M, uint32_t nocc, uint32_t *c) const {
+        if constexpr (kRegions) {
+            const uint32_t ce = occ.ce, cs = occ.cs;
+            const uint32_t ear = M.shape_air ? ce : ce - cs;
+            const uint32_t air = nocc - ce - (M.shape_air ? cs : 0u);
+            const int ma = M.bg_air, me = M.bg_earth, msh = M.shapes[0].mat;
+#pragma unroll
+            for (int j = 1; j < KMAX; ++j)
+                c[j - 1] = (ma == j ? air : 0u) + (me == j ? ear : 0u) + (msh == j ? cs : 0u);
+        } else {
+            occ.counts(c);
+        }
+    }
     __device__ __forceinline__ void bind(HistT *h) { occ.bind((uint32_t)__cvta_generic_to_shared(h)); }
 
     __device__ __forceinline__ void start(const ModelDev &M, const WalkArgs &A, double x0,
@@ -273,7 +332,8 @@ struct WalkerF32 {
                 return true;
             }
         }
-        occ.add(material(M, Xn, Zn));
+        if constexpr (kRegions) count_regions(M, Xn, Zn);
+        else occ.add(material(M, Xn, Zn));
         X = Xn;
         Z = Zn;
         dmin = dn;

@@ -71,7 +71,7 @@ struct WalkerF64 {
 
     __device__ __forceinline__ void bind(HistT *) {}
 
-    __device__ __forceinline__ void counts(uint32_t *c) const {
+    __device__ __forceinline__ void counts(const ModelDev &, uint32_t, uint32_t *c) const {
 #pragma unroll
         for (int j = 0; j < (KMAX > 1 ? KMAX - 1 : 1); ++j) c[j] = cnt[j];
     }

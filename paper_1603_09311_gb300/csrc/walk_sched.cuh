@@ -182,7 +182,8 @@ struct ExitInfo {
 //   start(M, A, x0, z0, path, node_id, model)  -- begin a walk
 //   iterate(M, A, path, ExitInfo&) -> 0 running, 1 exited, 2 truncated
 //     (a few Euler steps per call; max_steps is a multiple of them)
-//   counts(c): steps spent in materials 1..KMAX-1 (at the exit)
+//   counts(M, nocc, c): steps spent in materials 1..KMAX-1 (at the exit,
+//     after nocc occupation steps)
 //   bind(a): shared-memory address of the lane's occupancy histogram
 //   static sample(M, T, A, model, e, x, z, th, wall, mlast, counts) -> double2
 //   static to_abs(M, x, z, ax, az)
@@ -428,7 +429,7 @@ __global__ void __launch_bounds__(256, 3) walk_kernel(const __grid_constant__ Mo
             R.path[slot] = path;
             R.aux[slot] = ei.aux;
             typename W::Occ c[W::kStored];
-            w.counts(c);
+            w.counts(M, ei.nocc, c);
 #pragma unroll
             for (int j = 0; j < W::kStored; ++j) R.cnt[j][slot] = c[j];
             S.steps[lane] += (unsigned long long)ei.nocc + (tr ? 0ull : 1ull);

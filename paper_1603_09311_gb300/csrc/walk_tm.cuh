@@ -87,7 +87,7 @@ struct WalkerTM {
         for (int k = 0; k < KMAX; ++k) h[32 * k] = Real(0);
     }
 
-    __device__ __forceinline__ void counts(Occ *c) const {
+    __device__ __forceinline__ void counts(const ModelDev &, uint32_t, Occ *c) const {
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) c[k] = h[32 * k];
     }
@@ -449,7 +449,7 @@ struct WalkerTM32 {
         for (int k2 = 0; k2 < KMAX; ++k2) h[32 * k2] = 0.f;
     }
 
-    __device__ __forceinline__ void counts(Occ *c) const {
+    __device__ __forceinline__ void counts(const ModelDev &, uint32_t, Occ *c) const {
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) c[k] = h[32 * k];
     }

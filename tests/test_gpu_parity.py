@@ -58,8 +58,18 @@ def _many_materials():
     return {"domain": I.DOMAIN, "kappa": kap, "bg": (0, 1), "shapes": shapes, "g": ("columns", 1, 1)}
 
 
+def _one_rect(rect):
+    # one rectangle of material 2 (rate 20) in the layered half-space
+    return {"domain": I.DOMAIN, "kappa": [[0.0, 2.0, 20.0]], "bg": (0, 1),
+            "shapes": [(0, 2, tuple(rect) + (0.0, 0.0))], "g": ("columns", 1, 1)}
+
+
 MODELS = {
     "halfspace": (I.halfspace(2.0), (0.3, 0.25)),
+    # one rectangle wholly in the air, and one across the surface (the
+    # single-rectangle program counts regions only for a shape on one side)
+    "rect_air": (_one_rect((-0.3, 0.3, -0.4, -0.1)), (0.0, -0.05)),
+    "rect_straddle": (_one_rect((-0.2, 0.3, -0.2, 0.3)), (0.0, 0.1)),
     "quarterspace": (I.quarterspace(2.0, 20.0), (0.0, 0.5)),
     "block16": (I.block_batched(), (0.2, 0.35)),
     "triangle": (I.triangle(), (0.05, 0.4)),
@@ -144,9 +154,13 @@ def test_fp32_independent_seeds_agree_with_oracle(name):
     assert _fp32_close(mean, se, ref["mean"], ref["se"])
 
 
-@pytest.mark.parametrize("dt", [1e-3, 1e-4])
-def test_fp32_walks_follow_the_oracle_streams(dt):
-    model, (x0, z0) = MODELS["quarterspace"]
+@pytest.mark.parametrize("name,dt", [("quarterspace", 1e-3), ("quarterspace", 1e-4), ("block16", 1e-3),
+                                     ("rect_air", 1e-3), ("rect_straddle", 1e-3), ("triangle", 1e-3)])
+def test_fp32_walks_follow_the_oracle_streams(name, dt):
+    # walk by walk: the FP32 walk takes the oracle's steps, wall and
+    # per-material counts (the one-shape programs count regions and derive
+    # the material counts at the exit)
+    model, (x0, z0) = MODELS[name]
     ctx = sdd.sdd_create(model)
     n = 4000 if dt == 1e-3 else 1000
     g = sdd.sdd_walk_records(ctx, x0, z0, 3, 0, n, dt, 77)
