@@ -56,11 +56,10 @@ TM_INST_PER_STEP = 47
 # The same count for the other lookup programs of the single-precision walk
 # (the contact test's 4 replaced): one rectangle on one side of the surface
 # (earth compare 1, four compares 4, two predicated region adds 2): 46; one
-# triangle, counted by material (earth test and select 2, three edge
-# functions of two FMAs and a compare 9, a select 1, two occupation power
-# sums 2): 53.
+# triangle on one side of the surface (earth compare 1, three edge functions
+# of two FMAs and a compare 9, two predicated region adds 2): 51.
 RECT_INST_PER_STEP = 46
-TRI_INST_PER_STEP = 53
+TRI_INST_PER_STEP = 51
 # Walks per node of the double-precision leg of the triangle sweep.
 FP64_WALKS = 50_000
 

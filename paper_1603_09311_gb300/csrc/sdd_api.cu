@@ -232,6 +232,40 @@ sdd_status check_model(const sdd_model_desc *m) {
     return SDD_OK;
 }
 
+// Side of the surface on which a triangle's single-precision test can
+// accept a point: 0 the earth (every accepted point has Z >= fzs), 1 the air
+// (every accepted point has Z < fzs), -1 neither or not decided.  The test
+// is three edge functions fmaf(A, X, fmaf(B, Z, C)) >= 0 with float
+// coefficients over points of the domain (|X| <= hw, |Z| <= hh); each is
+// within 2^-23 (|A| hw + |B| hh + |C|) of its exact value, so an accepted
+// point lies in the triangle whose edges are moved out by that bound
+// (taken 8 times larger here).  That triangle's vertices decide.
+static int triangle_side(const sdd::ShapeDev &S, float hw, float hh, float fzs) {
+    double a[3], b[3], c[3];
+    for (int e = 0; e < 3; ++e) {
+        a[e] = S.f[3 * e];
+        b[e] = S.f[3 * e + 1];
+        c[e] = S.f[3 * e + 2];
+        const double eps = std::ldexp(1.0, -20) * (std::fabs(a[e]) * hw + std::fabs(b[e]) * hh + std::fabs(c[e]));
+        c[e] += eps;
+    }
+    double zmin = 1e300, zmax = -1e300;
+    for (int e = 0; e < 3; ++e) {
+        const int f = (e + 1) % 3;
+        const double det = a[e] * b[f] - a[f] * b[e];
+        if (!(std::fabs(det) > 1e-12 * (std::fabs(a[e] * b[f]) + std::fabs(a[f] * b[e]))) || det == 0.0)
+            return -1;
+        // a x + b z = -c for edges e and f
+        const double z = (-a[e] * c[f] + a[f] * c[e]) / det;
+        zmin = std::min(zmin, z);
+        zmax = std::max(zmax, z);
+    }
+    const double margin = 1e-6 * (double)hh;
+    if (zmin >= (double)fzs + margin) return 0;
+    if (zmax < (double)fzs - margin) return 1;
+    return -1;
+}
+
 void build_model(const sdd_model_desc *m, ModelDev &M) {
     std::memset(&M, 0, sizeof(M));
     const sdd_domain &d = m->domain;
@@ -315,6 +349,11 @@ void build_model(const sdd_model_desc *m, ModelDev &M) {
             } else {
                 M.gcode = GC_SHAPES4;  // straddles the surface
             }
+        } else if (M.gcode == GC_TRI1) {
+            const int side = triangle_side(M.shapes[0], M.fhw, M.fhh, M.fzs);
+            if (side == 0) M.shape_air = 0;
+            else if (side == 1) M.shape_air = 1;
+            else M.gcode = GC_SHAPES4;  // across or too near the surface
         }
     } else {
         M.gcode = GC_RASTER;

@@ -107,7 +107,7 @@ struct Occupancy<8> {
     }
 };
 
-// Region counters of the one-shape programs (GC_CONTACT, GC_RECT1): ce steps
+// Region counters of the one-shape programs (GC_CONTACT, GC_RECT1, GC_TRI1): ce steps
 // on the earth side of the surface, cs steps inside the shape.  The shape
 // lies wholly on one side of the surface, so these two give every
 // material's count at the exit (WalkerF32::counts).
@@ -129,10 +129,13 @@ struct WalkerF32 {
     static constexpr int kStored = KMAX - 1;
     static constexpr int kHist = KMAX == 8 ? 8 : 1;
     static constexpr bool kGrouped = GC == GC_RASTER_MULTI;
+    // 24 resident warps whose iterations carry four independent Philox
+    // chains keep the issue slots fuller than 32 warps in 64 registers
+    static constexpr int kMinCTAs = 3;
 
     // one-shape programs count regions (two predicated adds per step in
     // place of the material selects and the power sums)
-    static constexpr bool kRegions = GC == GC_CONTACT || GC == GC_RECT1;
+    static constexpr bool kRegions = GC == GC_CONTACT || GC == GC_RECT1 || GC == GC_TRI1;
 
     float X, Z, dmin;  // centred position, distance to the nearest wall
     uint32_t n;        // Euler steps accepted (even at the start of iterate)
@@ -197,6 +200,21 @@ struct WalkerF32 {
                 "@ps add.u32 %1, %1, 1;\n\t}"
                 : "+r"(occ.ce), "+r"(occ.cs)
                 : "f"(X), "f"(Z), "f"(M.fzs), "f"(M.shapes[0].f[0]));
+        } else if (GC == GC_TRI1) {
+            // the three edge functions as in in_tri(), the compares chained
+            const ShapeDev &S = M.shapes[0];
+            const float e0 = fmaf(S.f[0], X, fmaf(S.f[1], Z, S.f[2]));
+            const float e1 = fmaf(S.f[3], X, fmaf(S.f[4], Z, S.f[5]));
+            const float e2 = fmaf(S.f[6], X, fmaf(S.f[7], Z, S.f[8]));
+            asm("{\n\t.reg .pred pe, ps;\n\t"
+                "setp.ge.ftz.f32 pe, %2, %3;\n\t"
+                "setp.ge.ftz.f32 ps, %4, 0f00000000;\n\t"
+                "setp.ge.and.ftz.f32 ps, %5, 0f00000000, ps;\n\t"
+                "setp.ge.and.ftz.f32 ps, %6, 0f00000000, ps;\n\t"
+                "@pe add.u32 %0, %0, 1;\n\t"
+                "@ps add.u32 %1, %1, 1;\n\t}"
+                : "+r"(occ.ce), "+r"(occ.cs)
+                : "f"(Z), "f"(M.fzs), "f"(e0), "f"(e1), "f"(e2));
         } else {
             asm("{\n\t.reg .pred pe, ps;\n\t"
                 "setp.ge.ftz.f32 pe, %3, %4;\n\t"

@@ -27,6 +27,7 @@ struct WalkerF64 {
     static constexpr int KMAX = KMAX_;
     static constexpr bool kCoop = false;  // no cooperative tail: the parity walk stays plain
     static constexpr bool kGrouped = false;  // one queue (a grouped plan's order is one queue too)
+    static constexpr int kMinCTAs = 3;
     using Occ = uint32_t;
     using HistT = uint32_t;
     static constexpr int kStored = KMAX - 1;

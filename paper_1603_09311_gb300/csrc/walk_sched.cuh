@@ -188,12 +188,11 @@ struct ExitInfo {
 //   static sample(M, T, A, model, e, x, z, th, wall, mlast, counts) -> double2
 //   static to_abs(M, x, z, ax, az)
 //   kGrouped: takes items from per-model queues (multi-model launches)
-// Launch bounds: at most 256 threads, and at least 3 such CTAs per SM, which
-// leaves up to 85 registers a thread.  24 resident warps whose iterations
-// carry four independent Philox chains keep the issue slots fuller than 32
-// warps squeezed into 64 registers.
+//   kMinCTAs: CTAs of 256 threads that must fit on an SM (the register bound)
+// Launch bounds: at most 256 threads, and at least W::kMinCTAs such CTAs per
+// SM: 3 leaves up to 85 registers a thread, 4 leaves 64.
 template <class W>
-__global__ void __launch_bounds__(256, 3) walk_kernel(const __grid_constant__ ModelDev M,
+__global__ void __launch_bounds__(256, W::kMinCTAs) walk_kernel(const __grid_constant__ ModelDev M,
                                                    const WalkArgs A) {
     using Real = typename W::Real;
     constexpr int KMAX = W::KMAX;

@@ -43,6 +43,7 @@ struct WalkerTM {
     static constexpr bool kF64 = sizeof(Real) == 8;
     static constexpr bool kCoop = false;
     static constexpr bool kGrouped = false;
+    static constexpr int kMinCTAs = 3;
     using Occ = Real;  // occupation time of every strip
     using HistT = Real;
     static constexpr int kStored = KMAX;
@@ -381,6 +382,7 @@ struct WalkerTM32 {
     static constexpr int KMAX = KMAX_;
     static constexpr bool kCoop = false;
     static constexpr bool kGrouped = false;
+    static constexpr int kMinCTAs = 3;
     using Occ = float;
     using HistT = float;
     static constexpr int kStored = KMAX;

@@ -70,6 +70,10 @@ MODELS = {
     # single-rectangle program counts regions only for a shape on one side)
     "rect_air": (_one_rect((-0.3, 0.3, -0.4, -0.1)), (0.0, -0.05)),
     "rect_straddle": (_one_rect((-0.2, 0.3, -0.2, 0.3)), (0.0, 0.1)),
+    # one triangle wholly in the air (the single-triangle program's other side)
+    "tri_air": ({"domain": I.DOMAIN, "kappa": [[0.0, 2.0, 20.0]], "bg": (0, 1),
+                 "shapes": [(1, 2, (-0.4, -0.45, 0.3, -0.35, -0.1, -0.05))], "g": ("columns", 1, 1)},
+                (-0.05, -0.2)),
     "quarterspace": (I.quarterspace(2.0, 20.0), (0.0, 0.5)),
     "block16": (I.block_batched(), (0.2, 0.35)),
     "triangle": (I.triangle(), (0.05, 0.4)),
@@ -155,7 +159,8 @@ def test_fp32_independent_seeds_agree_with_oracle(name):
 
 
 @pytest.mark.parametrize("name,dt", [("quarterspace", 1e-3), ("quarterspace", 1e-4), ("block16", 1e-3),
-                                     ("rect_air", 1e-3), ("rect_straddle", 1e-3), ("triangle", 1e-3)])
+                                     ("rect_air", 1e-3), ("rect_straddle", 1e-3), ("triangle", 1e-3),
+                                     ("tri_air", 1e-3)])
 def test_fp32_walks_follow_the_oracle_streams(name, dt):
     # walk by walk: the FP32 walk takes the oracle's steps, wall and
     # per-material counts (the one-shape programs count regions and derive
