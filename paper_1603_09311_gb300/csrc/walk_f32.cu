@@ -28,9 +28,7 @@ namespace sdd {
 // Uniforms of the single-precision walk: the low 23 bits of a Philox word as
 // the mantissa of a float in [1, 2); u = (w mod 2^23 + 1/2) 2^-23 exactly
 // (1.m - (1 - 2^-24), an exact difference by Sterbenz' lemma).
-__device__ __forceinline__ float one_plus(uint32_t w) {
-    return __uint_as_float((w & 0x007fffffu) | 0x3f800000u);
-}
+__device__ __forceinline__ float one_plus(uint32_t w) { return mant_one(w); }
 __device__ __forceinline__ float uni23(uint32_t w) { return one_plus(w) - 0.99999994039535522f; }
 
 // Occupation counters.  KMAX = 2: the step count of material 1.  KMAX = 3, 4:

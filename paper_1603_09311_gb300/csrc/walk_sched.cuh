@@ -66,6 +66,15 @@ __device__ __forceinline__ uint4 philox4x32_10_pre(uint32_t c0, uint32_t c3, uin
     return c;
 }
 
+// The float 1.m whose mantissa m is the low 23 bits of w:
+// (w & 0x007fffff) | 0x3f800000 as one three-input logic operation, the
+// exponent bits held in a register (two immediates would take two).
+__device__ __forceinline__ float mant_one(uint32_t w) {
+    uint32_t r;
+    asm("lop3.b32 %0, %1, 0x007fffff, %2, 0xEA;" : "=r"(r) : "r"(w), "r"(0x3f800000u));
+    return __uint_as_float(r);
+}
+
 // 32 x 32 -> 64-bit product as one wide multiply.
 __device__ __forceinline__ void mul_wide(uint32_t a, uint32_t b, uint32_t &lo, uint32_t &hi) {
     uint64_t p;

@@ -640,7 +640,7 @@ struct WalkerTM32 {
     // (w mod 2^23 + 1/2) 2^-23 as the low 23 bits of w in the mantissa of a
     // float in [1, 2), minus 1 - 2^-24 (exact): the value of uni(w)
     __device__ __forceinline__ static float uni_m(uint32_t w) {
-        return __uint_as_float((w & 0x007fffffu) | 0x3f800000u) - 0.99999994039535522f;
+        return mant_one(w) - 0.99999994039535522f;
     }
     // One step of the short path, taken by every lane of the warp together
     // and always committed: the position moves to beta' whatever the lane's
