@@ -329,7 +329,7 @@ def serving(sdd, n_requests: int, seed: int = 5, prefix: int = 200):
             "small_requests": small_out}
 
 
-def tm_measure(sdd, torch, dev, peak_tinst, n_steps, cpu=True):
+def tm_measure(sdd, torch, dev, peak_tinst, n_steps, cpu=True, tune=True):
     """The TM walk on the analytic test model's 51 x 51 grid (2401 nodes x 1e4
     walks, dt 1e-4): walk-steps/s of the device entry point (CUDA events on the
     launching stream, L2 flushed between launches), its issue roofline, and
@@ -337,6 +337,7 @@ def tm_measure(sdd, torch, dev, peak_tinst, n_steps, cpu=True):
     w = I.workload("tm_analytic")
     n = len(w["nodes"])
     ctx = sdd.sdd_create(w["model"])
+    launch = tune_shape(sdd, ctx, w, w["dt"]) if tune else "default shape"
     d_nodes = torch.tensor(w["nodes"], dtype=torch.float64, device=dev)
     d_mean = torch.empty((n, ctx.E, 2), dtype=torch.float64, device=dev)
     d_se = torch.empty_like(d_mean)
@@ -366,6 +367,7 @@ def tm_measure(sdd, torch, dev, peak_tinst, n_steps, cpu=True):
            "launches": n_steps, "steps_per_launch": float(steps.mean()),
            "workload": "TM analytic test model: [-1,1]^2, D 1|10 across x=0, kappa -10 (lambda 10i), "
                        "2401 nodes (51x51 grid interior) x 1e4 walks, dt 1e-4, FP32 walk",
+           "launch": launch,
            "roofline": {"bound": "alu", "achieved": TM_INST_PER_STEP * value / 1e12, "peak": peak_tinst,
                         "unit": "Tinst/s", "frac": TM_INST_PER_STEP * value / 1e12 / peak_tinst,
                         "inst_per_step": TM_INST_PER_STEP}}
@@ -442,7 +444,14 @@ def fp32_error(sdd, ctx, w, idx, n_sub, dt, seed, ref_cache=None):
                  "sample": f"nodes {idx} x first {n_sub} walks, dt {dt} ({steps:.3e} steps, {sec:.1f} s)"}
 
 
-def block_measure(sdd, torch, dev, peak_tinst, flush, reps=2, cpu=True):
+def tune_shape(sdd, ctx, w, dt):
+    """The launch shape for a workload, searched on w (untimed; the context
+    keeps the fastest, as the main line's does)."""
+    cfg, rate = sdd.sdd_autotune(ctx, w["nodes"], w["n_paths"], dt, w["seed"] + 999)
+    return dict(cfg, walk_steps_per_s_while_tuning=rate)
+
+
+def block_measure(sdd, torch, dev, peak_tinst, flush, reps=2, cpu=True, tune=True):
     """The batched block workload in full: 256 nodes on the perimeter of the
     block [-0.2,0.2]x[0.2,0.5] (rates 20 and 0.2 in host 2, x 8 frequency
     scales = 16 evaluations per walk), walks per node log-uniform in
@@ -451,6 +460,8 @@ def block_measure(sdd, torch, dev, peak_tinst, flush, reps=2, cpu=True):
     w = I.workload("block")
     ctx = sdd.sdd_create(w["model"])
     sdd.sdd_interface_values(ctx, w["nodes"][:4], 2000, w["dt"], 1)  # loads the kernel
+    # shape searched on 64 of the nodes with their walk counts
+    launch = tune_shape(sdd, ctx, I.scaled(w, n_nodes=64), w["dt"]) if tune else "default shape"
     ms, steps, walks = device_launches(sdd, torch, dev, ctx, w, w["dt"],
                                        [w["seed"] + k for k in range(reps)], flush)
     value = float(steps.sum() / (sum(ms) * 1e-3))
@@ -460,6 +471,7 @@ def block_measure(sdd, torch, dev, peak_tinst, flush, reps=2, cpu=True):
            "workload": "block in half-space: 256 perimeter nodes, 1e4-1e6 walks per node (log-uniform, "
                        "seed 3), 16 evaluations per walk (rates 20 | 0.2 x 8 scales 0.1-100), dt 1e-4, "
                        "one launch, FP32 walk, FP64 sums",
+           "launch": launch,
            "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tinst, "unit": "Tinst/s",
                         "frac": ach / peak_tinst, "inst_per_step": RECT_INST_PER_STEP}}
     if cpu:
@@ -470,7 +482,7 @@ def block_measure(sdd, torch, dev, peak_tinst, flush, reps=2, cpu=True):
     return out
 
 
-def triangle_measure(sdd, torch, dev, peak_tinst, flush, cpu=True):
+def triangle_measure(sdd, torch, dev, peak_tinst, flush, cpu=True, tune=True):
     """The triangle time-step sweep in full: 128 nodes on the edges of the
     triangle (-0.3,0.2),(0.3,0.2),(0,0.6) (rate 50 in host 2), 1e6 walks per
     node, dt in {1e-3, 3e-4, 1e-4, 3e-5}, one FP32 launch per dt; the FP64
@@ -479,6 +491,8 @@ def triangle_measure(sdd, torch, dev, peak_tinst, flush, cpu=True):
     w = I.workload("triangle")
     ctx = sdd.sdd_create(w["model"])
     sdd.sdd_interface_values(ctx, w["nodes"][:4], 2000, 1e-3, 1)
+    # one shape for the sweep, searched at dt 1e-4 on 2e5 walks per node
+    launch = tune_shape(sdd, ctx, I.scaled(w, paths_per_node=200_000), 1e-4) if tune else "default shape"
     sub = [0, 40, 85, 127]
     per_dt, tot_steps, tot_ms = [], 0.0, 0.0
     for dt in (1e-3, 3e-4, 1e-4, 3e-5):
@@ -512,6 +526,7 @@ def triangle_measure(sdd, torch, dev, peak_tinst, flush, cpu=True):
     return {"metric": METRIC, "value": value, "unit": METRIC, "ms": tot_ms, "steps": tot_steps,
             "workload": "triangle in half-space: 128 edge nodes x 1e6 walks, rate 50 in host 2, "
                         "dt 1e-3, 3e-4, 1e-4, 3e-5 (one launch each), FP32 walk, FP64 sums",
+            "launch": launch,
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tinst, "unit": "Tinst/s",
                          "frac": ach / peak_tinst, "inst_per_step": TRI_INST_PER_STEP},
             "per_dt": per_dt}
@@ -1032,9 +1047,10 @@ def main():
             # of the line under their own node ids, their first 20000 walks
             line["fp32_error"], _ = fp32_error(sdd, ctx, w, [9, 32, 50, 63], 20000, w["dt"], w["seed"])
         if full and "block" in objs:
-            line["block"] = block_measure(sdd, torch, dev, peak_tinst, flush, cpu=cpu)
+            line["block"] = block_measure(sdd, torch, dev, peak_tinst, flush, cpu=cpu, tune=not args.no_autotune)
         if full and "triangle" in objs:
-            line["triangle"] = triangle_measure(sdd, torch, dev, peak_tinst, flush, cpu=cpu)
+            line["triangle"] = triangle_measure(sdd, torch, dev, peak_tinst, flush, cpu=cpu,
+                                                tune=not args.no_autotune)
         if args.small and world == 1 and args.objects != "all":
             # small cases of the block and triangle programs (for profiler
             # captures): 64 of the block's nodes with 1/8 of their walks; 16 of
@@ -1043,7 +1059,8 @@ def main():
         if args.serve_requests > 0 and full and "serving" in objs:
             line["serving"] = serving(sdd, args.serve_requests)
         if full and "tm" in objs:
-            line["tm"] = tm_measure(sdd, torch, dev, peak_tinst, max(1, min(args.steps, 3)), cpu=cpu)
+            line["tm"] = tm_measure(sdd, torch, dev, peak_tinst, max(1, min(args.steps, 3)), cpu=cpu,
+                                    tune=not args.no_autotune)
         if full and "interp" in objs:
             line["interp"] = interp_measure(sdd, cpu=cpu)
         if full and "mt" in objs:
