@@ -337,7 +337,7 @@ def tm_measure(sdd, torch, dev, peak_tinst, n_steps, cpu=True, tune=True):
     w = I.workload("tm_analytic")
     n = len(w["nodes"])
     ctx = sdd.sdd_create(w["model"])
-    launch = tune_shape(sdd, ctx, w, w["dt"]) if tune else "default shape"
+    shape = tune_shape(sdd, ctx, w, w["dt"]) if tune else "default shape"
     d_nodes = torch.tensor(w["nodes"], dtype=torch.float64, device=dev)
     d_mean = torch.empty((n, ctx.E, 2), dtype=torch.float64, device=dev)
     d_se = torch.empty_like(d_mean)
@@ -367,7 +367,7 @@ def tm_measure(sdd, torch, dev, peak_tinst, n_steps, cpu=True, tune=True):
            "launches": n_steps, "steps_per_launch": float(steps.mean()),
            "workload": "TM analytic test model: [-1,1]^2, D 1|10 across x=0, kappa -10 (lambda 10i), "
                        "2401 nodes (51x51 grid interior) x 1e4 walks, dt 1e-4, FP32 walk",
-           "launch": launch,
+           "launch": shape,
            "roofline": {"bound": "alu", "achieved": TM_INST_PER_STEP * value / 1e12, "peak": peak_tinst,
                         "unit": "Tinst/s", "frac": TM_INST_PER_STEP * value / 1e12 / peak_tinst,
                         "inst_per_step": TM_INST_PER_STEP}}
@@ -461,7 +461,7 @@ def block_measure(sdd, torch, dev, peak_tinst, flush, reps=2, cpu=True, tune=Tru
     ctx = sdd.sdd_create(w["model"])
     sdd.sdd_interface_values(ctx, w["nodes"][:4], 2000, w["dt"], 1)  # loads the kernel
     # shape searched on 64 of the nodes with their walk counts
-    launch = tune_shape(sdd, ctx, I.scaled(w, n_nodes=64), w["dt"]) if tune else "default shape"
+    shape = tune_shape(sdd, ctx, I.scaled(w, n_nodes=64), w["dt"]) if tune else "default shape"
     ms, steps, walks = device_launches(sdd, torch, dev, ctx, w, w["dt"],
                                        [w["seed"] + k for k in range(reps)], flush)
     value = float(steps.sum() / (sum(ms) * 1e-3))
@@ -471,7 +471,7 @@ def block_measure(sdd, torch, dev, peak_tinst, flush, reps=2, cpu=True, tune=Tru
            "workload": "block in half-space: 256 perimeter nodes, 1e4-1e6 walks per node (log-uniform, "
                        "seed 3), 16 evaluations per walk (rates 20 | 0.2 x 8 scales 0.1-100), dt 1e-4, "
                        "one launch, FP32 walk, FP64 sums",
-           "launch": launch,
+           "launch": shape,
            "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tinst, "unit": "Tinst/s",
                         "frac": ach / peak_tinst, "inst_per_step": RECT_INST_PER_STEP}}
     if cpu:
@@ -492,7 +492,7 @@ def triangle_measure(sdd, torch, dev, peak_tinst, flush, cpu=True, tune=True):
     ctx = sdd.sdd_create(w["model"])
     sdd.sdd_interface_values(ctx, w["nodes"][:4], 2000, 1e-3, 1)
     # one shape for the sweep, searched at dt 1e-4 on 2e5 walks per node
-    launch = tune_shape(sdd, ctx, I.scaled(w, paths_per_node=200_000), 1e-4) if tune else "default shape"
+    shape = tune_shape(sdd, ctx, I.scaled(w, paths_per_node=200_000), 1e-4) if tune else "default shape"
     sub = [0, 40, 85, 127]
     per_dt, tot_steps, tot_ms = [], 0.0, 0.0
     for dt in (1e-3, 3e-4, 1e-4, 3e-5):
@@ -526,7 +526,7 @@ def triangle_measure(sdd, torch, dev, peak_tinst, flush, cpu=True, tune=True):
     return {"metric": METRIC, "value": value, "unit": METRIC, "ms": tot_ms, "steps": tot_steps,
             "workload": "triangle in half-space: 128 edge nodes x 1e6 walks, rate 50 in host 2, "
                         "dt 1e-3, 3e-4, 1e-4, 3e-5 (one launch each), FP32 walk, FP64 sums",
-            "launch": launch,
+            "launch": shape,
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak_tinst, "unit": "Tinst/s",
                          "frac": ach / peak_tinst, "inst_per_step": TRI_INST_PER_STEP},
             "per_dt": per_dt}
