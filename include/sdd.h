@@ -728,6 +728,30 @@ sdd_status sdd_server_get_stats(sdd_server *srv, sdd_server_stats *out);
 int32_t sdd_n_eval(const sdd_ctx *ctx);
 int32_t sdd_n_materials(const sdd_ctx *ctx);
 
+/* Material-lookup programs of the single-precision walk: how the occupation
+ * update of Sec. 3.1 (the step's time to the material of the new point)
+ * finds the material.  The one-shape programs count steps by region (earth
+ * side of the surface, inside the shape) and form the material counts at the
+ * walk's exit; they are chosen only for a shape wholly on one side of z = 0. */
+#define SDD_PROGRAM_LAYERS 0    /* layered background (air z < 0, earth z >= 0) only */
+#define SDD_PROGRAM_RECT 1      /* one rectangle on one side of the surface */
+#define SDD_PROGRAM_TRIANGLE 2  /* one triangle on one side of the surface */
+#define SDD_PROGRAM_SHAPES4 3   /* up to 4 shapes, or one shape across the surface */
+#define SDD_PROGRAM_SHAPES16 4  /* up to 16 shapes */
+#define SDD_PROGRAM_RASTER 5    /* int8 raster through its tile map */
+#define SDD_PROGRAM_CONTACT 6   /* one rectangle that is the earth right of x0 (vertical contact) */
+#define SDD_PROGRAM_TM 8        /* TM walk over vertical strips */
+
+/* The lookup program sdd_create would give a model, decided on the host by
+ * the same code; no CUDA call and no allocation, so it works without a GPU.
+ *   model: as for sdd_create (read only, not kept).
+ *   *program: one of SDD_PROGRAM_*.
+ *   *shape_side (nullable): for SDD_PROGRAM_RECT, _TRIANGLE and _CONTACT 0 when
+ *   the shape lies in the earth and 1 when it lies in the air; -1 otherwise.
+ * Errors: SDD_E_ARG for a NULL model or program, and every model check of
+ * sdd_create. */
+sdd_status sdd_model_program(const sdd_model_desc *model, int32_t *program, int32_t *shape_side);
+
 /* Static description of a status; never NULL. */
 const char *sdd_status_str(sdd_status s);
 

@@ -10,6 +10,7 @@
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <map>
 #include <mutex>
 #include <thread>
@@ -970,6 +971,27 @@ void sdd_destroy(sdd_ctx *c) {
 
 int32_t sdd_n_eval(const sdd_ctx *c) { return c ? c->E : 0; }
 int32_t sdd_n_materials(const sdd_ctx *c) { return c ? c->K : 0; }
+
+static_assert(SDD_PROGRAM_LAYERS == GC_LAYER && SDD_PROGRAM_RECT == GC_RECT1 &&
+                  SDD_PROGRAM_TRIANGLE == GC_TRI1 && SDD_PROGRAM_SHAPES4 == GC_SHAPES4 &&
+                  SDD_PROGRAM_SHAPES16 == GC_SHAPES16 && SDD_PROGRAM_RASTER == GC_RASTER &&
+                  SDD_PROGRAM_CONTACT == GC_CONTACT && SDD_PROGRAM_TM == GC_TM,
+              "lookup program codes of the header and of the walk differ");
+
+sdd_status sdd_model_program(const sdd_model_desc *model, int32_t *program, int32_t *shape_side) {
+    if (!program) return fail(SDD_E_ARG, "program is NULL");
+    const sdd_status st = check_model(model);
+    if (st != SDD_OK) return st;
+    std::unique_ptr<ModelDev> M(new (std::nothrow) ModelDev());
+    if (!M) return fail(SDD_E_OOM, "host allocation failed");
+    build_model(model, *M);
+    *program = M->gcode;
+    if (shape_side) {
+        const bool one = M->gcode == GC_RECT1 || M->gcode == GC_TRI1 || M->gcode == GC_CONTACT;
+        *shape_side = one ? M->shape_air : -1;
+    }
+    return SDD_OK;
+}
 
 sdd_status sdd_interface_values(sdd_ctx *ctx, const double *nodes_xz, const uint32_t *node_ids,
                                 int32_t n_nodes, const int64_t *n_paths, double dt,

@@ -222,6 +222,7 @@ SIGNATURES = [
       ctypes.c_uint64, P(sdd_config), P(sdd_config), P(ctypes.c_double)]),
     ("sdd_n_eval", ctypes.c_int32, [ctypes.c_void_p]),
     ("sdd_n_materials", ctypes.c_int32, [ctypes.c_void_p]),
+    ("sdd_model_program", ctypes.c_int, [P(sdd_model_desc), P(ctypes.c_int32), P(ctypes.c_int32)]),
     ("sdd_status_str", ctypes.c_char_p, [ctypes.c_int]),
     ("sdd_last_error", ctypes.c_char_p, []),
 ]
@@ -337,6 +338,23 @@ def sdd_create(model: dict) -> Context:
     if st != SDD_OK:
         raise SddError(st, "sdd_create")
     return Context(h, d.n_eval, d.n_materials)
+
+
+# lookup programs of the single-precision walk (SDD_PROGRAM_* in include/sdd.h)
+PROGRAMS = {0: "layers", 1: "rect", 2: "triangle", 3: "shapes4", 4: "shapes16", 5: "raster",
+            6: "contact", 8: "tm"}
+
+
+def sdd_model_program(model: dict):
+    """The lookup program sdd_create would give the model (host only, no GPU):
+    (program name, shape side) with side 0 earth, 1 air, -1 not a one-shape
+    program."""
+    d, _keep = make_desc(model)
+    prog, side = ctypes.c_int32(), ctypes.c_int32()
+    st = lib().sdd_model_program(ctypes.byref(d), ctypes.byref(prog), ctypes.byref(side))
+    if st != SDD_OK:
+        raise SddError(st, "sdd_model_program")
+    return PROGRAMS[prog.value], side.value
 
 
 def sdd_destroy(ctx: Context) -> None:
