@@ -752,6 +752,23 @@ int32_t sdd_n_materials(const sdd_ctx *ctx);
  * sdd_create. */
 sdd_status sdd_model_program(const sdd_model_desc *model, int32_t *program, int32_t *shape_side);
 
+/* The work items one evaluation is cut into, as a launch with `warps`
+ * resident warps cuts them (node values are independent, Sec. 5, so every
+ * node's paths are split into (node, path range) items that the warps take
+ * from one queue); host only, no CUDA call.
+ *   n_paths [n_nodes] host; warps >= 1; guided_factor >= 1 (guided items of
+ *   about 1 / (guided_factor x warps) of the paths not yet cut, multiples of
+ *   32 shrinking toward the end of the queue) used when chunk_paths == 0,
+ *   else fixed items of chunk_paths paths, node by node.
+ *   node, path0, count [max_items] host, written in queue order; *n_items
+ *   the number of items.
+ * Errors: SDD_E_ARG for n_nodes < 0, a negative path count, warps < 1,
+ * guided_factor < 1, chunk_paths < 0, a NULL pointer, or a plan of more than
+ * max_items items (*n_items then holds the number needed). */
+sdd_status sdd_plan_items(int32_t n_nodes, const int64_t *n_paths, int32_t warps, int32_t guided_factor,
+                          int32_t chunk_paths, int32_t max_items, int32_t *node, uint32_t *path0,
+                          int32_t *count, int32_t *n_items);
+
 /* Static description of a status; never NULL. */
 const char *sdd_status_str(sdd_status s);
 

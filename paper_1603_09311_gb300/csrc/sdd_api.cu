@@ -993,6 +993,36 @@ sdd_status sdd_model_program(const sdd_model_desc *model, int32_t *program, int3
     return SDD_OK;
 }
 
+sdd_status sdd_plan_items(int32_t n_nodes, const int64_t *n_paths, int32_t warps, int32_t guided_factor,
+                          int32_t chunk_paths, int32_t max_items, int32_t *node, uint32_t *path0,
+                          int32_t *count, int32_t *n_items) {
+    if (!n_items) return fail(SDD_E_ARG, "n_items is NULL");
+    *n_items = 0;
+    if (n_nodes < 0 || (n_nodes > 0 && !n_paths)) return fail(SDD_E_ARG, "bad nodes / n_paths");
+    if (warps < 1 || guided_factor < 1 || chunk_paths < 0 || max_items < 0)
+        return fail(SDD_E_ARG, "warps and guided_factor must be >= 1, chunk_paths and max_items >= 0");
+    for (int32_t j = 0; j < n_nodes; ++j)
+        if (n_paths[j] < 0 || n_paths[j] > 0xffffffffLL) return fail(SDD_E_ARG, "path count out of range");
+    Launch L{};
+    L.grid = warps;
+    L.block = 32;
+    L.factor = guided_factor;
+    L.chunk = chunk_paths;
+    const Plan P = plan_work(n_nodes, nullptr, n_paths, 0, L);
+    const int64_t n = (int64_t)P.items.size();
+    if (n > 0x7fffffffLL) return fail(SDD_E_ARG, "too many items");
+    *n_items = (int32_t)n;
+    if (n > max_items) return fail(SDD_E_ARG, "more items than max_items");
+    if (n > 0 && (!node || !path0 || !count)) return fail(SDD_E_ARG, "output pointer is NULL");
+    for (int64_t q = 0; q < n; ++q) {
+        const Item &I = P.items[P.order.empty() ? q : P.order[q]];
+        node[q] = I.node;
+        path0[q] = I.path0;
+        count[q] = I.count;
+    }
+    return SDD_OK;
+}
+
 sdd_status sdd_interface_values(sdd_ctx *ctx, const double *nodes_xz, const uint32_t *node_ids,
                                 int32_t n_nodes, const int64_t *n_paths, double dt,
                                 uint64_t seed, const sdd_config *cfg, double *mean, double *se,

@@ -223,6 +223,9 @@ SIGNATURES = [
     ("sdd_n_eval", ctypes.c_int32, [ctypes.c_void_p]),
     ("sdd_n_materials", ctypes.c_int32, [ctypes.c_void_p]),
     ("sdd_model_program", ctypes.c_int, [P(sdd_model_desc), P(ctypes.c_int32), P(ctypes.c_int32)]),
+    ("sdd_plan_items", ctypes.c_int, [ctypes.c_int32, P(ctypes.c_int64), ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.c_int32, ctypes.c_int32, P(ctypes.c_int32), P(ctypes.c_uint32),
+                                      P(ctypes.c_int32), P(ctypes.c_int32)]),
     ("sdd_status_str", ctypes.c_char_p, [ctypes.c_int]),
     ("sdd_last_error", ctypes.c_char_p, []),
 ]
@@ -355,6 +358,25 @@ def sdd_model_program(model: dict):
     if st != SDD_OK:
         raise SddError(st, "sdd_model_program")
     return PROGRAMS[prog.value], side.value
+
+
+def sdd_plan_items(n_paths, warps: int, guided_factor: int = 2, chunk_paths: int = 0):
+    """The work items of one evaluation in queue order (host only, no GPU):
+    arrays node, path0, count."""
+    npth = np.ascontiguousarray(np.asarray(n_paths, dtype=np.int64).reshape(-1))
+    n = ctypes.c_int32()
+    args = (len(npth), npth.ctypes.data_as(P(ctypes.c_int64)), int(warps), int(guided_factor), int(chunk_paths))
+    lib().sdd_plan_items(*args, 0, None, None, None, ctypes.byref(n))  # the number of items
+    m = max(n.value, 1)
+    node = np.zeros(m, dtype=np.int32)
+    path0 = np.zeros(m, dtype=np.uint32)
+    count = np.zeros(m, dtype=np.int32)
+    st = lib().sdd_plan_items(*args, m, node.ctypes.data_as(P(ctypes.c_int32)),
+                              path0.ctypes.data_as(P(ctypes.c_uint32)), count.ctypes.data_as(P(ctypes.c_int32)),
+                              ctypes.byref(n))
+    if st != SDD_OK:
+        raise SddError(st, "sdd_plan_items")
+    return node[:n.value], path0[:n.value], count[:n.value]
 
 
 def sdd_destroy(ctx: Context) -> None:
