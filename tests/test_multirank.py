@@ -1,4 +1,4 @@
-"""One evaluation split across ranks (gloo, world size 2, CPU).
+"""One evaluation split across ranks (gloo, world sizes 2 and 3, CPU).
 
 Each rank evaluates its cost-balanced slice of the (node, path-range) list
 with the oracle's range sums, writes them into its rows of a zero table, and
@@ -115,19 +115,22 @@ def test_mean_exit_time_of_the_cost_model():
     assert np.all(np.abs(edge) < 1e-9)
 
 
-def test_two_ranks_reproduce_one_process(tmp_path):
+@pytest.mark.parametrize("world", [2, 3])
+def test_ranks_reproduce_one_process(tmp_path, world):
+    # the table, and the node means formed from it, do not depend on the
+    # number of ranks or on their slices
     torch = pytest.importorskip("torch")
     import torch.multiprocessing as mp
     from oracle import oracle as O
     port = _free_port()
-    mp.start_processes(_worker, args=(2, port, str(tmp_path)), nprocs=2, join=True, start_method="spawn")
+    mp.start_processes(_worker, args=(world, port, str(tmp_path)), nprocs=world, join=True, start_method="spawn")
     w = _job()
-    P = S.plan(w["nodes"], w["n_paths"], CHUNK, 2, I.DOMAIN)
-    # both ranks hold a nonempty slice
-    assert 0 < P["bounds"][1] < len(P["node"])
+    P = S.plan(w["nodes"], w["n_paths"], CHUNK, world, I.DOMAIN)
+    # every rank holds a nonempty slice
+    assert np.all(np.diff(P["bounds"]) > 0)
     sums, nv, _ = O.range_sums(w["model"], w["nodes"][P["node"]], P["node"], P["begin"], P["count"],
                                w["dt"], w["seed"], threads=3)
-    for r in (0, 1):
+    for r in range(world):
         t = np.load(tmp_path / f"table{r}.npy")
         n = np.load(tmp_path / f"nvalid{r}.npy")
         assert np.array_equal(t, sums) and np.array_equal(n, nv)
